@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the pgen graph generators on GB300.
+
+One step = one full pass of the generation path over the workload:
+  pba_n2p30_b1024_m5  two-phase PBA, 2^30 new vertices in 1024 blocks, m = 5
+                      (prefix -> phase 1 -> count scan -> phase 2 + substitution)
+  kron_k20_m16x_csr   stochastic Kronecker k = 20, 16 * 2^20 edges, then CSR
+  ba_n100k_m4         serial BA, 100,000 new vertices, m = 4
+Prints ONE JSON line (rank 0). Under torchrun every rank generates its own
+instance (seed + rank): replicas, weak scaling, no collective on the data path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference    # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1003_3684_gb300 import workloads as W  # noqa: E402
+
+DEFAULT_WORKLOAD = "pba_n2p30_b1024_m5"
+
+# Algorithmic work per unit (32-bit lane operations and bytes), per kernel.
+# A Philox4x32-10 call is 60 lane ops (10 rounds of two 32x32->64 multiplies,
+# counted as two ops each, and two three-input XORs); a 64-bit uniform draw
+# adds 4. Chain links recomputed beyond the first draw of a unit are NOT
+# counted: they are the implementation's overhead, not the method's work.
+PHILOX_OPS = 60
+KERNEL_WORK = {
+    # unit = one phase-1 entry: its own draw (coin + uniform index) + select
+    "pba_phase1": dict(ops=PHILOX_OPS + 4 + 6, bytes=2),
+    # unit = one edge: its endpoint draw + uniform + sigma/E index arithmetic
+    # and the rank bookkeeping; bytes = the (src, dst) pair written
+    "pba_emit": dict(ops=PHILOX_OPS + 4 + 16, bytes=8),
+    "ba_chain": dict(ops=PHILOX_OPS + 4 + 16, bytes=8),
+}
+
+
+def kron_work(k: int, id_bytes: int = 4):
+    # ceil(k/4) Philox calls + per level: 3 threshold compares + 2 shift-ors
+    return dict(ops=PHILOX_OPS * ((k + 3) // 4) + 5 * k, bytes=2 * id_bytes)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "utilization.gpu")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[0]), smax=float(parts[1]),
+                                 hw=parts[4], hwt=parts[5], swt=parts[6], swp=parts[7],
+                                 util=float(parts[8]) if parts[8] not in ("", "[N/A]") else 0.0))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        load = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in load),
+                    sm_max_mhz=max(r["smax"] for r in rows), reasons=sorted(reasons),
+                    samples=len(load))
+
+
+# --------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+# --------------------------------------------------------------------------
+def oracle_sample(name: str, cfg: dict, budget_s: float):
+    """Time the oracle, as it stands, on samples of the workload.
+
+    PBA: the full two-phase oracle on 2 blocks of the workload's own block size
+    (same n_b, m, n0, f, W): per-edge work is that of the full graph, which
+    only has more blocks. Kronecker: the oracle descent for 2^20 edges of the
+    same initiator and k, plus CSR of them. Returns (edges/s, description,
+    seconds, samples).
+    """
+    import oracle as o
+    t_total, edges_total, samples = 0.0, 0, 0
+    while samples == 0 or t_total < budget_s:
+        if cfg["kind"] == "pba" and cfg["blocks"] > 1:
+            B = 2
+            n = B * (cfg["n"] // cfg["blocks"])
+            t0 = time.perf_counter()
+            e, _, _ = o.pba(n, cfg["m"], B, cfg["n0"], cfg["faction_width"] if
+                            cfg["faction_width"] < B else 1, cfg["inter_frac"],
+                            cfg["seed"] + samples)
+            t_total += time.perf_counter() - t0
+            edges_total += e.shape[0]
+            desc = (f"or_pba, 2 blocks of n_b={cfg['n'] // cfg['blocks']}, m={cfg['m']}, "
+                    f"n0={cfg['n0']}, f={cfg['inter_frac']}: {e.shape[0]} edges per sample")
+        elif cfg["kind"] == "pba":
+            t0 = time.perf_counter()
+            e = o.ba(cfg["n"], cfg["m"], cfg["n0"], cfg["seed"] + samples)
+            t_total += time.perf_counter() - t0
+            edges_total += e.shape[0]
+            desc = f"or_ba, the full workload ({e.shape[0]} edges) per sample"
+        else:
+            M = 2**20
+            t0 = time.perf_counter()
+            e = o.kron(cfg["initiator"], cfg["k"], M, cfg["seed"] + samples)
+            if cfg.get("csr"):
+                o.csr(e, 2 ** cfg["k"])
+            t_total += time.perf_counter() - t0
+            edges_total += M
+            desc = f"or_kron k={cfg['k']}, {M} edges per sample" + (" + or_csr" if cfg.get("csr") else "")
+        samples += 1
+    return edges_total / t_total, desc, t_total, samples
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    cfg = W.CONFIGS[args.workload]
+    times, eps = [], []
+    desc = ""
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, cfg, 0.0)
+    for _ in range(args.steps):
+        v, desc, t, _ = oracle_sample(args.workload, cfg, 0.0)
+        times.append(t)
+        eps.append(v)
+    value = sum(v * t for v, t in zip(eps, times)) / sum(times)
+    line = dict(impl="reference", metric="edges/sec", value=value, unit="edges/s",
+                n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * statistics.mean(times), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
+                config=dict(workload=args.workload, sample=desc),
+                cpu_baseline=dict(kind="oracle", value=value, unit="edges/s", cores=1,
+                                  sample=desc),
+                e2e=dict(value=value, unit="edges/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_pgen(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1003_3684_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1003_3684_gb300 as pg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = dict(W.CONFIGS[args.workload])
+    seed = cfg["seed"] + rank
+    stream = torch.cuda.current_stream()
+    kind = cfg["kind"]
+
+    if kind == "pba":
+        n, m, B, n0 = cfg["n"], cfg["m"], cfg["blocks"], cfg["n0"]
+        E = pg.pg_pba_edge_count(n, m, B, n0)
+        out = torch.empty((E, 2), dtype=torch.int32, device=dev)
+        ws_bytes = pg.pg_pba_workspace_size(n, m, B)
+        ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+
+        def step():
+            pg.gen_pba(n, m, B, n0, cfg["faction_width"], cfg["inter_frac"], seed, out=out,
+                       workspace=ws if B > 1 else None)
+        units = {"pba_phase1": B * (n // B) * m, "pba_emit": B * (n // B) * m,
+                 "ba_chain": n * m}
+        work = dict(KERNEL_WORK)
+        out_bytes = E * 8
+        cfg_json = dict(workload=args.workload, n=n, m=m, blocks=B, n0=n0,
+                        faction_width=cfg["faction_width"], inter_frac=cfg["inter_frac"],
+                        seed=cfg["seed"], edges_per_step=E, id_width=32,
+                        workspace_bytes=ws_bytes)
+    else:
+        k, M = cfg["k"], cfg["n_edges"]
+        N = 2**k
+        E = M
+        out = torch.empty((M, 2), dtype=torch.int32, device=dev)
+        row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(M, dtype=torch.int32, device=dev)
+        ws_bytes = pg.pg_csr_workspace_size(M, N) if cfg.get("csr") else 0
+        ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+
+        def step():
+            pg.gen_kronecker(cfg["initiator"], k, M, seed, out=out)
+            if cfg.get("csr"):
+                pg.edges_to_csr(out, N, row_ptr=row_ptr, col=col, workspace=ws)
+        units = {"kron_descent_n0_2": M}
+        work = {"kron_descent_n0_2": kron_work(k)}
+        out_bytes = M * 8 + ((N + 1) * 8 + M * 4 if cfg.get("csr") else 0)
+        cfg_json = dict(workload=args.workload, initiator=cfg["initiator"], k=k, n_edges=M,
+                        seed=cfg["seed"], csr=bool(cfg.get("csr")), edges_per_step=M,
+                        id_width=32)
+    cfg_json["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    cfg_json["l2"] = (f"no flush: each step writes {out_bytes / 1e9:.2f} GB of output, "
+                      f"{'more' if out_bytes > 129e6 else 'LESS'} than the 129 MB L2")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pg.pg_trace_dump()              # drop anything recorded so far
+    pg.pg_trace_enable(True)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    pg.pg_trace_enable(False)
+    kernels = pg.pg_trace_dump()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = E * args.steps * world / (ms_max / 1000.0)
+    launches = sum(v[0] for v in kernels.values())
+
+    # roofline of the dominant kernel
+    peaks = load_peaks()
+    sms = pg.pg_device_sm_count()
+    alu_peak = sms * 128 * peaks["sm_max_mhz"] * 1e6       # int32 lane ops / s
+    hbm_peak = peaks["hbm_gbs"] * 1e9
+    dom = max((kname for kname in kernels if kname in work), key=lambda x: kernels[x][1],
+              default=None)
+    roof = None
+    if dom:
+        nl, tot_ms = kernels[dom]
+        per_launch_s = tot_ms / nl / 1000.0
+        u = units[dom]
+        ops_rate = u * work[dom]["ops"] / per_launch_s
+        byte_rate = u * work[dom]["bytes"] / per_launch_s
+        t_alu = u * work[dom]["ops"] / alu_peak
+        t_hbm = u * work[dom]["bytes"] / hbm_peak
+        if t_alu >= t_hbm:
+            roof = dict(bound="alu", kernel=dom, achieved=ops_rate / 1e12, peak=alu_peak / 1e12,
+                        unit="Tops/s (int32 lane ops)", frac=ops_rate / alu_peak, traffic=None,
+                        hbm=dict(achieved=byte_rate / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
+                                 frac=byte_rate / hbm_peak),
+                        peak_source=f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz")
+        else:
+            roof = dict(bound="hbm", kernel=dom, achieved=byte_rate / 1e9, peak=peaks["hbm_gbs"],
+                        unit="GB/s", frac=byte_rate / hbm_peak, traffic=None,
+                        peak_source=f"{peaks['source']} MEASURED_PEAKS hbm_gbs")
+        roof["ms_per_launch"] = per_launch_s * 1000.0
+        roof["units_per_launch"] = u
+        roof["ops_per_unit"] = work[dom]["ops"]
+        roof["bytes_per_unit"] = work[dom]["bytes"]
+        # whole-step roofline: slower of output bytes at HBM peak and the
+        # algorithmic integer work of every kernel at the int32 peak
+        step_alu = sum(units[kk] * work[kk]["ops"] for kk in kernels if kk in work) / alu_peak
+        step_hbm = out_bytes / hbm_peak
+        roof["step_bound_ms"] = 1000.0 * max(step_alu, step_hbm)
+        roof["step_frac"] = roof["step_bound_ms"] / (ms_max / args.steps)
+
+    line = dict(metric="edges/sec", value=value, unit="edges/s", n_gpus=world,
+                steps=args.steps, warmup=args.warmup, ms_per_step=ms_max / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u32",
+                data="synthetic", config=cfg_json, roofline=roof, gpu_launches=launches,
+                kernels={kk: [v[0], round(v[1], 4)] for kk, v in kernels.items()},
+                clocks=clocks)
+    if kind == "pba" and cfg["blocks"] > 1:
+        line["paper_context"] = ("PBA 1e9 vertices / 5e9 edges in 12.39 s on 1,000 CPUs "
+                                 "(~4.0e8 edges/s): context, other hardware")
+
+    # end to end through the public API with host buffers: the step plus the
+    # device-to-host copy of everything it produced into pinned host memory
+    if not args.no_e2e:
+        line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, tsec, ns = oracle_sample(args.workload, cfg, args.cpu_budget)
+        line["cpu_baseline"] = dict(value=v, unit="edges/s", cores=1, kind="oracle",
+                                    sample=f"{desc}; {ns} samples, {tsec:.1f} s")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(args, step, out, cfg, E, dev, world, rank):
+    import torch
+    import torch.distributed as dist
+    out_bytes = out.numel() * out.element_size()
+    chunk = min(out_bytes, 4 << 30)
+    host = torch.empty(chunk, dtype=torch.uint8, pin_memory=True)
+    flat = out.view(torch.uint8).view(-1)
+    h2d = 0
+    if cfg["kind"] == "kron":
+        init = torch.tensor(cfg["initiator"], dtype=torch.float64).pin_memory()
+        h2d = init.numel() * 8
+
+    def e2e_step():
+        if h2d:
+            init.to(dev, non_blocking=True)
+        step()
+        for off in range(0, out_bytes, chunk):
+            n = min(chunk, out_bytes - off)
+            host[:n].copy_(flat[off:off + n], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    steps = max(1, min(args.steps, 3))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dt = float(t.item())
+    return dict(value=E * steps * world / dt, unit="edges/s", h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=out_bytes, steps=steps,
+                host_buffer=f"pinned {chunk / 2**30:.1f} GiB, output copied through it in "
+                            f"{(out_bytes + chunk - 1) // chunk} chunk(s) per step")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pgen", "reference"], default="pgen")
+    ap.add_argument("--workload", choices=sorted(W.CONFIGS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0,
+                    help="seconds of oracle work for the cpu_baseline sample")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_pgen(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

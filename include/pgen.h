@@ -1,0 +1,164 @@
+/*
+ * pgen -- GB300-native generation of massive scale-free graphs.
+ *
+ * C ABI of the CUDA library libpgen.so (sm_103a). It implements the two
+ * generators of Yoo & Henderson, "Parallel Generation of Massive Scale-Free
+ * Graphs" (arXiv 1003.3684): the parallel Barabasi-Albert method with
+ * two-phase preferential attachment (Sec. 3, PBA method, Fig. 1) and the
+ * Kronecker method (Sec. 3, PK method, Fig. 2; stochastic initiator of the
+ * Kronecker model cited in Sec. 2), plus CSR assembly and batched launch.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
+ *    are host pointers. The caller owns every buffer; the library allocates
+ *    no device memory (scratch comes from the caller's workspace d_ws).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls only enqueue work; none synchronises the stream. Outputs
+ *    written through h_* pointers are computed from the arguments on the
+ *    host before any launch and are valid on return.
+ *  - Arguments are validated on the host before anything is launched; an
+ *    invalid call launches nothing and returns PG_EINVAL (bad value),
+ *    PG_ENOSPC (output capacity too small) or PG_ENOMEM (workspace too
+ *    small). PG_ECUDA reports a failed launch (cudaGetLastError).
+ *  - Vertex ids are written as (src, dst) pairs, interleaved: uint32 pairs
+ *    for PG_ID32, uint64 pairs for PG_ID64. Edge buffers must be 16-byte
+ *    aligned.
+ *  - Every random draw is Philox4x32-10 (Salmon et al., SC'11) with key
+ *    (seed & 0xffffffff, seed >> 32) and a counter that names the draw, so
+ *    the output is a pure function of the arguments.
+ */
+#ifndef PGEN_H
+#define PGEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PG_OK = 0,
+    PG_EINVAL = 1,   /* invalid argument (nothing launched) */
+    PG_ENOSPC = 2,   /* output capacity smaller than the edge count */
+    PG_ECUDA = 3,    /* a CUDA launch or API call failed */
+    PG_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    PG_ENOMEM = 5    /* workspace smaller than the size the library asks for */
+} pg_status;
+
+typedef enum { PG_ID32 = 0, PG_ID64 = 1 } pg_idwidth;
+
+typedef enum { PG_KRON_STOCHASTIC = 0, PG_KRON_DETERMINISTIC = 1 } pg_kron_mode;
+
+/* Human-readable name of a status code (static string). */
+const char* pg_status_string(pg_status s);
+
+/* Number of SMs and library version, for logging. */
+int pg_device_sm_count(void);
+const char* pg_version(void);
+
+/* ------------------------------------------------------------------------
+ * Parallel Barabasi-Albert generator (Sec. 3, PBA method; Fig. 1).
+ *
+ * n              new vertices in total (n % blocks == 0); n_b = n / blocks.
+ * m              edges added per new vertex (>= 1).
+ * blocks         B, the number of vertex blocks (the paper's processors),
+ *                1 <= B <= 1024.
+ * n0             size of each block's seed clique K_{n0} (>= 2).
+ * faction_width  W: blocks form aligned factions of W consecutive blocks
+ *                (B % W == 0); the first W entries of a block's phase-1
+ *                list are its faction's blocks, in order.
+ * inter_frac     f in [0, 1]: per later phase-1 entry, the probability of
+ *                an inter-faction pick (uniform over blocks outside the
+ *                faction); otherwise the entry copies a uniform earlier
+ *                entry (preferential attachment over blocks).
+ * seed           Philox key.
+ *
+ * Phase 1 draws use counter (j_lo, j_hi, p, 1) for entry j of block p;
+ * phase 2 draws use (i_lo, i_hi, q, 2) for local edge i of block q. Block q
+ * builds its R_q requested endpoints by preferential attachment over its
+ * own vertices, the i-th edge standing at source time floor(i*n_b/R_q);
+ * requesters receive slices of that list in ascending block order and
+ * substitute them in entry order.
+ *
+ * Vertex ids: block b owns ids b*(n0+n_b) .. b*(n0+n_b)+n0+n_b-1; the first
+ * n0 are its seed clique. Output: for each block p in order, its
+ * e0 = n0(n0-1)/2 seed edges (lexicographic) then its n_b*m new edges in
+ * entry order (src = the new vertex, dst = the attached vertex).
+ * Edge count = B*(e0 + n_b*m); blocks = 1 is serial BA on ids 0..n0+n-1.
+ *
+ * d_edges/cap_edges  output buffer and its capacity in edges.
+ * n_edges_out        (host, may be NULL) receives the edge count.
+ * d_ws/ws_bytes      device workspace of at least pg_pba_workspace_size()
+ *                    bytes, 256-byte aligned (unused when blocks == 1).
+ * ---------------------------------------------------------------------- */
+uint64_t pg_pba_edge_count(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0);
+size_t pg_pba_workspace_size(uint64_t n, uint32_t m, uint32_t blocks);
+pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t faction_width,
+                  double inter_frac, uint64_t seed, pg_idwidth w, void* d_edges,
+                  uint64_t cap_edges, uint64_t* n_edges_out, void* d_ws, size_t ws_bytes,
+                  void* stream);
+
+/* ------------------------------------------------------------------------
+ * Kronecker generator (Sec. 3, PK method; Fig. 2).
+ *
+ * h_initiator  host, n0*n0 doubles, row-major, all >= 0 with a positive sum.
+ * n0           initiator order: 1 <= n0 <= 16 (stochastic) or 1 <= n0 <= 256
+ *              with at most 8192 nonzero cells (deterministic). The graph
+ *              has n0^k vertices.
+ * k            number of Kronecker levels, 1 <= k <= 64.
+ * mode PG_KRON_STOCHASTIC: n_edges edges, each drawn independently by a
+ *   k-level descent (most significant level first). Cell c of the
+ *   initiator is chosen at a level when the level's 32-bit word w
+ *   satisfies T_{c-1} <= w < T_c, where T_c = round_half_even(2^32 *
+ *   (sum of cells 0..c) / (sum of all cells)), sums taken left to right in
+ *   double. Level l uses word (l mod 4) of the draw with counter
+ *   (e_lo, e_hi, l div 4, 3). Duplicates and self-loops are kept.
+ * mode PG_KRON_DETERMINISTIC: the nonzero cells are the seed graph's e0
+ *   edges (row-major); the output is all e0^k edges of the k-th Kronecker
+ *   power in meta-edge stack order (edge index written in base e0, most
+ *   significant digit = the seed edge chosen at the first expansion).
+ *   n_edges is ignored.
+ * Ids must fit the id width (n0^k <= 2^32 for PG_ID32).
+ * ---------------------------------------------------------------------- */
+uint64_t pg_kron_edge_count(const double* h_initiator, uint32_t n0, uint32_t k,
+                            uint64_t n_edges, pg_kron_mode mode);
+pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
+                        uint64_t seed, pg_kron_mode mode, pg_idwidth w, void* d_edges,
+                        uint64_t cap_edges, uint64_t* n_edges_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * CSR assembly (not in the paper; the usual input format of the graph
+ * algorithms the generated graphs feed).
+ *
+ * d_edges      n_edges (src, dst) pairs of width w; every src and every dst
+ *              is < n_vertices (rows are sorted on the bits of that range).
+ * d_row_ptr    n_vertices + 1 uint64: row_ptr[v] = #edges with src < v.
+ * d_col        n_edges ids of width w: the destinations grouped by source,
+ *              ascending within each row (duplicates kept). The result does
+ *              not depend on scheduling.
+ * d_ws         workspace of pg_csr_workspace_size() bytes, 256-byte aligned.
+ * An id >= n_vertices is not checked on the device; it is the caller's
+ * contract (the generators above always satisfy it).
+ * ---------------------------------------------------------------------- */
+size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices);
+pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices,
+                       pg_idwidth w, uint64_t* d_row_ptr, void* d_col, void* d_ws,
+                       size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Kernel timing trace (profiling aid, not part of the method).
+ * pg_trace_enable(1): from then on every kernel the library launches is
+ * bracketed by two CUDA events recorded on the launch's stream.
+ * pg_trace_dump(buf, len): waits for the recorded events, writes a JSON object
+ * {"kernel_name": [launches, total_ms], ...} into buf (NUL-terminated,
+ * truncated to len), clears the record and returns the bytes needed.
+ * ---------------------------------------------------------------------- */
+void pg_trace_enable(int on);
+size_t pg_trace_dump(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGEN_H */

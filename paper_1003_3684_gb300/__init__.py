@@ -1,0 +1,238 @@
+"""pgen: GB300-native generation of massive scale-free graphs (arXiv 1003.3684).
+
+Thin Python binding over the C ABI of ``libpgen.so`` (declared in
+``include/pgen.h``). Each function here carries the C entry point's name and
+only marshals arguments: torch supplies the device buffers and the current
+CUDA stream, and every step of generation runs in the library's sm_103a
+kernels. There is no CPU fallback: if the library is missing the first call
+raises.
+
+    import paper_1003_3684_gb300 as pgen
+    edges = pgen.gen_pba(n=2**20, m=5, blocks=64, n0=6, faction_width=1,
+                         inter_frac=0.1, seed=3)            # (E, 2) int32 view
+    row_ptr, col = pgen.edges_to_csr(edges, n_vertices=...)
+
+Edge tensors hold unsigned ids in signed containers (int32 for 32-bit ids,
+int64 for 64-bit ids); ``.view(torch.uint32)`` or numpy ``.view(np.uint32)``
+recovers the unsigned values.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+__all__ = [
+    "PG_OK", "PG_EINVAL", "PG_ENOSPC", "PG_ECUDA", "PG_ETIMEOUT", "PG_ENOMEM",
+    "PgenError", "lib", "library_path",
+    "pg_status_string", "pg_device_sm_count", "pg_version",
+    "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba",
+    "pg_kron_edge_count", "gen_kronecker",
+    "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
+]
+
+PG_OK, PG_EINVAL, PG_ENOSPC, PG_ECUDA, PG_ETIMEOUT, PG_ENOMEM = range(6)
+PG_ID32, PG_ID64 = 0, 1
+PG_KRON_STOCHASTIC, PG_KRON_DETERMINISTIC = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libpgen.so")
+_lock = threading.Lock()
+_lib = None
+
+u32, u64, i32, dbl, vp = C.c_uint32, C.c_uint64, C.c_int, C.c_double, C.c_void_p
+sz = C.c_size_t
+
+
+class PgenError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn}: {pg_status_string(status)} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libpgen.so (built by ``paper_1003_3684_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"{_LIB_PATH} is missing: build it with "
+                    "`python -m paper_1003_3684_gb300.build` (nvcc, sm_103a). "
+                    "pgen has no CPU fallback.")
+            L = C.CDLL(_LIB_PATH)
+            L.pg_status_string.argtypes = [i32]
+            L.pg_status_string.restype = C.c_char_p
+            L.pg_device_sm_count.argtypes = []
+            L.pg_device_sm_count.restype = i32
+            L.pg_version.argtypes = []
+            L.pg_version.restype = C.c_char_p
+            L.pg_pba_edge_count.argtypes = [u64, u32, u32, u32]
+            L.pg_pba_edge_count.restype = u64
+            L.pg_pba_workspace_size.argtypes = [u64, u32, u32]
+            L.pg_pba_workspace_size.restype = sz
+            L.gen_pba.argtypes = [u64, u32, u32, u32, u32, dbl, u64, i32, vp, u64,
+                                  C.POINTER(u64), vp, sz, vp]
+            L.gen_pba.restype = i32
+            L.pg_kron_edge_count.argtypes = [vp, u32, u32, u64, i32]
+            L.pg_kron_edge_count.restype = u64
+            L.gen_kronecker.argtypes = [vp, u32, u32, u64, u64, i32, i32, vp, u64,
+                                        C.POINTER(u64), vp]
+            L.gen_kronecker.restype = i32
+            L.pg_csr_workspace_size.argtypes = [u64, u64]
+            L.pg_csr_workspace_size.restype = sz
+            L.edges_to_csr.argtypes = [vp, u64, u64, i32, vp, vp, vp, sz, vp]
+            L.edges_to_csr.restype = i32
+            L.pg_trace_enable.argtypes = [i32]
+            L.pg_trace_enable.restype = None
+            L.pg_trace_dump.argtypes = [C.c_char_p, sz]
+            L.pg_trace_dump.restype = sz
+            _lib = L
+    return _lib
+
+
+def _check(fn: str, st: int):
+    if st != PG_OK:
+        raise PgenError(fn, st)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return vp(t.data_ptr()) if t is not None and t.numel() > 0 else vp(None)
+
+
+def _empty(nbytes_or_shape, dtype, device):
+    import torch
+    return torch.empty(nbytes_or_shape, dtype=dtype, device=device)
+
+
+# --------------------------------------------------------------------------
+def pg_status_string(status: int) -> str:
+    try:
+        return lib().pg_status_string(status).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def pg_device_sm_count() -> int:
+    return int(lib().pg_device_sm_count())
+
+
+def pg_version() -> str:
+    return lib().pg_version().decode()
+
+
+def pg_pba_edge_count(n: int, m: int, blocks: int, n0: int) -> int:
+    return int(lib().pg_pba_edge_count(n, m, blocks, n0))
+
+
+def pg_pba_workspace_size(n: int, m: int, blocks: int) -> int:
+    return int(lib().pg_pba_workspace_size(n, m, blocks))
+
+
+def gen_pba(n: int, m: int, blocks: int = 1, n0: int | None = None, faction_width: int = 1,
+            inter_frac: float = 0.1, seed: int = 0, id64: bool = False, out=None,
+            workspace=None, stream=None, device="cuda"):
+    """Two-phase PBA graph (Sec. 3, PBA method); returns an (E, 2) edge tensor.
+
+    ``n0`` defaults to m + 1. ``out`` (optional) is a preallocated 16-byte
+    aligned int32/int64 tensor with at least E rows; ``workspace`` a uint8
+    device tensor of at least ``pg_pba_workspace_size`` bytes (allocated here
+    when omitted and blocks > 1).
+    """
+    import torch
+    n0 = m + 1 if n0 is None else n0
+    E = pg_pba_edge_count(n, m, blocks, n0)
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(E, 1), 2), dtype, device)
+    if blocks > 1 and workspace is None:
+        workspace = _empty(max(pg_pba_workspace_size(n, m, blocks), 1), torch.uint8,
+                           out.device)
+    ws_bytes = workspace.numel() if workspace is not None else 0
+    n_out = u64(0)
+    st = lib().gen_pba(n, m, blocks, n0, faction_width, float(inter_frac), seed,
+                       PG_ID64 if id64 else PG_ID32, _ptr(out), out.shape[0], C.byref(n_out),
+                       _ptr(workspace), ws_bytes, _stream(stream))
+    _check("gen_pba", st)
+    return out[:n_out.value]
+
+
+def _initiator(initiator):
+    import numpy as np
+    P = np.ascontiguousarray(np.asarray(initiator, dtype=np.float64))
+    if P.ndim != 2 or P.shape[0] != P.shape[1]:
+        raise ValueError("initiator must be a square matrix")
+    return P
+
+
+def pg_kron_edge_count(initiator, k: int, n_edges: int, deterministic: bool = False) -> int:
+    P = _initiator(initiator)
+    return int(lib().pg_kron_edge_count(P.ctypes.data_as(vp), P.shape[0], k, n_edges,
+                                        PG_KRON_DETERMINISTIC if deterministic
+                                        else PG_KRON_STOCHASTIC))
+
+
+def gen_kronecker(initiator, k: int, n_edges: int = 0, seed: int = 0, deterministic: bool = False,
+                  id64: bool = False, out=None, stream=None, device="cuda"):
+    """Kronecker graph (Sec. 3, PK method); returns an (E, 2) edge tensor."""
+    import torch
+    P = _initiator(initiator)
+    E = pg_kron_edge_count(P, k, n_edges, deterministic)
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(E, 1), 2), dtype, device)
+    n_out = u64(0)
+    st = lib().gen_kronecker(P.ctypes.data_as(vp), P.shape[0], k, n_edges, seed,
+                             PG_KRON_DETERMINISTIC if deterministic else PG_KRON_STOCHASTIC,
+                             PG_ID64 if id64 else PG_ID32, _ptr(out), out.shape[0],
+                             C.byref(n_out), _stream(stream))
+    _check("gen_kronecker", st)
+    return out[:n_out.value]
+
+
+def pg_csr_workspace_size(n_edges: int, n_vertices: int) -> int:
+    return int(lib().pg_csr_workspace_size(n_edges, n_vertices))
+
+
+def edges_to_csr(edges, n_vertices: int, row_ptr=None, col=None, workspace=None, stream=None):
+    """CSR of an (E, 2) edge tensor: (row_ptr int64[N+1], col[E]) with rows sorted."""
+    import torch
+    id64 = edges.dtype == torch.int64
+    E = edges.shape[0]
+    if row_ptr is None:
+        row_ptr = _empty(n_vertices + 1, torch.int64, edges.device)
+    if col is None:
+        col = _empty(max(E, 1), edges.dtype, edges.device)
+    if workspace is None:
+        workspace = _empty(max(pg_csr_workspace_size(E, n_vertices), 1), torch.uint8,
+                           edges.device)
+    st = lib().edges_to_csr(_ptr(edges), E, n_vertices, PG_ID64 if id64 else PG_ID32,
+                            _ptr(row_ptr), _ptr(col), _ptr(workspace), workspace.numel(),
+                            _stream(stream))
+    _check("edges_to_csr", st)
+    return row_ptr, col[:E]
+
+
+def pg_trace_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events (see pgen.h)."""
+    lib().pg_trace_enable(1 if on else 0)
+
+
+def pg_trace_dump() -> dict:
+    """Per-kernel {name: (launches, total_ms)} since the last dump; clears it."""
+    import json
+    need = lib().pg_trace_dump(None, 0)
+    buf = C.create_string_buffer(need + 64)
+    lib().pg_trace_dump(buf, len(buf))
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}

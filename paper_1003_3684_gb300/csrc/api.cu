@@ -1,0 +1,274 @@
+// C ABI of libpgen (declared in include/pgen.h): argument validation, host
+// set-up (thresholds, divisors, geometry) and dispatch to the kernels.
+// Every check happens before the first launch, so an invalid call leaves the
+// device untouched.
+#include <cmath>
+#include <cstring>
+
+#include "../../include/pgen.h"
+#include "pg_internal.h"
+
+namespace pgen {
+
+int device_sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace pgen
+
+using namespace pgen;
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+pg_status from_cuda(cudaError_t e) { return e == cudaSuccess ? PG_OK : PG_ECUDA; }
+
+uint64_t seed_edges(uint32_t n0) { return (uint64_t)n0 * (n0 - 1) / 2; }
+
+// Inter-faction coin threshold min(2^32 - 1, round_half_even(f * 2^32)).
+uint32_t coin_threshold(double f)
+{
+    const double t = std::nearbyint(std::ldexp(f, 32));
+    if (!(t > 0.0)) return 0;
+    if (t >= 4294967295.0) return 0xFFFFFFFFu;
+    return (uint32_t)t;
+}
+
+struct PbaCheck {
+    pg_status st;
+    uint64_t n_b, N_e, edges;
+};
+
+PbaCheck check_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, double f,
+                   pg_idwidth w)
+{
+    PbaCheck c{PG_EINVAL, 0, 0, 0};
+    if (m < 1 || n0 < 2 || n0 > 65536 || B < 1 || B > 1024 || W < 1 || B % W != 0) return c;
+    if (n % B != 0) return c;
+    if (!(f >= 0.0 && f <= 1.0)) return c;
+    if (w != PG_ID32 && w != PG_ID64) return c;
+    const uint64_t n_b = n / B;
+    const u128 N_e = (u128)n_b * m;
+    const u128 e0 = seed_edges(n0);
+    const u128 edges = (u128)B * (e0 + N_e);
+    if (edges >> 62) return c;
+    const u128 ids = (u128)B * (n0 + (u128)n_b);
+    if (w == PG_ID32 && ids > ((u128)1 << 32)) return c;
+    if ((u128)n0 + n_b >= ((u128)1 << 32)) return c;       // local ids are 32-bit
+    // phase-2 index arithmetic: (total entries) * n_b must stay below 2^63
+    if ((u128)B * N_e * (n_b ? n_b : 1) >= ((u128)1 << 63)) return c;
+    c.st = PG_OK;
+    c.n_b = n_b;
+    c.N_e = (uint64_t)N_e;
+    c.edges = (uint64_t)edges;
+    return c;
+}
+
+PbaGeom make_geom(uint64_t n_b, uint64_t N_e, uint32_t m, uint32_t B, uint32_t n0, uint32_t W,
+                  double f, uint64_t seed)
+{
+    PbaGeom g;
+    std::memset(&g, 0, sizeof(g));
+    g.n_b = n_b;
+    g.N_e = N_e;
+    g.e0 = seed_edges(n0);
+    g.span = n0 + n_b;
+    g.A_stride = (N_e + 7) & ~(uint64_t)7;
+    g.m = m;
+    g.B = B;
+    g.W = W;
+    g.n0 = n0;
+    g.coin_thr = coin_threshold(f);
+    g.coin_on = (B > W && g.coin_thr > 0) ? 1 : 0;
+    g.key.k0 = (uint32_t)seed;
+    g.key.k1 = (uint32_t)(seed >> 32);
+    g.S = pba_segments(N_e, B, device_sm_count());
+    g.seg_len = pba_segment_length(N_e, g.S);
+    g.P = (uint32_t)(N_e < 65536 ? N_e : 65536);
+    g.div_m = make_fastdiv(m);
+    g.div_nb = make_fastdiv(n_b > 0 ? n_b : 1);
+    return g;
+}
+
+// Kronecker thresholds T_c, c < n0^2 - 1 (left-to-right double sums).
+bool kron_thresholds(const double* P, uint32_t n0, uint64_t* T)
+{
+    const uint32_t cells = n0 * n0;
+    double S = 0.0;
+    for (uint32_t c = 0; c < cells; ++c) {
+        if (!(P[c] >= 0.0) || !std::isfinite(P[c])) return false;
+        S += P[c];
+    }
+    if (!(S > 0.0) || !std::isfinite(S)) return false;
+    double cum = 0.0;
+    for (uint32_t c = 0; c + 1 < cells; ++c) {
+        cum += P[c];
+        T[c] = (uint64_t)std::nearbyint(std::ldexp(cum / S, 32));
+    }
+    return true;
+}
+
+// n0^k as a 128-bit value (saturating at 2^127).
+u128 ipow(uint64_t b, uint32_t k)
+{
+    u128 r = 1;
+    for (uint32_t i = 0; i < k; ++i) {
+        if (r > ((u128)1 << 100)) return (u128)1 << 127;
+        r *= b;
+    }
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pg_status_string(pg_status s)
+{
+    switch (s) {
+    case PG_OK: return "ok";
+    case PG_EINVAL: return "invalid argument";
+    case PG_ENOSPC: return "output capacity too small";
+    case PG_ECUDA: return "CUDA error";
+    case PG_ETIMEOUT: return "device wait timed out";
+    case PG_ENOMEM: return "workspace too small";
+    }
+    return "unknown status";
+}
+
+int pg_device_sm_count(void) { return device_sm_count(); }
+
+const char* pg_version(void) { return "pgen 0.1 (sm_103a)"; }
+
+uint64_t pg_pba_edge_count(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0)
+{
+    const PbaCheck c = check_pba(n, m, blocks, n0, blocks ? blocks : 1, 0.0, PG_ID64);
+    return c.st == PG_OK ? c.edges : 0;
+}
+
+size_t pg_pba_workspace_size(uint64_t n, uint32_t m, uint32_t blocks)
+{
+    if (blocks <= 1) return 0;
+    const PbaCheck c = check_pba(n, m, blocks, 2, blocks, 0.0, PG_ID64);
+    if (c.st != PG_OK) return 0;
+    const uint32_t S = pba_segments(c.N_e, blocks, device_sm_count());
+    return pba_workspace_layout((c.N_e + 7) & ~(uint64_t)7, blocks, S).total;
+}
+
+pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t faction_width,
+                  double inter_frac, uint64_t seed, pg_idwidth w, void* d_edges,
+                  uint64_t cap_edges, uint64_t* n_edges_out, void* d_ws, size_t ws_bytes,
+                  void* stream)
+{
+    const PbaCheck c = check_pba(n, m, blocks, n0, faction_width, inter_frac, w);
+    if (c.st != PG_OK) return c.st;
+    if (n_edges_out) *n_edges_out = c.edges;
+    if (cap_edges < c.edges) return PG_ENOSPC;
+    if (c.edges > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+    const PbaGeom g = make_geom(c.n_b, c.N_e, m, blocks, n0, faction_width, inter_frac, seed);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (blocks == 1) return from_cuda(launch_ba(g, w == PG_ID64, d_edges, s));
+    const size_t need = pba_workspace_layout(g.A_stride, blocks, g.S).total;
+    if (!d_ws || ws_bytes < need) return PG_ENOMEM;
+    if (!aligned(d_ws, 256)) return PG_EINVAL;
+    return from_cuda(launch_pba(g, w == PG_ID64, d_edges, d_ws, s));
+}
+
+uint64_t pg_kron_edge_count(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
+                            pg_kron_mode mode)
+{
+    if (mode == PG_KRON_STOCHASTIC) return n_edges;
+    if (!h_initiator || n0 < 1 || n0 > 256 || k < 1) return 0;
+    uint64_t e0 = 0;
+    for (uint32_t c = 0; c < n0 * n0; ++c) e0 += h_initiator[c] > 0.0;
+    const u128 total = ipow(e0, k);
+    return (total >> 63) ? 0 : (uint64_t)total;
+}
+
+pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
+                        uint64_t seed, pg_kron_mode mode, pg_idwidth w, void* d_edges,
+                        uint64_t cap_edges, uint64_t* n_edges_out, void* stream)
+{
+    if (!h_initiator || k < 1 || k > 64 || (w != PG_ID32 && w != PG_ID64)) return PG_EINVAL;
+    if (mode != PG_KRON_STOCHASTIC && mode != PG_KRON_DETERMINISTIC) return PG_EINVAL;
+    const uint32_t max_n0 = mode == PG_KRON_STOCHASTIC ? 16 : 256;
+    if (n0 < 1 || n0 > max_n0) return PG_EINVAL;
+    const u128 n_vertices = ipow(n0, k);
+    const u128 id_limit = (w == PG_ID32) ? ((u128)1 << 32) : ((u128)1 << 64);
+    if (n_vertices > id_limit) return PG_EINVAL;
+    const uint32_t cells = n0 * n0;
+    for (uint32_t c = 0; c < cells; ++c)
+        if (!(h_initiator[c] >= 0.0) || !std::isfinite(h_initiator[c])) return PG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    if (mode == PG_KRON_STOCHASTIC) {
+        uint64_t T[kMaxKronThr];
+        KronParams p;
+        std::memset(&p, 0, sizeof(p));
+        if (!kron_thresholds(h_initiator, n0, T)) return PG_EINVAL;
+        p.n0 = n0;
+        p.k = k;
+        p.key.k0 = (uint32_t)seed;
+        p.key.k1 = (uint32_t)(seed >> 32);
+        for (int t = 0; t < kMaxKronThr; ++t) p.u[t] = 0xFFFFFFFFu;
+        uint32_t c = 0;
+        while (c + 1 < cells && T[c] == 0) ++c;
+        p.n_zero = c;
+        for (; c + 1 < cells && T[c] < ((uint64_t)1 << 32); ++c) p.u[p.n_u++] = (uint32_t)(T[c] - 1);
+        if (n_edges_out) *n_edges_out = n_edges;
+        if (cap_edges < n_edges) return PG_ENOSPC;
+        if (n_edges > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+        return from_cuda(launch_kron_stochastic(p, w == PG_ID64, d_edges, 0, n_edges, s));
+    }
+
+    KronDetParams p;
+    std::memset(&p, 0, sizeof(p));
+    uint32_t e0 = 0;
+    for (uint32_t c = 0; c < cells; ++c) {
+        if (h_initiator[c] > 0.0) {
+            if (e0 >= (uint32_t)kMaxDetSeedEdges) return PG_EINVAL;
+            p.ab[e0++] = (uint16_t)((c / n0) | ((c % n0) << 8));
+        }
+    }
+    if (e0 == 0) return PG_EINVAL;
+    const u128 total = ipow(e0, k);
+    if (total >> 62) return PG_EINVAL;
+    p.n0 = n0;
+    p.k = k;
+    p.e0 = e0;
+    p.div_e0 = make_fastdiv(e0);
+    if (n_edges_out) *n_edges_out = (uint64_t)total;
+    if (cap_edges < (uint64_t)total) return PG_ENOSPC;
+    if (!d_edges || !aligned(d_edges, 16)) return PG_EINVAL;
+    return from_cuda(launch_kron_det(p, w == PG_ID64, d_edges, (uint64_t)total, s));
+}
+
+size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices)
+{
+    return csr_workspace_bytes(n_edges, n_vertices);
+}
+
+pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                       uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,
+                       void* stream)
+{
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (n_edges > 0 && n_vertices == 0) return PG_EINVAL;
+    if (!d_row_ptr || !aligned(d_row_ptr, 8)) return PG_EINVAL;
+    if (n_edges > 0 && (!d_edges || !d_col || !aligned(d_edges, 16))) return PG_EINVAL;
+    if (w == PG_ID32 && n_vertices > ((uint64_t)1 << 32)) return PG_EINVAL;
+    const size_t need = csr_workspace_bytes(n_edges, n_vertices);
+    if (ws_bytes < need || (need > 0 && !d_ws)) return PG_ENOMEM;
+    if (d_ws && !aligned(d_ws, 256)) return PG_EINVAL;
+    return from_cuda(launch_csr(d_edges, n_edges, n_vertices, w == PG_ID64, d_row_ptr, d_col, d_ws,
+                                ws_bytes, (cudaStream_t)stream));
+}
+
+}  // extern "C"

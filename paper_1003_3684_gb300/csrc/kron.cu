@@ -1,0 +1,255 @@
+// Kronecker graph kernels (arXiv 1003.3684, Sec. 3, PK method).
+//
+// Stochastic mode: every edge is independent -- one thread derives an edge
+// from its index alone by a k-level descent through the initiator (the
+// stochastic Kronecker model of Leskovec et al. that Sec. 2 cites), most
+// significant level first. Level l consumes word (l mod 4) of the Philox
+// block for counter (e_lo, e_hi, l div 4, 3), so ceil(k/4) Philox calls
+// give all k levels. A level picks cell c when T_{c-1} <= w < T_c with
+// 32-bit fixed-point thresholds T prepared on the host.
+//
+// Deterministic mode: the stack expansion of Sec. 3 visits meta-edges
+// depth first with children in seed order, so the e-th emitted edge is the
+// one whose base-e0 digits (most significant first) name the seed edge taken
+// at each expansion. Each thread decodes its own edge index; the order is
+// the stack's without running a stack.
+//
+// Both kernels are integer-ALU bound (Philox and digit arithmetic) and
+// write their output once, as coalesced 16-byte vector stores of two edges.
+#include "pg_internal.h"
+#include "pg_trace.h"
+
+namespace pgen {
+namespace {
+
+template <typename Id>
+struct Pair2;
+template <>
+struct Pair2<uint32_t> {
+    __device__ static void store(uint32_t* out, uint64_t e, uint64_t r0, uint64_t c0,
+                                 uint64_t r1, uint64_t c1)
+    {
+        *reinterpret_cast<uint4*>(out + 2 * e) =
+            make_uint4((uint32_t)r0, (uint32_t)c0, (uint32_t)r1, (uint32_t)c1);
+    }
+    __device__ static void store1(uint32_t* out, uint64_t e, uint64_t r0, uint64_t c0)
+    {
+        *reinterpret_cast<uint2*>(out + 2 * e) = make_uint2((uint32_t)r0, (uint32_t)c0);
+    }
+};
+template <>
+struct Pair2<uint64_t> {
+    __device__ static void store(uint64_t* out, uint64_t e, uint64_t r0, uint64_t c0,
+                                 uint64_t r1, uint64_t c1)
+    {
+        ulonglong2* o = reinterpret_cast<ulonglong2*>(out + 2 * e);
+        o[0] = make_ulonglong2(r0, c0);
+        o[1] = make_ulonglong2(r1, c1);
+    }
+    __device__ static void store1(uint64_t* out, uint64_t e, uint64_t r0, uint64_t c0)
+    {
+        *reinterpret_cast<ulonglong2*>(out + 2 * e) = make_ulonglong2(r0, c0);
+    }
+};
+
+// ---- stochastic descent, initiator order 2 (branch-free 3-threshold pick) --
+__device__ __forceinline__ void descend2(uint32_t w, uint32_t u0, uint32_t u1, uint32_t u2,
+                                         uint32_t base, uint64_t& row, uint64_t& col)
+{
+    const uint32_t cell = base + (w > u0) + (w > u1) + (w > u2);
+    row = (row << 1) | (cell >> 1);
+    col = (col << 1) | (cell & 1);
+}
+
+__device__ __forceinline__ void kron2_edge(const KronParams& p, uint64_t e, uint32_t u0,
+                                           uint32_t u1, uint32_t u2, uint64_t& row, uint64_t& col)
+{
+    row = 0;
+    col = 0;
+    const uint32_t k = p.k;
+    uint32_t l = 0;
+    for (uint32_t g = 0; l + 4 <= k; ++g, l += 4) {
+        const uint4 w = draw(e, g, 3, p.key);
+        descend2(w.x, u0, u1, u2, p.n_zero, row, col);
+        descend2(w.y, u0, u1, u2, p.n_zero, row, col);
+        descend2(w.z, u0, u1, u2, p.n_zero, row, col);
+        descend2(w.w, u0, u1, u2, p.n_zero, row, col);
+    }
+    if (l < k) {
+        const uint4 w = draw(e, l >> 2, 3, p.key);
+        descend2(w.x, u0, u1, u2, p.n_zero, row, col);
+        if (l + 1 < k) descend2(w.y, u0, u1, u2, p.n_zero, row, col);
+        if (l + 2 < k) descend2(w.z, u0, u1, u2, p.n_zero, row, col);
+    }
+}
+
+template <typename Id>
+__global__ void __launch_bounds__(256) kron2_kernel(const __grid_constant__ KronParams p,
+                                                    Id* __restrict__ out, uint64_t e_begin,
+                                                    uint64_t n_edges)
+{
+    const uint32_t u0 = p.u[0], u1 = p.u[1], u2 = p.u[2];   // padded to three
+    const uint64_t n_pairs = (n_edges + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
+        const uint64_t e = 2 * t;
+        uint64_t r0, c0;
+        kron2_edge(p, e_begin + e, u0, u1, u2, r0, c0);
+        if (e + 1 < n_edges) {
+            uint64_t r1, c1;
+            kron2_edge(p, e_begin + e + 1, u0, u1, u2, r1, c1);
+            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        } else {
+            Pair2<Id>::store1(out, e, r0, c0);
+        }
+    }
+}
+
+// ---- stochastic descent, any order n0 <= 16 (binary search in smem) -------
+__device__ __forceinline__ void kron_edge_generic(const KronParams& p, const uint32_t* u,
+                                                  uint32_t n_u, uint64_t e, uint64_t& row,
+                                                  uint64_t& col)
+{
+    row = 0;
+    col = 0;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (uint32_t l = 0; l < p.k; ++l) {
+        if ((l & 3) == 0) w = draw(e, l >> 2, 3, p.key);
+        const uint32_t x = (l & 3) == 0 ? w.x : (l & 3) == 1 ? w.y : (l & 3) == 2 ? w.z : w.w;
+        // count of u[t] < x (u ascending): first index with u[t] >= x
+        uint32_t lo = 0, hi = n_u;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (u[mid] < x) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint32_t cell = p.n_zero + lo;
+        row = row * p.n0 + cell / p.n0;
+        col = col * p.n0 + cell % p.n0;
+    }
+}
+
+template <typename Id>
+__global__ void __launch_bounds__(256) kron_generic_kernel(const __grid_constant__ KronParams p,
+                                                           Id* __restrict__ out, uint64_t e_begin,
+                                                           uint64_t n_edges)
+{
+    __shared__ uint32_t u[kMaxKronThr];
+    const uint32_t n_u = p.n_u;
+    for (uint32_t t = threadIdx.x; t < n_u; t += blockDim.x) u[t] = p.u[t];
+    __syncthreads();
+    const uint64_t n_pairs = (n_edges + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
+        const uint64_t e = 2 * t;
+        uint64_t r0, c0;
+        kron_edge_generic(p, u, n_u, e_begin + e, r0, c0);
+        if (e + 1 < n_edges) {
+            uint64_t r1, c1;
+            kron_edge_generic(p, u, n_u, e_begin + e + 1, r1, c1);
+            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        } else {
+            Pair2<Id>::store1(out, e, r0, c0);
+        }
+    }
+}
+
+// ---- deterministic expansion: base-e0 digits of the edge index ------------
+__device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint16_t* ab,
+                                              uint64_t e, uint64_t& row, uint64_t& col)
+{
+    row = 0;
+    col = 0;
+    uint64_t mul = 1;
+    for (uint32_t l = 0; l < p.k; ++l) {   // least significant digit first
+        const uint64_t q = fdiv(e, p.div_e0);
+        const uint32_t d = (uint32_t)(e - q * p.e0);
+        e = q;
+        const uint32_t v = ab[d];
+        row += (v & 0xFFu) * mul;
+        col += (v >> 8) * mul;
+        mul *= p.n0;
+    }
+}
+
+template <typename Id>
+__global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ KronDetParams p,
+                                                       Id* __restrict__ out, uint64_t n_edges)
+{
+    __shared__ uint16_t ab[kMaxDetSeedEdges];
+    for (uint32_t t = threadIdx.x; t < p.e0; t += blockDim.x) ab[t] = p.ab[t];
+    __syncthreads();
+    const uint64_t n_pairs = (n_edges + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
+        const uint64_t e = 2 * t;
+        uint64_t r0, c0;
+        kron_det_edge(p, ab, e, r0, c0);
+        if (e + 1 < n_edges) {
+            uint64_t r1, c1;
+            kron_det_edge(p, ab, e + 1, r1, c1);
+            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        } else {
+            Pair2<Id>::store1(out, e, r0, c0);
+        }
+    }
+}
+
+template <typename K>
+int grid_for(K kernel, uint64_t work_items, int threads)
+{
+    static int sms = device_sm_count();
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const uint64_t full = (uint64_t)sms * per_sm;
+    const uint64_t need = (work_items + threads - 1) / threads;
+    return (int)(need < full ? (need > 0 ? need : 1) : full);
+}
+
+}  // namespace
+
+cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, uint64_t e_begin,
+                                   uint64_t n_edges, cudaStream_t s)
+{
+    if (n_edges == 0) return cudaSuccess;
+    const uint64_t pairs = (n_edges + 1) / 2;
+    TraceScope trace(p.n0 == 2 ? "kron_descent_n0_2" : "kron_descent", s);
+    if (p.n0 == 2) {
+        if (id64) {
+            auto k = kron2_kernel<uint64_t>;
+            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+        } else {
+            auto k = kron2_kernel<uint32_t>;
+            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
+        }
+    } else {
+        if (id64) {
+            auto k = kron_generic_kernel<uint64_t>;
+            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+        } else {
+            auto k = kron_generic_kernel<uint32_t>;
+            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t n_edges,
+                            cudaStream_t s)
+{
+    if (n_edges == 0) return cudaSuccess;
+    const uint64_t pairs = (n_edges + 1) / 2;
+    TraceScope trace("kron_det", s);
+    if (id64) {
+        auto k = kron_det_kernel<uint64_t>;
+        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, n_edges);
+    } else {
+        auto k = kron_det_kernel<uint32_t>;
+        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, n_edges);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pgen

@@ -1,0 +1,112 @@
+// Device-side primitives shared by the generator kernels: the Philox4x32-10
+// counter RNG, 64-bit uniform draws and division by run-time invariant
+// divisors. Everything here is integer arithmetic; nothing depends on the
+// launch schedule.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pgen {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each
+// multiplying words 0 and 2 by the Philox constants (32x32 -> 64), XORing
+// the high halves into the other two words together with the round key;
+// the key advances by the Weyl constants between rounds. The key is uniform
+// across a launch, so its schedule lives in uniform registers.
+struct Key {
+    uint32_t k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox(uint4 c, Key key)
+{
+    uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t idx, uint32_t stream, uint32_t tag, Key key)
+{
+    return philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), stream, tag), key);
+}
+
+// Uniform integer in [0, R): high 64 bits of ((w1 << 32) | w0) * R.
+__device__ __forceinline__ uint64_t uniform64(uint32_t w0, uint32_t w1, uint64_t R)
+{
+    return __umul64hi(((uint64_t)w1 << 32) | w0, R);
+}
+
+// floor(n / d) for every 64-bit n with a precomputed multiplier
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Sec. 4: t = mulhi(mul, n),
+// q = (t + ((n - t) >> s1)) >> s2 with l = ceil(log2 d),
+// mul = floor(2^64 (2^l - d) / d) + 1, s1 = min(l, 1), s2 = max(l - 1, 0)).
+struct FastDiv {
+    uint64_t mul;
+    uint32_t s1, s2;
+};
+
+__host__ __device__ __forceinline__ uint64_t fdiv(uint64_t n, const FastDiv& f)
+{
+#ifdef __CUDA_ARCH__
+    const uint64_t t = __umul64hi(f.mul, n);
+#else
+    const uint64_t t = (uint64_t)(((unsigned __int128)f.mul * n) >> 64);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// Builds the multiplier for divisor d >= 1 (host or device; the device path
+// uses a bitwise long division and is meant for per-launch set-up only).
+__host__ __device__ inline FastDiv make_fastdiv(uint64_t d)
+{
+    uint32_t l = 0;
+    while (l < 64 && ((uint64_t)1 << l) < d) ++l;   // l = ceil(log2 d)
+    FastDiv f;
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 0 ? l - 1 : 0;
+    // numerator 2^64 * (2^l - d), a 128-bit value (hi, lo) with lo = 0
+    const uint64_t hi = (l == 64) ? (uint64_t)(0 - d) : (((uint64_t)1 << l) - d);
+#ifdef __CUDA_ARCH__
+    // restoring long division of (hi:0) by d; hi < d so the quotient fits
+    uint64_t rem = hi, quo = 0;
+    for (int b = 63; b >= 0; --b) {
+        const uint64_t top = rem >> 63;
+        rem <<= 1;
+        quo <<= 1;
+        if (top || rem >= d) {
+            rem -= d;
+            quo |= 1;
+        }
+    }
+    f.mul = quo + 1;
+#else
+    const unsigned __int128 num = (unsigned __int128)hi << 64;
+    f.mul = (uint64_t)(num / d) + 1;
+#endif
+    return f;
+}
+
+// Endpoint `side` (0 = smaller id) of seed-clique edge e, the edges of
+// K_{n0} being listed in lexicographic order (a, b), a < b.
+__device__ __forceinline__ uint32_t seed_endpoint(uint64_t e, uint32_t side, uint32_t n0)
+{
+    uint32_t a = 0;
+    uint64_t row = n0 - 1;
+    while (e >= row) {
+        e -= row;
+        ++a;
+        --row;
+    }
+    return side ? a + 1 + (uint32_t)e : a;
+}
+
+}  // namespace pgen

@@ -1,0 +1,73 @@
+// Internal launch interface between the C ABI (api.cu) and the kernel
+// translation units. Host-only declarations; every launcher enqueues work on
+// `stream` and returns the cudaGetLastError() of its launches.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pg_common.cuh"
+
+namespace pgen {
+
+constexpr int kMaxKronThr = 255;   // n0 <= 16 -> at most 255 thresholds
+
+// Stochastic Kronecker descent parameters. With thresholds T_c (c < n0^2-1),
+// a word w passes T_c when w >= T_c. Thresholds equal to 0 are always passed
+// (n_zero of them, at the front); the next n_u are stored as u = T_c - 1 so
+// that the test is w > u in 32 bits; thresholds equal to 2^32 are never
+// passed and are dropped. u[] is ascending and padded with 0xffffffff.
+struct KronParams {
+    uint32_t n0, k, n_zero, n_u;
+    Key key;
+    uint32_t u[kMaxKronThr];
+};
+
+// Deterministic Kronecker: seed edges (row-major; a in the low byte, b in
+// the high byte, so n0 <= 256) and the divisor for base-e0 digits.
+constexpr int kMaxDetSeedEdges = 8192;
+struct KronDetParams {
+    uint32_t n0, k, e0, pad;
+    FastDiv div_e0;
+    uint16_t ab[kMaxDetSeedEdges];
+};
+
+cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, uint64_t e_begin,
+                                   uint64_t n_edges, cudaStream_t s);
+cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t n_edges,
+                            cudaStream_t s);
+
+// PBA (two-phase preferential attachment) geometry.
+struct PbaGeom {
+    uint64_t n_b, N_e, e0, span;   // span = n0 + n_b (ids per block)
+    uint64_t A_stride;             // entries between rows of A (N_e rounded up to 8)
+    uint32_t m, B, W, n0;
+    uint32_t coin_on, coin_thr;    // inter-faction coin: w2 < coin_thr
+    Key key;
+    uint32_t S;                    // segments per block
+    uint64_t seg_len;              // entries per segment (multiple of the tile)
+    uint32_t P;                    // phase-1 prefix kept in shared memory
+    FastDiv div_m, div_nb;
+};
+
+// Workspace layout for B > 1 (all offsets 256-byte aligned).
+struct PbaWorkspace {
+    size_t off_A, off_cnt, off_off, off_R, off_magic, total;
+};
+PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S);
+uint32_t pba_segments(uint64_t N_e, uint32_t B, int sm_count);
+uint64_t pba_segment_length(uint64_t N_e, uint32_t S);
+
+cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s);
+cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s);
+
+// CSR assembly.
+size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices);
+cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
+                       uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,
+                       cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace pgen

@@ -1,0 +1,63 @@
+"""Synthetic workloads: the named configurations and seeded input generators.
+
+This module holds parameters and seeded random inputs only -- none of the
+generators' arithmetic -- so that both the CUDA path and the CPU oracle can be
+driven from the same inputs. The configurations follow the paper's problem
+statement (vertex count, edges per new vertex, block count, initiator, seed).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Initiator of the stochastic Kronecker configuration (2x2, row-major).
+KRON_INITIATOR = [[0.57, 0.19], [0.19, 0.05]]
+
+CONFIGS = {
+    # serial BA: 100,000 new vertices, 4 edges each, seed clique K5
+    "ba_n100k_m4": dict(kind="pba", n=100_000, m=4, blocks=1, n0=5, faction_width=1,
+                        inter_frac=0.0, seed=1),
+    # stochastic Kronecker, k = 20 levels (2^20 vertices), 16 * 2^20 edges, plus CSR
+    "kron_k20_m16x_csr": dict(kind="kron", initiator=KRON_INITIATOR, k=20,
+                              n_edges=16 * 2**20, seed=7, csr=True),
+    # two-phase PBA at the paper's headline size: 2^30 new vertices in 1024
+    # blocks of 2^20, 5 edges each, inter-block fraction 0.1
+    "pba_n2p30_b1024_m5": dict(kind="pba", n=2**30, m=5, blocks=1024, n0=6, faction_width=1,
+                               inter_frac=0.1, seed=3),
+}
+
+
+def random_edges(seed: int, n_edges: int, n_vertices: int, id64: bool = False,
+                 hub_fraction: float = 0.0) -> np.ndarray:
+    """Seeded random (src, dst) list; a fraction of edges is pinned on vertex 0.
+
+    The hub makes one very long CSR row, the shape that power-law graphs give.
+    """
+    rng = np.random.default_rng(seed)
+    dt = np.uint64 if id64 else np.uint32
+    e = rng.integers(0, max(n_vertices, 1), size=(n_edges, 2), dtype=np.uint64)
+    if hub_fraction > 0 and n_edges > 0:
+        k = int(n_edges * hub_fraction)
+        e[rng.choice(n_edges, size=k, replace=False), 0] = 0
+    return e.astype(dt)
+
+
+def batch_jobs(n_jobs: int = 4096, seed: int = 0):
+    """Mixed batch of independent generation jobs (uneven sizes).
+
+    Half serial-BA jobs (m uniform in 2..8, vertex count log-uniform in
+    2^10..2^22), half stochastic Kronecker jobs (scale uniform in 10..22,
+    16 edges per vertex); job i uses generator seed i.
+    """
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(n_jobs):
+        if i < n_jobs // 2:
+            m = int(rng.integers(2, 9))
+            n = int(2 ** rng.uniform(10, 22))
+            jobs.append(dict(kind="pba", n=n, m=m, blocks=1, n0=m + 1, faction_width=1,
+                             inter_frac=0.0, seed=i))
+        else:
+            k = int(rng.integers(10, 23))
+            jobs.append(dict(kind="kron", initiator=KRON_INITIATOR, k=k, n_edges=16 * 2**k,
+                             seed=i))
+    return jobs

@@ -1,0 +1,113 @@
+"""The C ABI library loads, exports every symbol include/pgen.h declares, and
+rejects bad arguments on the host before any launch (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "pgen.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1003_3684_gb300 import build
+    build.build()
+    import paper_1003_3684_gb300 as pg
+    return pg.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "defined")))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("gen_pba", "gen_kronecker", "edges_to_csr", "pg_status_string",
+                     "pg_pba_workspace_size", "pg_csr_workspace_size"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings(L):
+    import paper_1003_3684_gb300 as pg
+    assert pg.pg_status_string(pg.PG_OK) == "ok"
+    assert "invalid" in pg.pg_status_string(pg.PG_EINVAL)
+    assert pg.pg_status_string(99) == "unknown status"
+
+
+def test_edge_counts_on_host(L):
+    import paper_1003_3684_gb300 as pg
+    assert pg.pg_pba_edge_count(100_000, 4, 1, 5) == 400_010
+    assert pg.pg_pba_edge_count(2**30, 5, 1024, 6) == 1024 * (15 + 2**20 * 5)
+    assert pg.pg_pba_edge_count(10, 2, 3, 4) == 0             # blocks do not divide n
+    G1 = [[1, 1, 1, 1, 0], [1, 1, 0, 0, 0], [1, 0, 1, 0, 0], [1, 0, 0, 1, 0], [0, 0, 0, 0, 1]]
+    assert pg.pg_kron_edge_count(G1, 3, 0, deterministic=True) == 11 ** 3
+    assert pg.pg_kron_edge_count([[0.5, 0.5], [0.5, 0.5]], 5, 1234) == 1234
+
+
+@pytest.mark.parametrize("args", [
+    (100, 0, 1, 5, 1, 0.1),       # m = 0
+    (100, 4, 1, 1, 1, 0.1),       # n0 = 1
+    (100, 4, 3, 5, 1, 0.1),       # blocks do not divide n
+    (120, 4, 4, 5, 3, 0.1),       # faction width does not divide blocks
+    (120, 4, 4, 5, 1, -0.5),      # f outside [0, 1]
+    (120, 4, 4, 5, 1, float("nan")),
+    (2048 * 2, 4, 2048, 5, 1, 0.1),   # more blocks than supported
+])
+def test_gen_pba_rejects_bad_arguments(L, args):
+    n, m, B, n0, W, f = args
+    cnt = C.c_uint64(7)
+    st = L.gen_pba(n, m, B, n0, W, f, 1, 0, None, 0, C.byref(cnt), None, 0, None)
+    assert st == 1
+
+
+def test_gen_pba_capacity_and_ids(L):
+    cnt = C.c_uint64(0)
+    # capacity too small: reports the count, launches nothing
+    st = L.gen_pba(100, 4, 1, 5, 1, 0.0, 1, 0, C.c_void_p(16), 5, C.byref(cnt), None, 0, None)
+    assert st == 2 and cnt.value == 410
+    # 2^32 vertex ids do not fit 32-bit ids
+    st = L.gen_pba(2**32, 1, 1, 5, 1, 0.0, 1, 0, None, 0, C.byref(cnt), None, 0, None)
+    assert st == 1
+    # misaligned output
+    st = L.gen_pba(100, 4, 1, 5, 1, 0.0, 1, 0, C.c_void_p(8), 10**6, C.byref(cnt), None, 0, None)
+    assert st == 1
+
+
+def test_gen_kronecker_rejects_bad_arguments(L):
+    import numpy as np
+    cnt = C.c_uint64(0)
+    P = np.array([[0.5, 0.2], [0.2, 0.1]])
+    Z = np.zeros((2, 2))
+    Neg = np.array([[0.5, -0.2], [0.2, 0.1]])
+    pp = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert L.gen_kronecker(pp(Z), 2, 4, 10, 1, 0, 0, C.c_void_p(16), 10, C.byref(cnt), None) == 1
+    assert L.gen_kronecker(pp(Neg), 2, 4, 10, 1, 0, 0, C.c_void_p(16), 10, C.byref(cnt), None) == 1
+    assert L.gen_kronecker(pp(P), 2, 33, 10, 1, 0, 0, C.c_void_p(16), 10, C.byref(cnt), None) == 1
+    assert L.gen_kronecker(pp(P), 2, 4, 10, 1, 0, 0, C.c_void_p(16), 9, C.byref(cnt), None) == 2
+    assert L.gen_kronecker(pp(P), 17, 2, 10, 1, 0, 0, C.c_void_p(16), 10, C.byref(cnt), None) == 1
+
+
+def test_edges_to_csr_rejects_bad_arguments(L):
+    assert L.edges_to_csr(C.c_void_p(16), 10, 0, 0, C.c_void_p(16), C.c_void_p(16),
+                          None, 0, None) == 1
+    assert L.edges_to_csr(C.c_void_p(16), 10, 100, 0, C.c_void_p(16), C.c_void_p(16),
+                          None, 0, None) == 5
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_1003_3684_gb300 as pg
+    monkeypatch.setattr(pg, "_LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(pg, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        pg.lib()

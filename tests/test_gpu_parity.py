@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Every comparison is bit-exact: the generators are integer-only and the
+output is a pure function of the arguments. Oracle inputs come from the
+oracle itself or from the seeded generators in ``workloads``; nothing the
+GPU produced is ever fed to the oracle.
+"""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+import paper_1003_3684_gb300 as pg
+from paper_1003_3684_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIG2 = [[1, 1, 1, 1, 0], [1, 1, 0, 0, 0], [1, 0, 1, 0, 0], [1, 0, 0, 1, 0], [0, 0, 0, 0, 1]]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1003_3684_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+    torch.cuda.synchronize()
+
+
+def host(t, id64=False):
+    a = t.cpu().numpy()
+    return a.view(np.uint64 if id64 else np.uint32).astype(np.uint64)
+
+
+def assert_same(gpu, ref):
+    assert gpu.shape == ref.shape, (gpu.shape, ref.shape)
+    bad = np.nonzero((gpu != ref).any(axis=-1) if gpu.ndim == 2 else gpu != ref)[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first at {bad[:5]}: {gpu[bad[:3]]} vs {ref[bad[:3]]}"
+
+
+# --------------------------------------------------------------------------
+# Kronecker
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("P,k,M,seed,id64", [
+    (W.KRON_INITIATOR, 20, 200_001, 7, False),
+    (W.KRON_INITIATOR, 20, 1, 7, False),
+    (W.KRON_INITIATOR, 20, 0, 7, False),
+    ([[0.5, 0.3], [0.15, 0.05]], 7, 50_000, 1, False),
+    ([[0.0, 0.6], [0.4, 0.0]], 9, 20_000, 2, False),          # zero cells at both ends
+    ([[0.2, 0.5, 0.0], [0.1, 0.05, 0.05], [0.0, 0.02, 0.08]], 5, 30_001, 3, False),
+    (np.arange(16.0).reshape(4, 4), 6, 40_000, 4, False),
+    (np.ones((16, 16)), 2, 10_000, 6, False),
+    ([[1.0]], 5, 17, 5, False),
+    (W.KRON_INITIATOR, 40, 100_003, 11, True),                 # 2^40 vertices
+    (W.KRON_INITIATOR, 12, 65_536, 2**40 + 3, True),           # 64-bit seed
+])
+def test_kron_stochastic(P, k, M, seed, id64):
+    got = pg.gen_kronecker(P, k, M, seed, id64=id64)
+    torch.cuda.synchronize()
+    assert_same(host(got, id64), o.kron(P, k, M, seed))
+
+
+@pytest.mark.parametrize("P,k,id64", [
+    (FIG2, 1, False), (FIG2, 2, False), (FIG2, 3, False), (FIG2, 5, False),
+    ([[1, 1], [1, 0]], 12, False), ([[0, 1], [1, 1]], 7, True),
+])
+def test_kron_deterministic(P, k, id64):
+    got = pg.gen_kronecker(P, k, deterministic=True, id64=id64)
+    ref, _ = o.kron_det(np.asarray(P, float), k)
+    torch.cuda.synchronize()
+    assert_same(host(got, id64), ref)
+
+
+def test_kron_deterministic_large_seed():
+    rng = np.random.default_rng(9)
+    P = (rng.random((40, 40)) < 0.15).astype(float)
+    P[0, 0] = 1.0
+    got = pg.gen_kronecker(P, 2, deterministic=True)
+    ref, _ = o.kron_det(P, 2)
+    assert_same(host(got), ref)
+
+
+# --------------------------------------------------------------------------
+# Serial BA (blocks = 1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m,n0,seed,id64", [
+    (100_000, 4, 5, 1, False),    # serial BA workload: 100k new vertices, m = 4, K5 seed
+    (33_333, 3, 2, 5, False),
+    (5_000, 8, 9, 2**33 + 1, True),
+    (1, 1, 2, 0, False),
+    (0, 4, 5, 1, False),
+    (4097, 1, 3, 8, False),
+])
+def test_ba(n, m, n0, seed, id64):
+    got = pg.gen_pba(n, m, 1, n0, 1, 0.0, seed, id64=id64)
+    torch.cuda.synchronize()
+    assert_same(host(got, id64), o.ba(n, m, n0, seed).astype(np.uint64))
+
+
+# --------------------------------------------------------------------------
+# Two-phase PBA
+# --------------------------------------------------------------------------
+
+PBA_CASES = [
+    # B, n_b, m, W, f, n0, seed
+    (8, 30_000, 5, 1, 0.1, 6, 3),      # spans the smem prefix, tiles and segments
+    (16, 10_000, 4, 2, 0.3, 4, 7),
+    (6, 20_000, 7, 3, 1.0, 3, 11),     # every later entry is an inter-faction pick
+    (5, 40_000, 2, 5, 0.5, 5, 2),      # one faction holds every block
+    (4, 70_000, 3, 1, 0.0, 2, 9),      # isolated blocks
+    (1024, 100, 5, 1, 0.1, 6, 3),      # many blocks, short lists
+    (3, 1, 1, 1, 0.2, 2, 1),           # one vertex per block
+    (7, 0, 3, 7, 0.1, 4, 1),           # no new vertices: seed cliques only
+    (2, 50_000, 1, 1, 0.9, 2, 12345),
+]
+
+
+@pytest.mark.parametrize("B,n_b,m,Wf,f,n0,seed", PBA_CASES)
+def test_pba(B, n_b, m, Wf, f, n0, seed):
+    n = B * n_b
+    got = pg.gen_pba(n, m, B, n0, Wf, f, seed)
+    ref, _, _ = o.pba(n, m, B, n0, Wf, f, seed)
+    torch.cuda.synchronize()
+    assert_same(host(got), ref)
+
+
+def test_pba_id64_and_repeat_is_identical():
+    B, n_b, m = 12, 9_000, 3
+    a = pg.gen_pba(B * n_b, m, B, 4, 2, 0.2, 77, id64=True)
+    b = pg.gen_pba(B * n_b, m, B, 4, 2, 0.2, 77, id64=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    ref, _, _ = o.pba(B * n_b, m, B, 4, 2, 0.2, 77)
+    assert_same(host(a, True), ref)
+
+
+def test_pba_other_stream():
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        got = pg.gen_pba(6 * 7000, 4, 6, 5, 1, 0.1, 5)
+    s.synchronize()
+    ref, _, _ = o.pba(6 * 7000, 4, 6, 5, 1, 0.1, 5)
+    assert_same(host(got), ref)
+
+
+@pytest.mark.slow
+def test_pba_headline_size_sampled():
+    """2^30 new vertices, 1024 blocks, m = 5, f = 0.1 -- the launch the
+    benchmark times. The oracle runs phase 1 for every block (threads over
+    independent blocks) and the full substitution for sampled blocks."""
+    cfg = W.CONFIGS["pba_n2p30_b1024_m5"]
+    n, m, B, n0, Wf, f, seed = (cfg[k] for k in ("n", "m", "blocks", "n0", "faction_width",
+                                                 "inter_frac", "seed"))
+    n_b, N_e, e0 = n // B, (n // B) * m, n0 * (n0 - 1) // 2
+    span, per = n0 + n_b, e0 + N_e
+    edges = pg.gen_pba(n, m, B, n0, Wf, f, seed)
+    torch.cuda.synchronize()
+    assert edges.shape[0] == B * per
+
+    # oracle phase 1 on every block
+    counts = np.zeros((B, B), np.uint64)
+    sampled = {0: None, 1: None, 511: None, B - 1: None}
+
+    def run(p):
+        A, c, _ = o.pba_phase1(p, B, Wf, N_e, f, seed)
+        return p, (A if p in sampled else None), c
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
+        for p, A, c in ex.map(run, range(B)):
+            counts[p] = c
+            if A is not None:
+                sampled[p] = A
+    R = counts.sum(axis=0)
+    assert R.sum() == n * m
+
+    # per-block target counts of the GPU output (computed on the device)
+    e = edges.view(B, per, 2)
+    gpu_counts = np.zeros((B, B), np.int64)
+    for p in range(B):
+        q = (e[p, e0:, 1].to(torch.int64) & 0xFFFFFFFF) // span
+        gpu_counts[p] = torch.bincount(q, minlength=B).cpu().numpy()
+    assert np.array_equal(gpu_counts, counts.astype(np.int64))
+
+    start_all = np.concatenate([np.zeros((1, B), np.uint64), np.cumsum(counts, axis=0)[:-1]])
+    for p, A in sampled.items():
+        blk = host(e[p])
+        ids = np.arange(n0)
+        assert np.array_equal(blk[:e0], np.array([[p * span + a, p * span + b] for a in ids
+                                                  for b in ids if a < b], np.uint64))
+        gen = blk[e0:]
+        assert np.array_equal(gen[:, 0], p * span + n0 + np.arange(N_e, dtype=np.uint64) // m)
+        assert np.array_equal(gen[:, 1] // span, A.astype(np.uint64))
+        local = gen[:, 1] % span
+        qs = range(B) if p < 2 else sorted({p, int(A[-1]), 0})
+        for q in qs:
+            sel = np.nonzero(A == q)[0]
+            s0 = int(start_all[p, q])
+            T = o.pba_endpoints(q, int(R[q]), n_b, n0, seed, s0 + sel.size)
+            assert np.array_equal(local[sel], T[s0:].astype(np.uint64)), (p, q)
+
+
+# --------------------------------------------------------------------------
+# CSR
+# --------------------------------------------------------------------------
+
+def csr_check(edges_np, N, id64=False):
+    t = torch.from_numpy(edges_np.view(np.int64 if id64 else np.int32)).cuda()
+    rp, col = pg.edges_to_csr(t, N)
+    torch.cuda.synchronize()
+    ref_rp, ref_col = o.csr(edges_np.astype(np.uint64), N)
+    assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp)
+    assert_same(host(col, id64), ref_col)
+
+
+@pytest.mark.parametrize("M,N,hub,id64", [
+    (300_001, 5_000, 0.3, False),    # one very long row
+    (100_000, 2**20, 0.0, False),
+    (8_191, 3, 0.0, False),
+    (50_000, 1, 0.0, False),         # a single row: nothing to sort on
+    (0, 10, 0.0, False),
+    (70_000, 2**33 + 5, 0.1, True),  # 34-bit ids
+])
+def test_csr_random(M, N, hub, id64):
+    csr_check(W.random_edges(M + N, M, N, id64=id64, hub_fraction=hub), N, id64)
+
+
+def test_csr_of_kronecker_and_pba_graphs():
+    ek = o.kron(W.KRON_INITIATOR, 16, 2**20, 7).astype(np.uint32)
+    csr_check(ek, 2**16)
+    ep, _, _ = o.pba(8 * 5000, 4, 8, 5, 1, 0.1, 3)
+    csr_check(ep.astype(np.uint32), 8 * (5 + 5000))
+
+
+@pytest.mark.slow
+def test_csr_kron_workload_full():
+    """Kronecker k = 20, 16 * 2^20 edges, seed 7 -- edge list and CSR."""
+    cfg = W.CONFIGS["kron_k20_m16x_csr"]
+    ref_edges = o.kron(cfg["initiator"], cfg["k"], cfg["n_edges"], cfg["seed"])
+    got = pg.gen_kronecker(cfg["initiator"], cfg["k"], cfg["n_edges"], cfg["seed"])
+    rp, col = pg.edges_to_csr(got, 2 ** cfg["k"])
+    torch.cuda.synchronize()
+    assert_same(host(got), ref_edges)
+    ref_rp, ref_col = o.csr(ref_edges, 2 ** cfg["k"])
+    assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp)
+    assert_same(host(col), ref_col)
