@@ -214,6 +214,10 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     cfg = dict(W.CONFIGS[args.workload])
+    if args.blocks and cfg["kind"] == "pba":
+        # a smaller case of the same workload: fewer blocks of the same size
+        cfg["n"] = cfg["n"] // cfg["blocks"] * args.blocks
+        cfg["blocks"] = args.blocks
     seed = cfg["seed"] + rank
     stream = torch.cuda.current_stream()
     kind = cfg["kind"]
@@ -232,7 +236,8 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                  "ba_chain": n * m}
         work = dict(KERNEL_WORK)
         out_bytes = E * 8
-        cfg_json = dict(workload=args.workload, n=n, m=m, blocks=B, n0=n0,
+        cfg_json = dict(workload=args.workload + (f" (blocks={B})" if args.blocks else ""),
+                        n=n, m=m, blocks=B, n0=n0,
                         faction_width=cfg["faction_width"], inter_frac=cfg["inter_frac"],
                         seed=cfg["seed"], edges_per_step=E, id_width=32,
                         workspace_bytes=ws_bytes)
@@ -402,6 +407,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(W.CONFIGS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--blocks", type=int, default=0,
+                    help="PBA only: run this many blocks of the workload's block size "
+                         "(a smaller case, e.g. for profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     args = ap.parse_args()

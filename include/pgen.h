@@ -150,9 +150,11 @@ pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertice
  * Kernel timing trace (profiling aid, not part of the method).
  * pg_trace_enable(1): from then on every kernel the library launches is
  * bracketed by two CUDA events recorded on the launch's stream.
- * pg_trace_dump(buf, len): waits for the recorded events, writes a JSON object
- * {"kernel_name": [launches, total_ms], ...} into buf (NUL-terminated,
- * truncated to len), clears the record and returns the bytes needed.
+ * pg_trace_dump(buf, len): waits for the recorded events and returns the
+ * size (with the NUL) of a JSON object {"kernel_name": [launches, total_ms],
+ * ...}. When buf holds at least that many bytes the object is written there
+ * and the record is cleared; otherwise (buf NULL or too small) nothing is
+ * written and the record is kept, so the call doubles as a size query.
  * ---------------------------------------------------------------------- */
 void pg_trace_enable(int on);
 size_t pg_trace_dump(char* buf, size_t len);

@@ -62,6 +62,7 @@ PbaCheck check_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, 
     const u128 ids = (u128)B * (n0 + (u128)n_b);
     if (w == PG_ID32 && ids > ((u128)1 << 32)) return c;
     if ((u128)n0 + n_b >= ((u128)1 << 32)) return c;       // local ids are 32-bit
+    if (N_e >= ((u128)1 << 32)) return c;                  // entries per block are 32-bit
     // phase-2 index arithmetic: (total entries) * n_b must stay below 2^63
     if ((u128)B * N_e * (n_b ? n_b : 1) >= ((u128)1 << 63)) return c;
     c.st = PG_OK;
@@ -87,12 +88,17 @@ PbaGeom make_geom(uint64_t n_b, uint64_t N_e, uint32_t m, uint32_t B, uint32_t n
     g.n0 = n0;
     g.coin_thr = coin_threshold(f);
     g.coin_on = (B > W && g.coin_thr > 0) ? 1 : 0;
-    g.key.k0 = (uint32_t)seed;
-    g.key.k1 = (uint32_t)(seed >> 32);
+    g.key = make_key(seed);
     g.S = pba_segments(N_e, B, device_sm_count());
     g.seg_len = pba_segment_length(N_e, g.S);
-    g.P = (uint32_t)(N_e < 65536 ? N_e : 65536);
+    g.P = pba_prefix_len(N_e);
+    g.nb_shift = 0xFFFFFFFFu;
+    if (n_b > 0 && (n_b & (n_b - 1)) == 0) {
+        g.nb_shift = 0;
+        while (((uint64_t)1 << g.nb_shift) < n_b) ++g.nb_shift;
+    }
     g.div_m = make_fastdiv(m);
+    g.div_m32 = make_fastdiv32(m);
     g.div_nb = make_fastdiv(n_b > 0 ? n_b : 1);
     return g;
 }
@@ -215,8 +221,7 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
         if (!kron_thresholds(h_initiator, n0, T)) return PG_EINVAL;
         p.n0 = n0;
         p.k = k;
-        p.key.k0 = (uint32_t)seed;
-        p.key.k1 = (uint32_t)(seed >> 32);
+        p.key = make_key(seed);
         for (int t = 0; t < kMaxKronThr; ++t) p.u[t] = 0xFFFFFFFFu;
         uint32_t c = 0;
         while (c + 1 < cells && T[c] == 0) ++c;

@@ -1,57 +1,66 @@
 // Parallel Barabasi-Albert generator (arXiv 1003.3684, Sec. 3, PBA method).
 //
 // The paper runs one processor per vertex block and exchanges messages
-// between phases. Here a block's phases run as data-parallel kernels over
-// (block, segment) pairs on one GPU, and every message becomes HBM traffic:
+// between phases. Here the phases of all blocks run as data-parallel kernels
+// on one GPU, and every message becomes HBM traffic:
 //
-//   pba_prefix   phase 1, first P entries of every block's list A_p, built
-//                in shared memory level by level (entries [L, 2L) only copy
-//                from [0, 2L)); written to A_p.
-//   pba_phase1   phase 1, the rest of A_p. Entry j copies a uniform earlier
-//                entry r < j, or is an inter-faction pick. Instead of walking
-//                A_p in order, each entry follows its own chain of copy
-//                pointers (one Philox per link, recomputed from the counter)
-//                until it reaches a pick or the shared-memory prefix. Writes
-//                A_p (uint16) and a per-(block, segment) count of each
-//                target block -- the paper's count message.
+//   pba_prefix   phase 1, first P entries of every block's list A_p, built in
+//                shared memory level by level: entries [L, 2L) copy from
+//                [0, L) (already final) or follow their own chain inside
+//                [L, 2L). Writes A_p[0, P) and counts it.
+//   pba_pass     phase 1, one doubling level [L, min(2L, N_e)) of every block
+//                per launch. Entry j draws once (Philox, counter (j, p, 1)):
+//                an inter-faction pick, or a copy of entry r < j. A copy with
+//                r < L reads the finished A_p[r] from global memory (the
+//                grid is block-major, so the few blocks in flight keep their
+//                A_p in L2); a copy with r >= L follows r's own draw. Adds
+//                the counts of each (block, segment) -- the paper's count
+//                message -- into cnt.
 //   pba_scan     exclusive scan of the counts over (requester, segment) per
 //                target block: R_q (how many endpoints q must produce) and
-//                the start of each requester segment's slice of q's list.
+//                where each requester segment's slice of q's list starts.
 //   pba_emit     phase 2 and substitution. The stable rank of entry j among
-//                the entries of its segment that name the same block (warp
-//                match + per-warp counters + cross-warp scan) gives index i
-//                into q's endpoint list T_q; T_q[i] is resolved by its own
-//                copy chain through q's local preferential attachment
-//                (recomputed, never materialised), and the finished (src,
-//                dst) pairs leave through a shared-memory staging tile as
-//                coalesced vector stores.
+//                the earlier entries of its segment naming the same block
+//                (warp match + per-warp counters + cross-warp scan) gives its
+//                index i in q's endpoint list T_q; T_q[i] is resolved by its
+//                own copy chain through q's local preferential attachment
+//                (recomputed, never stored), and the (src, dst) pairs leave
+//                through a shared-memory tile as coalesced vector stores.
 //
 // blocks = 1 is serial BA: ba_kernel resolves edge j's chain directly.
 //
-// Copy chains are geometric in length, so each thread owns ITEMS entries and
-// advances whichever one it is working on by one link per loop trip; a warp
-// then waits for the slowest lane's sum of ITEMS chains rather than for the
-// longest single chain.
+// Copy chains have geometric lengths. A warp works on a run of consecutive
+// entries; each lane follows one chain, one Philox per loop trip, and a lane
+// whose entry is finished takes the next unclaimed entry of the run (ballot),
+// so lanes stay busy until the run is exhausted.
+#include <type_traits>
+
 #include "pg_internal.h"
 #include "pg_trace.h"
 
 namespace pgen {
 namespace {
 
-constexpr uint32_t kPrefixMax = 65536;    // phase-1 prefix held in smem (uint16)
-constexpr int kP1Threads = 1024;
-constexpr int kP1Items = 16;
-constexpr uint64_t kP1Tile = (uint64_t)kP1Threads * kP1Items;   // 16384
-constexpr int kEmitWarps = 16;
+constexpr uint32_t kGranule = 16384;        // segment lengths are multiples of this
+constexpr uint32_t kPrefixMax = 6 * kGranule;   // phase-1 prefix built in smem (192 KB)
+constexpr int kPrefixThreads = 1024;
+constexpr int kPassThreads = 512;
+constexpr uint32_t kPassRun = 1024;             // entries per warp run in a pass
+constexpr uint32_t kPassChunk = (kPassThreads / 32) * kPassRun;   // 16384 per CTA
+constexpr int kEmitWarps = 8;
 constexpr int kEmitThreads = kEmitWarps * 32;
 constexpr int kEmitItems = 16;
-constexpr uint32_t kEmitTile = kEmitThreads * kEmitItems;        // 8192
+constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 512 entries per warp run
 constexpr uint32_t kMaxBlocks = 1024;
 constexpr int kBaThreads = 256;
-constexpr int kBaItems = 16;
-constexpr uint32_t kBaTile = kBaThreads * kBaItems;              // 4096
+template <typename Id>
+struct BaShape {   // 32 KB of staging for either id width
+    static constexpr uint32_t run = sizeof(Id) == 4 ? 1024 : 512;
+    static constexpr uint32_t tile = (kBaThreads / 32) * run;
+};
 
-static_assert(kP1Tile % kEmitTile == 0, "segment length must suit both tiles");
+static_assert(kPassChunk == kGranule, "a pass CTA covers one granule");
+static_assert(kGranule % kEmitRun == 0, "segments hold whole emit runs");
 
 // Inter-faction pick: uniform over the B - W blocks outside [phi, phi + W).
 __device__ __forceinline__ uint32_t fresh_block(uint32_t w3, uint32_t B, uint32_t W,
@@ -61,14 +70,25 @@ __device__ __forceinline__ uint32_t fresh_block(uint32_t w3, uint32_t B, uint32_
     return x < phi ? x : x + W;
 }
 
+// Adds a smem histogram of B counters to cnt row (p, sgm), skipping zeros.
+__device__ __forceinline__ void flush_counts(const uint32_t* hist, uint32_t* cnt,
+                                             const PbaGeom& g, uint32_t p, uint32_t sgm)
+{
+    uint32_t* row = cnt + ((uint64_t)p * g.S + sgm) * g.B;
+    for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x)
+        if (hist[t]) atomicAdd(&row[t], hist[t]);
+}
+
 // ---------------------------------------------------------------------------
 // Phase 1, prefix [0, P) of each block, built in shared memory.
-// grid = B, block = kP1Threads, dynamic smem = P * 2 bytes.
+// grid = B, block = kPrefixThreads, dynamic smem = P*2 (rounded to 16) + B*4.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kP1Threads) pba_prefix_kernel(const __grid_constant__ PbaGeom g,
-                                                                uint16_t* __restrict__ A)
+__global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
+    const __grid_constant__ PbaGeom g, uint16_t* __restrict__ A, uint32_t* __restrict__ cnt)
 {
-    extern __shared__ uint16_t sA[];
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint16_t* sA = reinterpret_cast<uint16_t*>(smem);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((g.P * 2 + 15) & ~15u));
     const uint32_t p = blockIdx.x;
     const uint32_t phi = (p / g.W) * g.W;
     const uint32_t P = g.P;
@@ -78,15 +98,14 @@ __global__ void __launch_bounds__(kP1Threads) pba_prefix_kernel(const __grid_con
     for (uint32_t L = s; L < P;) {
         const uint32_t hi = (2 * L < P) ? 2 * L : P;
         for (uint32_t j = L + threadIdx.x; j < hi; j += blockDim.x) {
-            uint64_t cur = j;
-            uint32_t v;
+            uint32_t cur = j, v;
             for (;;) {
-                const uint4 w = draw(cur, p, 1, g.key);
+                const uint4 w = philox(make_uint4(cur, 0u, p, 1u), g.key);
                 if (g.coin_on && w.z < g.coin_thr) {
                     v = fresh_block(w.w, g.B, g.W, phi);
                     break;
                 }
-                const uint64_t r = uniform64(w.x, w.y, cur);
+                const uint32_t r = uniform32(w.x, w.y, cur);
                 if (r < L) {
                     v = sA[r];
                     break;
@@ -100,78 +119,86 @@ __global__ void __launch_bounds__(kP1Threads) pba_prefix_kernel(const __grid_con
     }
     uint16_t* Ap = A + (uint64_t)p * g.A_stride;
     for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) Ap[t] = sA[t];
+    // counts of the prefix, per segment it overlaps
+    for (uint32_t sgm = 0; (uint64_t)sgm * g.seg_len < P; ++sgm) {
+        const uint32_t a = (uint32_t)((uint64_t)sgm * g.seg_len);
+        const uint32_t b = (uint32_t)((a + g.seg_len < P) ? a + g.seg_len : P);
+        for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x) hist[t] = 0;
+        __syncthreads();
+        for (uint32_t t = a + threadIdx.x; t < b; t += blockDim.x) atomicAdd(&hist[sA[t]], 1u);
+        __syncthreads();
+        flush_counts(hist, cnt, g, p, sgm);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Phase 1, entries of one (block, segment); grid = (S, B).
-// dynamic smem: prefix P*2 | histogram B*4 | staging kP1Tile*2
+// Phase 1, one doubling level [L, hi) of every block; grid = (chunks, B),
+// chunk c = [L + c*kPassChunk, ...). dynamic smem = B*4 (histogram).
+// A copy that lands below L loads A_p[r]; the load is consumed one loop trip
+// later (after the next Philox), so its latency overlaps arithmetic.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kP1Threads, 1) pba_phase1_kernel(const __grid_constant__ PbaGeom g,
-                                                                   uint16_t* __restrict__ A,
-                                                                   uint32_t* __restrict__ cnt)
+__global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_constant__ PbaGeom g,
+                                                                uint32_t L, uint32_t hi,
+                                                                uint16_t* __restrict__ A,
+                                                                uint32_t* __restrict__ cnt)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t* sA = reinterpret_cast<uint16_t*>(smem);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((g.P * 2 + 15) & ~15u));
-    uint16_t* sOut = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(hist) +
-                                                 (((size_t)g.B * 4 + 15) & ~(size_t)15));
-    const uint32_t p = blockIdx.y, sgm = blockIdx.x;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+    const uint32_t p = blockIdx.y;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint32_t phi = (p / g.W) * g.W;
-    const uint32_t P = g.P;
-    uint16_t* Ap = A + (uint64_t)p * g.A_stride;   // 16-byte aligned row
-    const uint64_t lo = (uint64_t)sgm * g.seg_len;
-    const uint64_t hi = (lo + g.seg_len < g.N_e) ? lo + g.seg_len : g.N_e;
-
-    for (uint32_t t = threadIdx.x; t < P / 8; t += blockDim.x)
-        reinterpret_cast<uint4*>(sA)[t] = reinterpret_cast<const uint4*>(Ap)[t];
-    for (uint32_t t = (P & ~7u) + threadIdx.x; t < P; t += blockDim.x) sA[t] = Ap[t];
+    uint16_t* Ap = A + (uint64_t)p * g.A_stride;
+    const uint32_t chunk = L + blockIdx.x * kPassChunk;   // a granule: one segment
     for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x) hist[t] = 0;
     __syncthreads();
 
-    for (uint64_t base = lo; base < hi; base += kP1Tile) {
-        int k = 0;
-        uint64_t j = base + threadIdx.x;
-        uint64_t cur = j;
-        while (k < kP1Items) {
-            bool done = true;
-            uint32_t v = 0;
-            if (j < hi) {
-                if (cur < P) {
-                    v = sA[cur];
+    const uint32_t run = chunk + wid * kPassRun;
+    const uint32_t n_items = run < hi ? ((hi - run < kPassRun) ? hi - run : kPassRun) : 0;
+    const bool coin_on = g.coin_on != 0;
+    uint32_t next = 32, item = lane;
+    uint32_t cur = run + item;
+    bool active = item < n_items;
+    bool pend = false;
+    uint32_t pend_j = 0, pend_v = 0;
+    while (__any_sync(0xFFFFFFFFu, active || pend)) {
+        uint4 w = make_uint4(0, 0, 0, 0);
+        if (active) w = philox(make_uint4(cur, 0u, p, 1u), g.key);
+        if (pend) {   // the value loaded one trip ago
+            Ap[pend_j] = (uint16_t)pend_v;
+            atomicAdd(&hist[pend_v], 1u);
+            pend = false;
+        }
+        bool done = false;
+        if (active) {
+            if (coin_on && w.z < g.coin_thr) {
+                pend_v = fresh_block(w.w, g.B, g.W, phi);
+                done = true;
+            } else {
+                const uint32_t r = uniform32(w.x, w.y, cur);
+                if (r < L) {
+                    pend_v = __ldg(Ap + r);
+                    done = true;
                 } else {
-                    const uint4 w = draw(cur, p, 1, g.key);
-                    if (g.coin_on && w.z < g.coin_thr) {
-                        v = fresh_block(w.w, g.B, g.W, phi);
-                    } else {
-                        cur = uniform64(w.x, w.y, cur);
-                        done = false;
-                    }
+                    cur = r;
                 }
             }
             if (done) {
-                if (j < hi) {
-                    sOut[k * kP1Threads + threadIdx.x] = (uint16_t)v;
-                    atomicAdd(&hist[v], 1u);
-                }
-                ++k;
-                j += kP1Threads;
-                cur = j;
+                pend = true;
+                pend_j = run + item;
             }
         }
-        __syncthreads();
-        // coalesced store of the tile (entries [base, min(base + tile, hi)))
-        const uint64_t n = (hi - base < kP1Tile) ? hi - base : kP1Tile;
-        if (n == kP1Tile) {   // base is a multiple of the tile: aligned
-            const uint4* src = reinterpret_cast<const uint4*>(sOut);
-            uint4* dst = reinterpret_cast<uint4*>(Ap + base);
-            for (uint32_t t = threadIdx.x; t < kP1Tile / 8; t += blockDim.x) dst[t] = src[t];
-        } else {
-            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) Ap[base + t] = sOut[t];
+        const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+        if (done) {
+            item = next + __popc(dm & lt);
+            cur = run + item;
+            active = item < n_items;
         }
-        __syncthreads();
+        next += __popc(dm);
     }
-    uint32_t* row = cnt + ((uint64_t)p * g.S + sgm) * g.B;
-    for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x) row[t] = hist[t];
+    __syncthreads();
+    flush_counts(hist, cnt, g, p, (uint32_t)(chunk / g.seg_len));
 }
 
 // ---------------------------------------------------------------------------
@@ -179,11 +206,46 @@ __global__ void __launch_bounds__(kP1Threads, 1) pba_phase1_kernel(const __grid_
 // of cnt[row][q]; writes off[row][q], R[q] and the divisor for R[q].
 // grid = ceil(B / 32), block = 1024 (warp w scans a slab of rows, lane = q).
 // ---------------------------------------------------------------------------
+// Exact reciprocal of R for sigma(x) = floor(x * n_b / R), x < R < 2^32:
+// C = ceil(n_b * 2^64 / R) as three 32-bit words (C2 = n_b div R). Then
+// x*C/2^64 = x*n_b/R + x*d/2^64 with 0 <= d < 1, and x/2^64 < 1/R because
+// R^2 < 2^64; the fractional part of x*n_b/R is a multiple of 1/R below 1, so
+// adding less than 1/R never carries: floor(x*C/2^64) = sigma(x) exactly.
+struct QRecip {
+    uint32_t R, C2, C1, C0;
+};
+
+__device__ inline QRecip make_recip(uint64_t R, uint32_t nb)
+{
+    QRecip c{0, 0, 0, 0};
+    if (R == 0 || R >= ((uint64_t)1 << 32)) return c;
+    c.R = (uint32_t)R;
+    c.C2 = (uint32_t)(nb / R);
+    const uint64_t rem = nb % R;                     // < R < 2^32
+    const uint64_t a = rem << 32;
+    const uint64_t q_hi = a / R, r1 = a % R;
+    const uint64_t b = r1 << 32;
+    const uint64_t q_lo = b / R, r2 = b % R;
+    const uint64_t frac = (q_hi << 32) + q_lo + (r2 != 0 ? 1 : 0);
+    c.C1 = (uint32_t)(frac >> 32);
+    c.C0 = (uint32_t)frac;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t sigma32(uint32_t x, const QRecip& c)
+{
+    const uint64_t t0 = (uint64_t)x * c.C0;
+    const uint64_t t1 = (uint64_t)x * c.C1 + (t0 >> 32);
+    return (uint32_t)(t1 >> 32) + x * c.C2;
+}
+
 __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restrict__ cnt,
                                                         uint64_t* __restrict__ off,
                                                         uint64_t* __restrict__ R,
-                                                        FastDiv* __restrict__ divR, uint32_t B,
-                                                        uint32_t rows)
+                                                        FastDiv* __restrict__ divR,
+                                                        QRecip* __restrict__ recip, uint32_t nb,
+                                                        uint32_t B, uint32_t rows, uint64_t e0,
+                                                        uint32_t* __restrict__ wide_flag)
 {
     __shared__ uint64_t part[32][33];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -206,6 +268,8 @@ __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restri
         if (q < B) {
             R[q] = acc;
             divR[q] = make_fastdiv(acc > 0 ? acc : 1);
+            recip[q] = make_recip(acc, nb);
+            if (acc + e0 >= ((uint64_t)1 << 32)) atomicOr(wide_flag, 1u);
         }
     }
     __syncthreads();
@@ -224,20 +288,15 @@ __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restri
 // local preferential attachment: local edge i stands at source time
 // sigma(i) = floor(i*n_b/R_q) and copies a uniform slot among the seed clique
 // and the E(sigma(i)) = ceil(sigma(i)*R_q/n_b) edges of earlier source times.
-// One Philox per link; returns after the link that lands on a seed slot or on
-// the source end of an earlier edge.
+// One Philox per link; a link ends the chain when it lands on a seed slot or
+// on the source end of an earlier edge.
 // ---------------------------------------------------------------------------
 struct QDiv {
     uint64_t R;
     FastDiv d;
 };
 
-__device__ __forceinline__ uint16_t pack_shifts(const FastDiv& f)
-{
-    return (uint16_t)(f.s1 | (f.s2 << 8));
-}
-
-// one link of the chain; returns true and sets v when finished
+// 64-bit link (any R_q).
 __device__ __forceinline__ bool t_step(uint64_t& cur, uint32_t q, const QDiv& qd,
                                        const PbaGeom& g, uint32_t& v)
 {
@@ -259,6 +318,37 @@ __device__ __forceinline__ bool t_step(uint64_t& cur, uint32_t q, const QDiv& qd
     return false;
 }
 
+// 32-bit link (R_q + e0 < 2^32): the same values as t_step.
+__device__ __forceinline__ bool t_step32(uint32_t& cur, uint32_t q, const QRecip& c,
+                                         const PbaGeom& g, uint32_t& v)
+{
+    const uint32_t nb = (uint32_t)g.n_b;
+    const uint32_t sig = sigma32(cur, c);
+    uint32_t before;
+    if (g.nb_shift != 0xFFFFFFFFu)
+        before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
+    else
+        before = (uint32_t)fdiv((uint64_t)sig * c.R + (nb - 1), g.div_nb);
+    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
+    // r = floor(W * 2X / 2^64) with W = (w1:w0), X = e0 + before < 2^32:
+    // e = r >> 1 is the high word of s = w1*X + (w0*X >> 32), side = bit 31
+    const uint32_t X = (uint32_t)g.e0 + before;
+    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
+    const uint32_t e = (uint32_t)(s >> 32);
+    const uint32_t side = ((uint32_t)s) >> 31;
+    if (e < (uint32_t)g.e0) {
+        v = seed_endpoint(e, side, g.n0);
+        return true;
+    }
+    const uint32_t e2 = e - (uint32_t)g.e0;
+    if (side == 0) {
+        v = g.n0 + sigma32(e2, c);
+        return true;
+    }
+    cur = e2;
+    return false;
+}
+
 // Serial BA (blocks = 1): sigma(i) = i div m, E = sigma * m.
 __device__ __forceinline__ bool ba_step(uint64_t& cur, const PbaGeom& g, uint64_t& v)
 {
@@ -276,6 +366,28 @@ __device__ __forceinline__ bool ba_step(uint64_t& cur, const PbaGeom& g, uint64_
         return true;
     }
     cur = e;
+    return false;
+}
+
+// 32-bit serial BA link (n*m + e0 < 2^32).
+__device__ __forceinline__ bool ba_step32(uint32_t& cur, const PbaGeom& g, uint32_t& v)
+{
+    const uint32_t sig = fdiv32(cur, g.div_m32);
+    const uint4 w = philox(make_uint4(cur, 0u, 0u, 2u), g.key);
+    const uint32_t X = (uint32_t)g.e0 + sig * g.m;
+    const uint64_t hi = (uint64_t)w.y * X, lo = (uint64_t)w.x * X;
+    const uint64_t r = (hi + (lo >> 32)) >> 31;
+    const uint32_t e = (uint32_t)(r >> 1);
+    if (e < (uint32_t)g.e0) {
+        v = seed_endpoint(e, (uint32_t)(r & 1), g.n0);
+        return true;
+    }
+    const uint32_t e2 = e - (uint32_t)g.e0;
+    if ((r & 1) == 0) {
+        v = g.n0 + fdiv32(e2, g.div_m32);
+        return true;
+    }
+    cur = e2;
     return false;
 }
 
@@ -336,154 +448,215 @@ __device__ void write_seed_edges(Id* out, uint64_t e_first, uint64_t base, uint3
                    base + seed_endpoint(e, 1, n0));
 }
 
+// Warp-scoped version of emit_tile: lanes of one warp write n edges.
+template <typename Id, typename F>
+__device__ __forceinline__ void emit_run(Id* out, uint64_t e_first, uint32_t n, uint32_t lane,
+                                         F&& edge_at)
+{
+    const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
+    if (head && lane == 0) {
+        uint64_t s0, d0;
+        edge_at(0, s0, d0);
+        store_pair(out, e_first, s0, d0);
+    }
+    for (uint32_t t2 = head + 2 * lane; t2 < n; t2 += 64) {
+        uint64_t s0, d0;
+        edge_at(t2, s0, d0);
+        if (t2 + 1 < n) {
+            uint64_t s1, d1;
+            edge_at(t2 + 1, s1, d1);
+            store_two(out, e_first + t2, s0, d0, s1, d1);
+        } else {
+            store_pair(out, e_first + t2, s0, d0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Phase 2 + substitution + emission for one (block, segment); grid = (S, B).
+// Phase 2 + substitution + emission. Every warp owns one segment of one block
+// (grid = (ceil(S / kEmitWarps), B)) and walks it in runs of kEmitRun entries:
+//   rank   entry j gets i = (next unused slot of T_{A[j]} for this segment),
+//          by a warp match over 32 entries and per-warp cursors in smem;
+//   chain  the lanes resolve T_q[i] for the run's entries, pooled;
+//   emit   the run's (src, dst) pairs leave as vector stores.
+// Warps never wait on each other. kFast: 32-bit arithmetic, valid when every
+// R_q + e0 < 2^32 (the scan's flag says which variant does the work).
 // ---------------------------------------------------------------------------
-struct EmitSmem {   // 108 KB: two CTAs per SM
-    uint64_t cur[kMaxBlocks];                   // next unused index into T_q
-    uint64_t R[kMaxBlocks];                     // R_q
-    uint64_t mul[kMaxBlocks];                   // divisor multiplier for R_q
-    uint16_t sh[kMaxBlocks];                    // divisor shifts (s1 | s2 << 8)
-    uint16_t wcnt[kEmitWarps + 1][kMaxBlocks];  // per-warp counts / prefixes; last row = tile total
-    uint32_t item[kEmitTile];                   // local rank, then resolved local id
-    uint16_t qs[kEmitTile];                     // target block of each entry
+template <typename CurT>
+struct EmitWarpSmem {
+    CurT cur[kMaxBlocks];      // next unused index into T_q, per target block
+    CurT item[kEmitRun];       // slot index i, then the resolved local id
+    uint16_t qs[kEmitRun];     // target block of each entry of the run
 };
 
-template <typename Id>
-__global__ void __launch_bounds__(kEmitThreads, 2) pba_emit_kernel(
+template <typename Id, bool kFast>
+__global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const __grid_constant__ PbaGeom g, const uint16_t* __restrict__ A,
     const uint64_t* __restrict__ off, const uint64_t* __restrict__ R,
-    const FastDiv* __restrict__ divR, Id* __restrict__ out)
+    const FastDiv* __restrict__ divR, const QRecip* __restrict__ recip,
+    const uint32_t* __restrict__ wide_flag, Id* __restrict__ out)
 {
+    using CurT = typename std::conditional<kFast, uint32_t, uint64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    EmitSmem& sm = *reinterpret_cast<EmitSmem*>(smem_raw);
-    const uint32_t p = blockIdx.y, sgm = blockIdx.x;
+    if ((*wide_flag == 0) != kFast) return;   // the other variant does the work
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t p = blockIdx.y;
+    const uint32_t sw = blockIdx.x * kEmitWarps + wid;
+    if (sw >= g.S) return;                   // no block-wide barrier follows
+    EmitWarpSmem<CurT>& ws = reinterpret_cast<EmitWarpSmem<CurT>*>(smem_raw)[wid];
     const uint32_t B = g.B;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint16_t* Ap = A + (uint64_t)p * g.A_stride;
-    const uint64_t lo = (uint64_t)sgm * g.seg_len;
+    const uint64_t lo = (uint64_t)sw * g.seg_len;
     const uint64_t hi = (lo + g.seg_len < g.N_e) ? lo + g.seg_len : g.N_e;
     const uint64_t out_block = (uint64_t)p * (g.e0 + g.N_e);
     const uint64_t src_base = (uint64_t)p * g.span + g.n0;
 
-    const uint64_t* offrow = off + ((uint64_t)p * g.S + sgm) * B;
-    for (uint32_t q = threadIdx.x; q < B; q += blockDim.x) {
-        sm.cur[q] = offrow[q];
-        sm.R[q] = R[q];
-        const FastDiv d = divR[q];
-        sm.mul[q] = d.mul;
-        sm.sh[q] = pack_shifts(d);
-        for (int x = 0; x <= kEmitWarps; ++x) sm.wcnt[x][q] = 0;
+    const uint64_t* offrow = off + ((uint64_t)p * g.S + sw) * B;
+    for (uint32_t q = lane; q < B; q += 32) ws.cur[q] = (CurT)offrow[q];
+    if (sw == 0) {
+        const uint64_t e0 = g.e0, base_id = (uint64_t)p * g.span;
+        for (uint64_t e = lane; e < e0; e += 32)
+            store_pair(out, out_block + e, base_id + seed_endpoint(e, 0, g.n0),
+                       base_id + seed_endpoint(e, 1, g.n0));
     }
-    if (sgm == 0) write_seed_edges(out, out_block, (uint64_t)p * g.span, g.n0);
-    __syncthreads();
+    __syncwarp();
 
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (uint64_t base = lo; base < hi; base += kEmitTile) {
-        // 1. stable rank within each warp's contiguous run of 32*ITEMS entries
+    for (uint64_t base = lo; base < hi; base += kEmitRun) {
+        // rank: the run's block ids are loaded before the first match
+        uint32_t qv[kEmitItems];
+#pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
-            const uint32_t t = wid * (32 * kEmitItems) + r * 32 + lane;
-            const uint64_t j = base + t;
-            const uint32_t q = (j < hi) ? Ap[j] : 0xFFFFu;
+            const uint64_t j = base + r * 32 + lane;
+            qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
+        }
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r) {
+            const uint32_t q = qv[r];
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, q);
-            uint32_t prev = 0;
-            if (q != 0xFFFFu) prev = sm.wcnt[wid][q];
+            CurT prev = 0;
+            if (q != 0xFFFFu) prev = ws.cur[q];
             __syncwarp();
-            if (q != 0xFFFFu && (peers & lt_mask) == 0) sm.wcnt[wid][q] = (uint16_t)(prev + __popc(peers));
+            if (q != 0xFFFFu && (peers & lt) == 0) ws.cur[q] = prev + __popc(peers);
             __syncwarp();
-            sm.item[t] = prev + __popc(peers & lt_mask);
-            sm.qs[t] = (uint16_t)q;
+            ws.item[r * 32 + lane] = prev + __popc(peers & lt);
+            ws.qs[r * 32 + lane] = (uint16_t)q;
         }
-        __syncthreads();
-        // 2. exclusive scan of the per-warp counts, per target block
-        for (uint32_t q = threadIdx.x; q < B; q += blockDim.x) {
-            uint32_t acc = 0;
-            for (int x = 0; x < kEmitWarps; ++x) {
-                const uint32_t c = sm.wcnt[x][q];
-                sm.wcnt[x][q] = (uint16_t)acc;
-                acc += c;
-            }
-            sm.wcnt[kEmitWarps][q] = (uint16_t)acc;
-        }
-        __syncthreads();
-        // 3. resolve T_q[i] for every entry the thread owns
+        __syncwarp();
+        // chains: a lane that finishes an entry takes the next unclaimed one
         {
-            int k = 0;
-            uint32_t t = wid * (32 * kEmitItems) + lane;
-            uint64_t cur = 0;
-            uint32_t q = 0;
+            uint32_t k = lane, next = 32, q = 0;
+            bool active = true, fresh = true;
+            CurT cur = 0;
+            QRecip c{0, 0, 0, 0};
             QDiv qd;
-            bool fresh = true;
-            while (k < kEmitItems) {
-                if (fresh) {
-                    q = sm.qs[t];
-                    if (q == 0xFFFFu) {
-                        ++k;
-                        t += 32;
-                        continue;
+            qd.R = 0;
+            qd.d = FastDiv{0, 0, 0};
+            while (__any_sync(0xFFFFFFFFu, active)) {
+                bool done = false;
+                if (active) {
+                    if (fresh) {
+                        q = ws.qs[k];
+                        if (q == 0xFFFFu) {
+                            done = true;   // past the end of the segment
+                        } else {
+                            cur = ws.item[k];
+                            if (kFast) {
+                                c = recip[q];
+                            } else {
+                                qd.R = R[q];
+                                qd.d = divR[q];
+                            }
+                            fresh = false;
+                        }
                     }
-                    cur = sm.cur[q] + sm.wcnt[wid][q] + sm.item[t];
-                    qd.R = sm.R[q];
-                    qd.d.mul = sm.mul[q];
-                    qd.d.s1 = sm.sh[q] & 0xFFu;
-                    qd.d.s2 = sm.sh[q] >> 8;
-                    fresh = false;
+                    if (!done) {
+                        uint32_t v;
+                        bool fin;
+                        if constexpr (kFast) {
+                            uint32_t c32 = cur;
+                            fin = t_step32(c32, q, c, g, v);
+                            cur = c32;
+                        } else {
+                            uint64_t c64 = cur;
+                            fin = t_step(c64, q, qd, g, v);
+                            cur = c64;
+                        }
+                        if (fin) {
+                            ws.item[k] = v;
+                            done = true;
+                        }
+                    }
                 }
-                uint32_t v;
-                if (t_step(cur, q, qd, g, v)) {
-                    sm.item[t] = v;
-                    ++k;
-                    t += 32;
+                const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+                if (done) {
+                    k = next + __popc(dm & lt);
+                    active = k < kEmitRun;
                     fresh = true;
                 }
+                next += __popc(dm);
             }
         }
-        __syncthreads();
-        // 4. advance the per-block cursors; emit the tile
-        for (uint32_t q = threadIdx.x; q < B; q += blockDim.x) {
-            sm.cur[q] += sm.wcnt[kEmitWarps][q];
-            for (int x = 0; x <= kEmitWarps; ++x) sm.wcnt[x][q] = 0;
-        }
-        const uint32_t n = (uint32_t)((hi - base < kEmitTile) ? hi - base : kEmitTile);
-        const uint64_t e_first = out_block + g.e0 + base;
+        __syncwarp();
+        const uint32_t n = (uint32_t)((hi - base < kEmitRun) ? hi - base : kEmitRun);
         auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
-            s_ = src_base + fdiv(base + t2, g.div_m);
-            d_ = (uint64_t)sm.qs[t2] * g.span + sm.item[t2];
+            s_ = src_base + fdiv32((uint32_t)(base + t2), g.div_m32);
+            d_ = (uint64_t)ws.qs[t2] * g.span + (uint32_t)ws.item[t2];
         };
-        emit_tile(out, e_first, n, edge_at);
-        __syncthreads();
+        emit_run(out, out_block + g.e0 + base, n, lane, edge_at);
+        __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------------------
 // Serial BA (blocks = 1): edge j's target by its own copy chain.
-// grid-stride over tiles of kBaTile edges; block = kBaThreads.
+// Each CTA takes tiles of kBaTile edges; each warp a run of kBaRun edges
+// with pooled chains; targets are staged in smem and leave as vector stores.
 // ---------------------------------------------------------------------------
-template <typename Id>
+template <typename Id, bool kFast>
 __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ PbaGeom g,
                                                         Id* __restrict__ out)
 {
+    constexpr uint32_t kBaRun = BaShape<Id>::run, kBaTile = BaShape<Id>::tile;
     __shared__ __align__(16) Id sDst[kBaTile];
     if (blockIdx.x == 0) write_seed_edges(out, 0, 0, g.n0);
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint64_t N = g.N_e;
     for (uint64_t base = (uint64_t)blockIdx.x * kBaTile; base < N;
          base += (uint64_t)gridDim.x * kBaTile) {
-        int k = 0;
-        uint64_t j = base + threadIdx.x;
-        uint64_t cur = j;
-        while (k < kBaItems) {
-            uint64_t v = 0;
-            if (j >= N || ba_step(cur, g, v)) {
-                sDst[k * kBaThreads + threadIdx.x] = (Id)v;
-                ++k;
-                j += kBaThreads;
-                cur = j;
+        const uint64_t run = base + wid * kBaRun;
+        const uint32_t n_items = run < N ? (uint32_t)((N - run < kBaRun) ? N - run : kBaRun) : 0;
+        uint32_t next = 32, item = lane;
+        uint64_t cur = run + item;
+        uint32_t cur32 = (uint32_t)cur;
+        bool active = item < n_items;
+        while (__any_sync(0xFFFFFFFFu, active)) {
+            bool done = false;
+            if (active) {
+                if (kFast) {
+                    uint32_t v;
+                    done = ba_step32(cur32, g, v);
+                    if (done) sDst[wid * kBaRun + item] = (Id)v;
+                } else {
+                    uint64_t v;
+                    done = ba_step(cur, g, v);
+                    if (done) sDst[wid * kBaRun + item] = (Id)v;
+                }
             }
+            const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+            if (done) {
+                item = next + __popc(dm & lt);
+                cur = run + item;
+                cur32 = (uint32_t)cur;
+                active = item < n_items;
+            }
+            next += __popc(dm);
         }
         __syncthreads();
         const uint32_t n = (uint32_t)((N - base < kBaTile) ? N - base : kBaTile);
         auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
-            s_ = g.n0 + fdiv(base + t2, g.div_m);
+            s_ = g.n0 + (kFast ? fdiv32((uint32_t)(base + t2), g.div_m32) : fdiv(base + t2, g.div_m));
             d_ = (uint64_t)sDst[t2];
         };
         emit_tile(out, g.e0 + base, n, edge_at);
@@ -493,18 +666,18 @@ __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t p1_smem_bytes(const PbaGeom& g)
-{
-    return ((g.P * 2 + 15) & ~15u) + (((size_t)g.B * 4 + 15) & ~(size_t)15) + kP1Tile * 2;
-}
-
 }  // namespace
+
+uint32_t pba_prefix_len(uint64_t N_e) { return (uint32_t)(N_e < kPrefixMax ? N_e : kPrefixMax); }
 
 uint32_t pba_segments(uint64_t N_e, uint32_t B, int sm_count)
 {
-    const uint64_t target = 8ull * (uint64_t)(sm_count > 0 ? sm_count : 1);
+    // about eight waves of warps (32 resident per SM), each warp one segment;
+    // a multiple of kEmitWarps segments per block when the entries allow
+    const uint64_t target = 8ull * 32ull * (uint64_t)(sm_count > 0 ? sm_count : 1);
     uint64_t S = (target + B - 1) / B;
-    const uint64_t max_s = (N_e + kP1Tile - 1) / kP1Tile;
+    S = (S + kEmitWarps - 1) / kEmitWarps * kEmitWarps;
+    const uint64_t max_s = (N_e + kGranule - 1) / kGranule;
     if (S > max_s) S = max_s;
     if (S < 1) S = 1;
     const uint64_t len = pba_segment_length(N_e, (uint32_t)S);
@@ -515,8 +688,8 @@ uint32_t pba_segments(uint64_t N_e, uint32_t B, int sm_count)
 uint64_t pba_segment_length(uint64_t N_e, uint32_t S)
 {
     const uint64_t per = (N_e + S - 1) / (S ? S : 1);
-    uint64_t len = (per + kP1Tile - 1) / kP1Tile * kP1Tile;
-    return len ? len : kP1Tile;
+    uint64_t len = (per + kGranule - 1) / kGranule * kGranule;
+    return len ? len : kGranule;
 }
 
 PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S)
@@ -533,6 +706,10 @@ PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S)
     o += align256((size_t)B * 8);
     w.off_magic = o;
     o += align256((size_t)B * sizeof(FastDiv));
+    w.off_recip = o;
+    o += align256((size_t)B * sizeof(QRecip));
+    w.off_flag = o;
+    o += 256;
     w.total = o;
     return w;
 }
@@ -540,14 +717,19 @@ PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S)
 cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s)
 {
     const int sms = device_sm_count();
-    const uint64_t tiles = (g.N_e + kBaTile - 1) / kBaTile;
-    const uint64_t full = (uint64_t)sms * (id64 ? 6 : 8);
+    const uint64_t tile = id64 ? BaShape<uint64_t>::tile : BaShape<uint32_t>::tile;
+    const uint64_t tiles = (g.N_e + tile - 1) / tile;
+    const uint64_t full = (uint64_t)sms * 8;
     const int grid = (int)(tiles < full ? (tiles > 0 ? tiles : 1) : full);
+    const bool fast = g.N_e + g.e0 < ((uint64_t)1 << 32);
     TraceScope trace("ba_chain", s);
-    if (id64)
-        ba_kernel<uint64_t><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out);
-    else
-        ba_kernel<uint32_t><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out);
+    if (id64) {
+        if (fast) ba_kernel<uint64_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out);
+        else ba_kernel<uint64_t, false><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out);
+    } else {
+        if (fast) ba_kernel<uint32_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out);
+        else ba_kernel<uint32_t, false><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out);
+    }
     return cudaGetLastError();
 }
 
@@ -561,47 +743,68 @@ cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cuda
     uint64_t* off = (uint64_t*)(ws + L.off_off);
     uint64_t* R = (uint64_t*)(ws + L.off_R);
     FastDiv* divR = (FastDiv*)(ws + L.off_magic);
+    QRecip* recip = (QRecip*)(ws + L.off_recip);
+    uint32_t* wide = (uint32_t*)(ws + L.off_flag);
     cudaError_t err;
 
+    const size_t smem_fast = kEmitWarps * sizeof(EmitWarpSmem<uint32_t>);
+    const size_t smem_wide = kEmitWarps * sizeof(EmitWarpSmem<uint64_t>);
     static bool attrs_set = false;
     if (!attrs_set) {
         cudaFuncSetAttribute(pba_prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kPrefixMax * 2));
-        cudaFuncSetAttribute(pba_phase1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kPrefixMax * 2 + kMaxBlocks * 4 + kP1Tile * 2 + 64));
-        cudaFuncSetAttribute(pba_emit_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(EmitSmem));
-        cudaFuncSetAttribute(pba_emit_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(EmitSmem));
+                             (int)(kPrefixMax * 2 + kMaxBlocks * 4));
+        cudaFuncSetAttribute(pba_emit_kernel<uint32_t, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast);
+        cudaFuncSetAttribute(pba_emit_kernel<uint64_t, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast);
+        cudaFuncSetAttribute(pba_emit_kernel<uint32_t, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide);
+        cudaFuncSetAttribute(pba_emit_kernel<uint64_t, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide);
         attrs_set = true;
     }
+    cudaMemsetAsync(cnt, 0, (size_t)g.B * g.S * g.B * 4, s);
+    cudaMemsetAsync(wide, 0, 4, s);
     if (g.N_e > 0) {
         {
             TraceScope trace("pba_prefix", s);
-            pba_prefix_kernel<<<g.B, kP1Threads, g.P * 2, s>>>(g, A);
+            const size_t smem = ((size_t)g.P * 2 + 15) / 16 * 16 + (size_t)g.B * 4;
+            pba_prefix_kernel<<<g.B, kPrefixThreads, smem, s>>>(g, A, cnt);
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        {
-            TraceScope trace("pba_phase1", s);
-            pba_phase1_kernel<<<dim3(g.S, g.B), kP1Threads, p1_smem_bytes(g), s>>>(g, A, cnt);
+        TraceScope trace("pba_phase1", s);
+        for (uint64_t lvl = g.P; lvl < g.N_e;) {
+            const uint64_t hi = (2 * lvl < g.N_e) ? 2 * lvl : g.N_e;
+            const uint32_t chunks = (uint32_t)((hi - lvl + kPassChunk - 1) / kPassChunk);
+            pba_pass_kernel<<<dim3(chunks, g.B), kPassThreads, (size_t)g.B * 4, s>>>(
+                g, (uint32_t)lvl, (uint32_t)hi, A, cnt);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            lvl = hi;
         }
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    } else {
-        cudaMemsetAsync(cnt, 0, (size_t)g.B * g.S * g.B * 4, s);
     }
     {
         TraceScope trace("pba_scan", s);
-        pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(cnt, off, R, divR, g.B, g.B * g.S);
+        pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(cnt, off, R, divR, recip, (uint32_t)g.n_b,
+                                                          g.B, g.B * g.S, g.e0, wide);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const dim3 grid(g.S, g.B);
+    const dim3 grid((g.S + kEmitWarps - 1) / kEmitWarps, g.B);
+    // every R_q + e0 < 2^32 is certain when all entries together are fewer
+    const bool surely_fast = (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);
     TraceScope trace("pba_emit", s);
-    if (id64)
-        pba_emit_kernel<uint64_t><<<grid, kEmitThreads, sizeof(EmitSmem), s>>>(g, A, off, R, divR,
-                                                                              (uint64_t*)d_out);
-    else
-        pba_emit_kernel<uint32_t><<<grid, kEmitThreads, sizeof(EmitSmem), s>>>(g, A, off, R, divR,
-                                                                              (uint32_t*)d_out);
+    if (id64) {
+        pba_emit_kernel<uint64_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
+            g, A, off, R, divR, recip, wide, (uint64_t*)d_out);
+        if (!surely_fast)
+            pba_emit_kernel<uint64_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
+                g, A, off, R, divR, recip, wide, (uint64_t*)d_out);
+    } else {
+        pba_emit_kernel<uint32_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
+            g, A, off, R, divR, recip, wide, (uint32_t*)d_out);
+        if (!surely_fast)
+            pba_emit_kernel<uint32_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
+                g, A, off, R, divR, recip, wide, (uint32_t*)d_out);
+    }
     return cudaGetLastError();
 }
 

@@ -11,29 +11,40 @@ namespace pgen {
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each
 // multiplying words 0 and 2 by the Philox constants (32x32 -> 64), XORing
-// the high halves into the other two words together with the round key;
-// the key advances by the Weyl constants between rounds. The key is uniform
-// across a launch, so its schedule lives in uniform registers.
+// the high halves into the other two words together with the round key.
+// The round keys (the seed key advanced by the Weyl constants once per
+// round) are computed on the host, so inside a kernel they are plain
+// constant-bank operands of the XORs.
 struct Key {
-    uint32_t k0, k1;
+    uint32_t k0[10], k1[10];
 };
 
-__device__ __forceinline__ uint4 philox(uint4 c, Key key)
+__host__ __device__ inline Key make_key(uint64_t seed)
 {
-    uint32_t k0 = key.k0, k1 = key.k1;
+    Key k;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = a;
+        k.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const Key& key)
+{
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
         const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ key.k0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ key.k1[r], (uint32_t)p0);
     }
     return c;
 }
 
-__device__ __forceinline__ uint4 draw(uint64_t idx, uint32_t stream, uint32_t tag, Key key)
+__device__ __forceinline__ uint4 draw(uint64_t idx, uint32_t stream, uint32_t tag, const Key& key)
 {
     return philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), stream, tag), key);
 }
@@ -62,6 +73,42 @@ __host__ __device__ __forceinline__ uint64_t fdiv(uint64_t n, const FastDiv& f)
     const uint64_t t = (uint64_t)(((unsigned __int128)f.mul * n) >> 64);
 #endif
     return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// floor(n / d) for 32-bit n (same method with 32-bit words).
+struct FastDiv32 {
+    uint32_t mul, s1, s2;
+};
+
+__host__ __device__ __forceinline__ uint32_t fdiv32(uint32_t n, const FastDiv32& f)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.mul, n);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)f.mul * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+__host__ inline FastDiv32 make_fastdiv32(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && ((uint64_t)1 << l) < d) ++l;
+    FastDiv32 f;
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 0 ? l - 1 : 0;
+    const uint64_t hi = ((uint64_t)1 << l) - d;   // < d
+    f.mul = (uint32_t)((hi << 32) / d + 1);
+    return f;
+}
+
+// Uniform integer in [0, R) for R < 2^32: the same value as uniform64 (the
+// high 64 bits of the 96-bit product), from two 32x32->64 multiplies.
+__device__ __forceinline__ uint32_t uniform32(uint32_t w0, uint32_t w1, uint32_t R)
+{
+    const uint64_t hi = (uint64_t)w1 * R;
+    const uint64_t lo = (uint64_t)w0 * R;
+    return (uint32_t)((hi + (lo >> 32)) >> 32);
 }
 
 // Builds the multiplier for divisor d >= 1 (host or device; the device path

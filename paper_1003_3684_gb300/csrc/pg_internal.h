@@ -45,18 +45,21 @@ struct PbaGeom {
     uint32_t m, B, W, n0;
     uint32_t coin_on, coin_thr;    // inter-faction coin: w2 < coin_thr
     Key key;
-    uint32_t S;                    // segments per block
-    uint64_t seg_len;              // entries per segment (multiple of the tile)
+    uint32_t S;                    // segments per block (one emit warp each)
+    uint64_t seg_len;              // entries per segment (a multiple of 16384)
     uint32_t P;                    // phase-1 prefix kept in shared memory
+    uint32_t nb_shift;             // log2(n_b) when n_b is a power of two, else 0xffffffff
     FastDiv div_m, div_nb;
+    FastDiv32 div_m32;             // j div m for j < 2^32
 };
 
 // Workspace layout for B > 1 (all offsets 256-byte aligned).
 struct PbaWorkspace {
-    size_t off_A, off_cnt, off_off, off_R, off_magic, total;
+    size_t off_A, off_cnt, off_off, off_R, off_magic, off_recip, off_flag, total;
 };
 PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S);
 uint32_t pba_segments(uint64_t N_e, uint32_t B, int sm_count);
+uint32_t pba_prefix_len(uint64_t N_e);
 uint64_t pba_segment_length(uint64_t N_e, uint32_t S);
 
 cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s);

@@ -77,10 +77,7 @@ size_t pg_trace_dump(char* buf, size_t len)
         auto& v = agg[r.name];
         v.first += 1;
         v.second += ms;
-        g_pool.push_back(r.a);
-        g_pool.push_back(r.b);
     }
-    g_recs.clear();
     std::string out = "{";
     bool first = true;
     for (const auto& kv : agg) {
@@ -91,11 +88,13 @@ size_t pg_trace_dump(char* buf, size_t len)
         first = false;
     }
     out += "}";
-    if (buf && len > 0) {
-        const size_t n = out.size() < len - 1 ? out.size() : len - 1;
-        std::memcpy(buf, out.data(), n);
-        buf[n] = '\0';
+    if (!buf || len < out.size() + 1) return out.size() + 1;   // size query: keep the record
+    std::memcpy(buf, out.data(), out.size() + 1);
+    for (const Rec& r : g_recs) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
     }
+    g_recs.clear();
     return out.size() + 1;
 }
 
