@@ -141,8 +141,18 @@ def oracle_sample(name: str, cfg: dict, budget_s: float):
     """
     import oracle as o
     t_total, edges_total, samples = 0.0, 0, 0
+    if cfg["kind"] == "batch":
+        jobs = W.batch_jobs(cfg["n_jobs"], seed=cfg["seed"])
     while samples == 0 or t_total < budget_s:
-        if cfg["kind"] == "pba" and cfg["blocks"] > 1:
+        if cfg["kind"] == "batch":
+            j = jobs[(samples * 97) % len(jobs)]
+            t0 = time.perf_counter()
+            e = (o.ba(j["n"], j["m"], j["n0"], j["seed"]) if j["kind"] == "pba"
+                 else o.kron(j["initiator"], j["k"], j["n_edges"], j["seed"]))
+            t_total += time.perf_counter() - t0
+            edges_total += e.shape[0]
+            desc = "oracle on jobs of the batch (every 97th job)"
+        elif cfg["kind"] == "pba" and cfg["blocks"] > 1:
             B = 2
             n = B * (cfg["n"] // cfg["blocks"])
             t0 = time.perf_counter()
@@ -201,6 +211,179 @@ def run_reference(args, rank: int, world: int):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def batch_work(jobs):
+    """Algorithmic int32 ops of a batch (one draw per edge, as KERNEL_WORK)."""
+    ops = 0
+    for j in jobs:
+        if j["kind"] == "pba":
+            ops += j["n"] * j["m"] * KERNEL_WORK["ba_chain"]["ops"]
+        else:
+            ops += j["n_edges"] * kron_work(j["k"])["ops"]
+    return ops
+
+
+def run_batch(args, rank: int, world: int, local_rank: int):
+    """Batched workload: one CUDA-graph replay of the persistent batch kernel
+    per step, against the same jobs launched one graph at a time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1003_3684_gb300 import autotune
+    from paper_1003_3684_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1003_3684_gb300 as pg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = W.CONFIGS[args.workload]
+    jobs = W.batch_jobs(cfg["n_jobs"], seed=cfg["seed"] + rank)
+    if args.batch_jobs:
+        jobs = jobs[:args.batch_jobs // 2] + jobs[cfg["n_jobs"] // 2:][:args.batch_jobs // 2]
+    total = sum(j["n"] * j["m"] + j["n0"] * (j["n0"] - 1) // 2 if j["kind"] == "pba"
+                else j["n_edges"] for j in jobs)
+    free, _ = torch.cuda.mem_get_info()
+    # waves: split the jobs so that one wave's arena fits in free memory
+    waves = 1
+    while total * 8 / waves > 0.8 * free and waves < 8:
+        waves += 1
+    chunks = [jobs[i::waves] for i in range(waves)]
+    tune = autotune.tune_batch(chunks[0], reps=1, tiles=(2048, 4096, 8192), fractions=(1.0,))
+    plans = [pg.BatchPlan(c, tile_edges=tune["tile_edges"]) for c in chunks]
+    # one arena serves both arms; the per-graph arm places every job at an
+    # even edge offset (16-byte aligned output, as gen_pba/gen_kronecker need)
+    arena = torch.empty((max(p.total_edges for p in plans) + len(jobs) + 2, 2), dtype=torch.int32,
+                        device=dev)
+    ws = torch.empty(pg.pg_batch_workspace_size(), dtype=torch.uint8, device=dev)
+    graphs = []
+    for p in plans:
+        pg.gen_batch(p, arena=arena, workspace=ws, grid_ctas=tune["grid_ctas"])
+        torch.cuda.synchronize()
+        gph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gph):
+            pg.gen_batch(p, arena=arena, workspace=ws, grid_ctas=tune["grid_ctas"])
+        graphs.append(gph)
+
+    def step():
+        for gph in graphs:
+            gph.replay()
+
+    # per-graph baseline: every job its own gen_pba / gen_kronecker call
+    def per_graph():
+        for c, p in zip(chunks, plans):
+            a = 0
+            for i, j in enumerate(c):
+                size = int(p.offsets[i + 1] - p.offsets[i])
+                if j["kind"] == "pba":
+                    pg.gen_pba(j["n"], j["m"], 1, j["n0"], 1, 0.0, j["seed"],
+                               out=arena[a:a + size])
+                else:
+                    pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"],
+                                     out=arena[a:a + size])
+                a += size + (size & 1)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    per_graph()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    pg.pg_trace_dump()
+    pg.pg_trace_enable(True)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    pg.pg_trace_enable(False)
+    kernels = pg.pg_trace_dump()
+    ms = ev0.elapsed_time(ev1)
+    # per-graph launches, timed the same way
+    pg_steps = max(1, min(args.steps, 3))
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(pg_steps):
+        per_graph()
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    ms_pg = ev2.elapsed_time(ev3) / pg_steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = total * args.steps * world / (ms_max / 1000.0)
+    peaks = load_peaks()
+    sms = pg.pg_device_sm_count()
+    alu_peak = sms * 128 * peaks["sm_max_mhz"] * 1e6
+    nl, tot_ms = kernels.get("batch_persistent", (1, ms_max))
+    per_launch = tot_ms / nl / 1000.0
+    ops = batch_work(jobs) / waves
+    roof = dict(bound="alu", kernel="batch_persistent", achieved=ops / per_launch / 1e12,
+                peak=alu_peak / 1e12, unit="Tops/s (int32 lane ops)",
+                frac=ops / per_launch / alu_peak, traffic=None,
+                hbm=dict(achieved=total * 8 / waves / per_launch / 1e9, peak=peaks["hbm_gbs"],
+                         unit="GB/s", frac=total * 8 / waves / per_launch / (peaks["hbm_gbs"] * 1e9)),
+                ms_per_launch=per_launch * 1000.0,
+                peak_source=f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz")
+    line = dict(metric="edges/sec", value=value, unit="edges/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
+                config=dict(workload=args.workload, n_jobs=len(jobs), edges_per_step=total,
+                            waves=waves, tile_edges=tune["tile_edges"],
+                            grid_ctas=tune["grid_ctas"], autotune_cached=tune["cached"],
+                            launch="CUDA graph of one persistent kernel per wave",
+                            l2=f"no flush: each step writes {total * 8 / 1e9:.1f} GB"),
+                per_graph=dict(value=total * world / (ms_pg / 1000.0), unit="edges/s",
+                               ms_per_step=ms_pg, launches=len(jobs),
+                               speedup_batched=ms_pg / (ms_max / args.steps)),
+                roofline=roof, gpu_launches=sum(v[0] for v in kernels.values()),
+                kernels={kk: [v[0], round(v[1], 4)] for kk, v in kernels.items()},
+                clocks=clocks)
+    if not args.no_e2e:
+        # end to end: the batch plus the device-to-host copy of the arena
+        out_bytes = total * 8 // waves
+        chunk = min(out_bytes, 4 << 30)
+        host = torch.empty(chunk, dtype=torch.uint8, pin_memory=True)
+        flat = arena.view(torch.uint8).view(-1)
+        t0 = time.perf_counter()
+        for gph in graphs:
+            gph.replay()
+            for off in range(0, out_bytes, chunk):
+                n = min(chunk, out_bytes - off)
+                host[:n].copy_(flat[off:off + n], non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        line["e2e"] = dict(value=total / dt, unit="edges/s", h2d_bytes_per_step=0,
+                           d2h_bytes_per_step=total * 8, steps=1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as o
+        t_cpu, e_cpu, i = 0.0, 0, 0
+        while t_cpu < args.cpu_budget and i < len(jobs):
+            j = jobs[(i * 97) % len(jobs)]
+            t0 = time.perf_counter()
+            if j["kind"] == "pba":
+                e_cpu += o.ba(j["n"], j["m"], j["n0"], j["seed"]).shape[0]
+            else:
+                e_cpu += o.kron(j["initiator"], j["k"], j["n_edges"], j["seed"]).shape[0]
+            t_cpu += time.perf_counter() - t0
+            i += 1
+        line["cpu_baseline"] = dict(value=e_cpu / t_cpu, unit="edges/s", cores=1, kind="oracle",
+                                    sample=f"{i} jobs of the batch (every 97th), {t_cpu:.1f} s")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_pgen(args, rank: int, world: int, local_rank: int):
     import torch
     import torch.distributed as dist
@@ -410,6 +593,8 @@ def main():
     ap.add_argument("--blocks", type=int, default=0,
                     help="PBA only: run this many blocks of the workload's block size "
                          "(a smaller case, e.g. for profiler captures)")
+    ap.add_argument("--batch-jobs", type=int, default=0,
+                    help="batch workload only: use this many of its jobs (a smaller case)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     args = ap.parse_args()
@@ -418,6 +603,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if W.CONFIGS[args.workload]["kind"] == "batch":
+        return run_batch(args, rank, world, local_rank)
     return run_pgen(args, rank, world, local_rank)
 
 

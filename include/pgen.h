@@ -147,6 +147,52 @@ pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertice
                        size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched generation: many independent graphs in one persistent launch.
+ *
+ * A job is a serial BA graph (gen_pba with blocks = 1: n new vertices, m
+ * edges each, seed clique K_{n0}) or a stochastic Kronecker graph (as
+ * gen_kronecker with PG_KRON_STOCHASTIC). Job i's edges are exactly those the
+ * single-graph call with the same arguments writes, placed at
+ * h_edge_offsets[i] in one shared output arena.
+ *
+ * pg_batch_plan (host only) validates the jobs and writes a plan of
+ * pg_batch_plan_size() bytes into h_plan: per-job records (parameters,
+ * Philox round keys, thresholds, arena offset) and a work-item table that
+ * cuts every job into tiles of tile_edges edges (64 <= tile_edges <= 8192,
+ * a multiple of 64). h_edge_offsets (n_jobs + 1 entries, may be NULL)
+ * receives each job's first edge and the total; h_n_items the number of
+ * work items. 32-bit chain arithmetic is used, so BA jobs need
+ * n*m + e0 < 2^32. At most 8192 jobs.
+ *
+ * gen_batch launches one persistent kernel over a copy of the plan in
+ * device memory (d_plan, 16-byte aligned): resident CTAs claim work items
+ * from a counter in d_ws (pg_batch_workspace_size() bytes, reset by the
+ * call) until none are left. grid_ctas = 0 picks one wave of resident CTAs.
+ * The call is stream-ordered with no host synchronisation and can be
+ * captured in a CUDA graph; a replay regenerates the same edges.
+ * ---------------------------------------------------------------------- */
+typedef enum { PG_JOB_BA = 0, PG_JOB_KRON = 1 } pg_job_kind;
+
+typedef struct {
+    uint32_t kind;            /* pg_job_kind */
+    uint32_t m;               /* BA: edges per new vertex */
+    uint32_t n0;              /* BA: seed clique size; KRON: initiator order (<= 16) */
+    uint32_t k;               /* KRON: levels */
+    uint64_t n;               /* BA: new vertices; KRON: edge count */
+    uint64_t seed;            /* Philox key */
+    const double* initiator;  /* KRON: host, n0*n0 doubles, row-major */
+} pg_job;
+
+size_t pg_batch_plan_size(const pg_job* jobs, uint32_t n_jobs);
+size_t pg_batch_workspace_size(void);
+pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges, pg_idwidth w,
+                        void* h_plan, size_t plan_size, uint64_t* h_edge_offsets,
+                        uint64_t* h_n_items);
+pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_arena,
+                    uint64_t cap_edges, uint64_t total_edges, uint32_t grid_ctas, void* d_ws,
+                    size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Kernel timing trace (profiling aid, not part of the method).
  * pg_trace_enable(1): from then on every kernel the library launches is
  * bracketed by two CUDA events recorded on the launch's stream.

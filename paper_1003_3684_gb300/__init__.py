@@ -236,3 +236,96 @@ def pg_trace_dump() -> dict:
     buf = C.create_string_buffer(need + 64)
     lib().pg_trace_dump(buf, len(buf))
     return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+# --------------------------------------------------------------------------
+# Batched generation (one persistent launch for many graphs)
+# --------------------------------------------------------------------------
+PG_JOB_BA, PG_JOB_KRON = 0, 1
+
+
+class _PgJob(C.Structure):
+    _fields_ = [("kind", u32), ("m", u32), ("n0", u32), ("k", u32), ("n", u64), ("seed", u64),
+                ("initiator", vp)]
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.pg_batch_plan_size.argtypes = [vp, u32]
+        L.pg_batch_plan_size.restype = sz
+        L.pg_batch_workspace_size.argtypes = []
+        L.pg_batch_workspace_size.restype = sz
+        L.pg_batch_plan.argtypes = [vp, u32, u32, i32, vp, sz, vp, vp]
+        L.pg_batch_plan.restype = i32
+        L.gen_batch.argtypes = [vp, u32, i32, vp, u64, u64, u32, vp, sz, vp]
+        L.gen_batch.restype = i32
+        L._batch_ready = True
+    return L
+
+
+class BatchPlan:
+    """Host-built plan of a batch of jobs, copied to the device.
+
+    ``jobs`` is a list of dicts: ``dict(kind="pba", n=..., m=..., n0=..., seed=...)``
+    (serial BA, i.e. gen_pba with blocks = 1) or ``dict(kind="kron",
+    initiator=..., k=..., n_edges=..., seed=...)`` (stochastic Kronecker).
+    ``offsets[i]`` is job i's first edge in the arena, ``offsets[-1]`` the total.
+    """
+
+    def __init__(self, jobs, tile_edges: int = 4096, id64: bool = False, device="cuda"):
+        import numpy as np
+        import torch
+        L = _batch_lib()
+        n = len(jobs)
+        arr = (_PgJob * max(n, 1))()
+        self._keep = []
+        for i, j in enumerate(jobs):
+            if j["kind"] == "pba":
+                if j.get("blocks", 1) != 1:
+                    raise ValueError("batched PBA jobs are serial BA (blocks = 1)")
+                arr[i] = _PgJob(PG_JOB_BA, j["m"], j.get("n0") or j["m"] + 1, 0, j["n"], j["seed"],
+                                None)
+            elif j["kind"] == "kron":
+                P = _initiator(j["initiator"])
+                self._keep.append(P)
+                arr[i] = _PgJob(PG_JOB_KRON, 0, P.shape[0], j["k"], j["n_edges"], j["seed"],
+                                P.ctypes.data_as(vp))
+            else:
+                raise ValueError(f"unknown job kind {j['kind']!r}")
+        size = int(L.pg_batch_plan_size(C.cast(arr, vp), n))
+        host = np.zeros(max(size, 16), dtype=np.uint8)
+        offsets = np.zeros(n + 1, dtype=np.uint64)
+        n_items = u64(0)
+        st = L.pg_batch_plan(C.cast(arr, vp), n, tile_edges, PG_ID64 if id64 else PG_ID32,
+                             host.ctypes.data_as(vp), host.size, offsets.ctypes.data_as(vp),
+                             C.byref(n_items))
+        _check("pg_batch_plan", st)
+        self.n_jobs = n
+        self.tile_edges = tile_edges
+        self.id64 = id64
+        self.offsets = offsets
+        self.total_edges = int(offsets[-1])
+        self.n_items = int(n_items.value)
+        self.d_plan = torch.from_numpy(host).to(device)
+        self.device = self.d_plan.device
+
+
+def pg_batch_workspace_size() -> int:
+    return int(_batch_lib().pg_batch_workspace_size())
+
+
+def gen_batch(plan: "BatchPlan", arena=None, workspace=None, grid_ctas: int = 0, stream=None):
+    """Run a BatchPlan in one persistent launch; returns the (total, 2) arena."""
+    import torch
+    L = _batch_lib()
+    dtype = torch.int64 if plan.id64 else torch.int32
+    if arena is None:
+        arena = _empty((max(plan.total_edges, 1), 2), dtype, plan.device)
+    if workspace is None:
+        workspace = _empty(pg_batch_workspace_size(), torch.uint8, plan.device)
+    st = L.gen_batch(_ptr(plan.d_plan), plan.n_jobs, PG_ID64 if plan.id64 else PG_ID32,
+                     _ptr(arena), arena.shape[0], plan.total_edges, grid_ctas, _ptr(workspace),
+                     workspace.numel(), _stream(stream))
+    _check("gen_batch", st)
+    return arena[:plan.total_edges]

@@ -1,0 +1,418 @@
+// Batched generation: many independent graphs in one persistent launch.
+//
+// The host turns a list of jobs (serial BA or stochastic Kronecker graphs of
+// any size) into a plan: one record per job with its parameters, its Philox
+// round keys, its Kronecker thresholds, where its edges start in a shared
+// output arena, and how many work items (tiles of `tile` edges) it has. The
+// kernel's CTAs stay resident; each repeatedly claims the next work item from
+// a device counter (one atomicAdd, never a wait), finds the item's job by a
+// binary search over the per-job first-item table in shared memory, and runs
+// the job's tile with the same arithmetic as the single-graph kernels: pooled
+// copy chains for BA, k-level descent for Kronecker. Small and large jobs
+// thus share the GPU without a launch per graph. The whole call (counter reset
+// + kernel) is stream-ordered and contains no host synchronisation, so it can
+// be captured in a CUDA graph and replayed.
+#include <cmath>
+#include <cstring>
+
+#include "../../include/pgen.h"
+#include "pg_internal.h"
+#include "pg_trace.h"
+
+namespace pgen {
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr uint32_t kBatchWarps = kBatchThreads / 32;
+constexpr uint32_t kMaxTile = 8192;        // staging limit (edges per work item)
+constexpr uint32_t kMaxBatchJobs = 8192;   // first-item table held in smem
+
+struct BatchJob {              // 256 bytes, one per job
+    uint32_t kind, m, n0, k;
+    uint64_t n_units;          // BA: n*m generated edges; KRON: edges
+    uint64_t out_edge;         // first edge of the job in the arena
+    uint64_t e0;               // BA: seed-clique edges (written by tile 0)
+    uint32_t tile;             // edges per work item
+    uint32_t n_zero, n_u;      // KRON thresholds (see KronParams)
+    uint32_t u_off;            // KRON: offset of u[] in the threshold pool (n0 > 2)
+    uint32_t u0, u1, u2, pad;  // KRON n0 = 2 thresholds
+    FastDiv32 div_m;
+    uint32_t pad2;
+    Key key;                   // 80 bytes
+    uint8_t reserved[256 - 80 - 88];
+};
+static_assert(sizeof(BatchJob) == 256, "job record is 256 bytes");
+
+struct PlanHeader {
+    uint32_t n_jobs, n_pool;
+    uint64_t n_items, total_edges;
+    uint64_t off_jobs, off_first, off_pool;
+    uint64_t pad;
+};
+
+size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+size_t plan_bytes(uint32_t n_jobs, uint32_t n_pool)
+{
+    return a16(sizeof(PlanHeader)) + a16((size_t)n_jobs * sizeof(BatchJob)) +
+           a16((size_t)(n_jobs + 1) * 4) + a16((size_t)n_pool * 4);
+}
+
+template <typename Id>
+__device__ __forceinline__ void put_pair(Id* out, uint64_t e, uint64_t s, uint64_t d)
+{
+    out[2 * e] = (Id)s;
+    out[2 * e + 1] = (Id)d;
+}
+
+template <typename Id>
+__device__ __forceinline__ void put_two(Id* out, uint64_t e, uint64_t s0, uint64_t d0, uint64_t s1,
+                                        uint64_t d1)
+{
+    if constexpr (sizeof(Id) == 4) {
+        *reinterpret_cast<uint4*>(out + 2 * e) =
+            make_uint4((uint32_t)s0, (uint32_t)d0, (uint32_t)s1, (uint32_t)d1);
+    } else {
+        ulonglong2* o = reinterpret_cast<ulonglong2*>(out + 2 * e);
+        o[0] = make_ulonglong2(s0, d0);
+        o[1] = make_ulonglong2(s1, d1);
+    }
+}
+
+// One serial-BA link with 32-bit indices (as in the single-graph kernel).
+__device__ __forceinline__ bool ba_link(uint32_t& cur, const BatchJob& J, const Key& key,
+                                        uint32_t& v)
+{
+    const uint32_t sig = fdiv32(cur, J.div_m);
+    const uint4 w = philox(make_uint4(cur, 0u, 0u, 2u), key);
+    const uint32_t X = (uint32_t)J.e0 + sig * J.m;
+    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
+    const uint32_t e = (uint32_t)(s >> 32);
+    const uint32_t side = ((uint32_t)s) >> 31;
+    if (e < (uint32_t)J.e0) {
+        v = seed_endpoint(e, side, J.n0);
+        return true;
+    }
+    const uint32_t e2 = e - (uint32_t)J.e0;
+    if (side == 0) {
+        v = J.n0 + fdiv32(e2, J.div_m);
+        return true;
+    }
+    cur = e2;
+    return false;
+}
+
+__device__ __forceinline__ void kron_level(uint32_t w, uint32_t base, uint32_t u0, uint32_t u1,
+                                           uint32_t u2, uint64_t& row, uint64_t& col)
+{
+    const uint32_t cell = base + (w > u0) + (w > u1) + (w > u2);
+    row = (row << 1) | (cell >> 1);
+    col = (col << 1) | (cell & 1);
+}
+
+__device__ __forceinline__ void kron_edge(const BatchJob& J, const Key& key,
+                                          const uint32_t* pool, uint64_t e, uint64_t& row,
+                                          uint64_t& col)
+{
+    row = 0;
+    col = 0;
+    if (J.n0 == 2) {
+        uint32_t l = 0;
+        for (uint32_t g = 0; l < J.k; ++g, l += 4) {
+            const uint4 w = philox(make_uint4((uint32_t)e, (uint32_t)(e >> 32), g, 3u), key);
+            kron_level(w.x, J.n_zero, J.u0, J.u1, J.u2, row, col);
+            if (l + 1 < J.k) kron_level(w.y, J.n_zero, J.u0, J.u1, J.u2, row, col);
+            if (l + 2 < J.k) kron_level(w.z, J.n_zero, J.u0, J.u1, J.u2, row, col);
+            if (l + 3 < J.k) kron_level(w.w, J.n_zero, J.u0, J.u1, J.u2, row, col);
+        }
+        return;
+    }
+    const uint32_t* u = pool + J.u_off;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (uint32_t l = 0; l < J.k; ++l) {
+        if ((l & 3) == 0)
+            w = philox(make_uint4((uint32_t)e, (uint32_t)(e >> 32), l >> 2, 3u), key);
+        const uint32_t x = (l & 3) == 0 ? w.x : (l & 3) == 1 ? w.y : (l & 3) == 2 ? w.z : w.w;
+        uint32_t lo = 0, hi = J.n_u;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (u[mid] < x) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint32_t cell = J.n_zero + lo;
+        row = row * J.n0 + cell / J.n0;
+        col = col * J.n0 + cell % J.n0;
+    }
+}
+
+template <typename Id>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned char* __restrict__ plan,
+                                                              Id* __restrict__ arena,
+                                                              unsigned long long* __restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PlanHeader& H = *reinterpret_cast<const PlanHeader*>(plan);
+    const BatchJob* jobs = reinterpret_cast<const BatchJob*>(plan + H.off_jobs);
+    const uint32_t* first_g = reinterpret_cast<const uint32_t*>(plan + H.off_first);
+    const uint32_t* pool = reinterpret_cast<const uint32_t*>(plan + H.off_pool);
+    const uint32_t n_jobs = H.n_jobs;
+    const uint64_t n_items = H.n_items;
+
+    Id* sDst = reinterpret_cast<Id*>(smem);                                    // kMaxTile ids
+    uint32_t* first = reinterpret_cast<uint32_t*>(smem + kMaxTile * sizeof(Id));   // n_jobs + 1
+    __shared__ uint32_t s_item, s_job;
+    __shared__ BatchJob sJ;
+
+    for (uint32_t t = threadIdx.x; t <= n_jobs; t += blockDim.x) first[t] = first_g[t];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (;;) {
+        __syncthreads();   // previous item finished with s_item / sJ / sDst
+        if (threadIdx.x == 0) {
+            const unsigned long long it = atomicAdd(counter, 1ull);
+            s_item = it < n_items ? (uint32_t)it : 0xFFFFFFFFu;
+            if (it < n_items) {
+                uint32_t lo = 0, hi = n_jobs;   // last job with first[job] <= it
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (first[mid] <= (uint32_t)it) lo = mid;
+                    else hi = mid;
+                }
+                s_job = lo;
+            }
+        }
+        __syncthreads();
+        if (s_item == 0xFFFFFFFFu) break;
+        for (uint32_t t = threadIdx.x; t < sizeof(BatchJob) / 4; t += blockDim.x)
+            reinterpret_cast<uint32_t*>(&sJ)[t] = reinterpret_cast<const uint32_t*>(&jobs[s_job])[t];
+        __syncthreads();
+        const BatchJob& J = sJ;
+        const Key key = J.key;
+        const uint64_t t0 = (uint64_t)(s_item - first[s_job]) * J.tile;
+        const uint32_t n = (uint32_t)((J.n_units - t0 < J.tile) ? J.n_units - t0 : J.tile);
+
+        if (J.kind == PG_JOB_BA) {
+            if (t0 == 0)
+                for (uint64_t e = threadIdx.x; e < J.e0; e += blockDim.x)
+                    put_pair(arena, J.out_edge + e, seed_endpoint(e, 0, J.n0),
+                             seed_endpoint(e, 1, J.n0));
+            // warps take runs of the tile; lanes pool their chains
+            const uint32_t per = (n + kBatchWarps - 1) / kBatchWarps;
+            const uint32_t r0 = wid * per < n ? wid * per : n;
+            const uint32_t r1 = r0 + per < n ? r0 + per : n;
+            const uint32_t n_items_w = r1 - r0;
+            uint32_t next = 32, item = lane;
+            uint32_t cur = (uint32_t)(t0 + r0 + item);
+            bool active = item < n_items_w;
+            while (__any_sync(0xFFFFFFFFu, active)) {
+                bool done = false;
+                if (active) {
+                    uint32_t v;
+                    done = ba_link(cur, J, key, v);
+                    if (done) sDst[r0 + item] = (Id)v;
+                }
+                const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+                if (done) {
+                    item = next + __popc(dm & lt);
+                    cur = (uint32_t)(t0 + r0 + item);
+                    active = item < n_items_w;
+                }
+                next += __popc(dm);
+            }
+            __syncthreads();
+            const uint64_t e_first = J.out_edge + J.e0 + t0;
+            const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
+            if (head && threadIdx.x == 0)
+                put_pair(arena, e_first, J.n0 + fdiv32((uint32_t)t0, J.div_m), (uint64_t)sDst[0]);
+            for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
+                const uint64_t s0 = J.n0 + fdiv32((uint32_t)(t0 + t2), J.div_m);
+                if (t2 + 1 < n)
+                    put_two(arena, e_first + t2, s0, (uint64_t)sDst[t2],
+                            J.n0 + fdiv32((uint32_t)(t0 + t2 + 1), J.div_m), (uint64_t)sDst[t2 + 1]);
+                else
+                    put_pair(arena, e_first + t2, s0, (uint64_t)sDst[t2]);
+            }
+        } else {
+            const uint64_t e_first = J.out_edge + t0;
+            const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
+            if (head && threadIdx.x == 0) {
+                uint64_t r, c;
+                kron_edge(J, key, pool, t0, r, c);
+                put_pair(arena, e_first, r, c);
+            }
+            for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
+                uint64_t r0, c0;
+                kron_edge(J, key, pool, t0 + t2, r0, c0);
+                if (t2 + 1 < n) {
+                    uint64_t r1, c1;
+                    kron_edge(J, key, pool, t0 + t2 + 1, r1, c1);
+                    put_two(arena, e_first + t2, r0, c0, r1, c1);
+                } else {
+                    put_pair(arena, e_first + t2, r0, c0);
+                }
+            }
+        }
+    }
+}
+
+bool kron_thresholds_host(const double* P, uint32_t n0, uint64_t* T)
+{
+    const uint32_t cells = n0 * n0;
+    double S = 0.0;
+    for (uint32_t c = 0; c < cells; ++c) {
+        if (!(P[c] >= 0.0) || !std::isfinite(P[c])) return false;
+        S += P[c];
+    }
+    if (!(S > 0.0) || !std::isfinite(S)) return false;
+    double cum = 0.0;
+    for (uint32_t c = 0; c + 1 < cells; ++c) {
+        cum += P[c];
+        T[c] = (uint64_t)std::nearbyint(std::ldexp(cum / S, 32));
+    }
+    return true;
+}
+
+}  // namespace
+
+}  // namespace pgen
+
+using namespace pgen;
+
+extern "C" {
+
+size_t pg_batch_plan_size(const pg_job* jobs, uint32_t n_jobs)
+{
+    uint64_t pool = 0;
+    for (uint32_t i = 0; jobs && i < n_jobs; ++i)
+        if (jobs[i].kind == PG_JOB_KRON && jobs[i].n0 > 2 && jobs[i].n0 <= 16)
+            pool += (uint64_t)jobs[i].n0 * jobs[i].n0;
+    return plan_bytes(n_jobs, (uint32_t)pool);
+}
+
+size_t pg_batch_workspace_size(void) { return 256; }
+
+pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges, pg_idwidth w,
+                        void* h_plan, size_t plan_size, uint64_t* h_edge_offsets,
+                        uint64_t* h_n_items)
+{
+    if (!jobs || n_jobs == 0 || n_jobs > kMaxBatchJobs || !h_plan) return PG_EINVAL;
+    if (tile_edges < 64 || tile_edges > kMaxTile || tile_edges % 64 != 0) return PG_EINVAL;
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (plan_size < pg_batch_plan_size(jobs, n_jobs)) return PG_ENOMEM;
+    std::memset(h_plan, 0, plan_size);
+    unsigned char* base = (unsigned char*)h_plan;
+    PlanHeader& H = *(PlanHeader*)base;
+    H.n_jobs = n_jobs;
+    H.off_jobs = a16(sizeof(PlanHeader));
+    H.off_first = H.off_jobs + a16((size_t)n_jobs * sizeof(BatchJob));
+    H.off_pool = H.off_first + a16((size_t)(n_jobs + 1) * 4);
+    BatchJob* J = (BatchJob*)(base + H.off_jobs);
+    uint32_t* first = (uint32_t*)(base + H.off_first);
+    uint32_t* pool = (uint32_t*)(base + H.off_pool);
+    uint64_t edges = 0, items = 0;
+    uint32_t n_pool = 0;
+    const uint64_t id_limit = w == PG_ID32 ? ((uint64_t)1 << 32) : ~(uint64_t)0;
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        const pg_job& q = jobs[i];
+        BatchJob& b = J[i];
+        b.kind = q.kind;
+        b.tile = tile_edges;
+        b.key = make_key(q.seed);
+        b.out_edge = edges;
+        if (q.kind == PG_JOB_BA) {
+            if (q.m < 1 || q.n0 < 2 || q.n0 > 65536) return PG_EINVAL;
+            const unsigned __int128 ne = (unsigned __int128)q.n * q.m;
+            b.e0 = (uint64_t)q.n0 * (q.n0 - 1) / 2;
+            if (ne + b.e0 >= ((unsigned __int128)1 << 32)) return PG_EINVAL;   // 32-bit links
+            if ((uint64_t)q.n0 + q.n > id_limit) return PG_EINVAL;
+            b.m = q.m;
+            b.n0 = q.n0;
+            b.n_units = (uint64_t)ne;
+            b.div_m = make_fastdiv32(q.m);
+            edges += b.e0 + b.n_units;
+        } else if (q.kind == PG_JOB_KRON) {
+            if (!q.initiator || q.n0 < 1 || q.n0 > 16 || q.k < 1 || q.k > 64) return PG_EINVAL;
+            unsigned __int128 nv = 1;
+            for (uint32_t l = 0; l < q.k && nv <= id_limit; ++l) nv *= q.n0;
+            if (nv > id_limit) return PG_EINVAL;
+            uint64_t T[255];
+            if (!kron_thresholds_host(q.initiator, q.n0, T)) return PG_EINVAL;
+            const uint32_t cells = q.n0 * q.n0;
+            uint32_t c = 0;
+            while (c + 1 < cells && T[c] == 0) ++c;
+            b.n_zero = c;
+            uint32_t u[255];
+            uint32_t nu = 0;
+            for (; c + 1 < cells && T[c] < ((uint64_t)1 << 32); ++c) u[nu++] = (uint32_t)(T[c] - 1);
+            b.n_u = nu;
+            b.n0 = q.n0;
+            b.k = q.k;
+            b.n_units = q.n;
+            if (q.n0 == 2) {
+                b.u0 = nu > 0 ? u[0] : 0xFFFFFFFFu;
+                b.u1 = nu > 1 ? u[1] : 0xFFFFFFFFu;
+                b.u2 = nu > 2 ? u[2] : 0xFFFFFFFFu;
+            } else {
+                b.u_off = n_pool;
+                for (uint32_t t = 0; t < nu; ++t) pool[n_pool++] = u[t];
+            }
+            edges += b.n_units;
+        } else {
+            return PG_EINVAL;
+        }
+        first[i] = (uint32_t)items;
+        uint64_t job_items = (b.n_units + tile_edges - 1) / tile_edges;
+        if (job_items == 0 && q.kind == PG_JOB_BA) job_items = 1;   // its seed clique
+        items += job_items;
+        if (items >= 0xFFFFFFFFull) return PG_EINVAL;
+        if (h_edge_offsets) h_edge_offsets[i] = b.out_edge;
+    }
+    first[n_jobs] = (uint32_t)items;
+    H.n_items = items;
+    H.total_edges = edges;
+    H.n_pool = n_pool;
+    if (h_edge_offsets) h_edge_offsets[n_jobs] = edges;
+    if (h_n_items) *h_n_items = items;
+    return PG_OK;
+}
+
+pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_arena,
+                    uint64_t cap_edges, uint64_t total_edges, uint32_t grid_ctas, void* d_ws,
+                    size_t ws_bytes, void* stream)
+{
+    if (!d_plan || n_jobs == 0 || n_jobs > kMaxBatchJobs) return PG_EINVAL;
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (cap_edges < total_edges) return PG_ENOSPC;
+    if (total_edges > 0 && (!d_arena || ((uintptr_t)d_arena & 15))) return PG_EINVAL;
+    if (!d_ws || ws_bytes < pg_batch_workspace_size() || ((uintptr_t)d_ws & 255)) return PG_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t id_bytes = w == PG_ID64 ? 8 : 4;
+    const size_t smem = kMaxTile * id_bytes + (size_t)(n_jobs + 1) * 4;
+    static bool attrs = false;
+    if (!attrs) {
+        cudaFuncSetAttribute(batch_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kMaxTile * 4 + (kMaxBatchJobs + 1) * 4));
+        cudaFuncSetAttribute(batch_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kMaxTile * 8 + (kMaxBatchJobs + 1) * 4));
+        attrs = true;
+    }
+    int per_sm = 0;
+    if (w == PG_ID64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint64_t>, kBatchThreads, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint32_t>, kBatchThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t full = (uint32_t)(device_sm_count() * per_sm);
+    const uint32_t grid = grid_ctas == 0 || grid_ctas > full ? full : grid_ctas;
+    if (cudaMemsetAsync(d_ws, 0, 8, s) != cudaSuccess) return PG_ECUDA;
+    TraceScope trace("batch_persistent", s);
+    if (w == PG_ID64)
+        batch_kernel<uint64_t><<<grid, kBatchThreads, smem, s>>>(
+            (const unsigned char*)d_plan, (uint64_t*)d_arena, (unsigned long long*)d_ws);
+    else
+        batch_kernel<uint32_t><<<grid, kBatchThreads, smem, s>>>(
+            (const unsigned char*)d_plan, (uint32_t*)d_arena, (unsigned long long*)d_ws);
+    return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
+}
+
+}  // extern "C"

@@ -543,9 +543,12 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             ws.qs[r * 32 + lane] = (uint16_t)q;
         }
         __syncwarp();
-        // chains: a lane that finishes an entry takes the next unclaimed one
+        // chains: a lane that finishes an entry takes the next unclaimed one.
+        // The loop body is kept straight-line -- load the new entry, reconverge,
+        // then ONE link for every lane -- so a warp whose lanes are at
+        // different depths still runs the link code once per trip.
         {
-            uint32_t k = lane, next = 32, q = 0;
+            uint32_t k = lane, next = 32, q = 0xFFFFu;
             bool active = true, fresh = true;
             CurT cur = 0;
             QRecip c{0, 0, 0, 0};
@@ -553,41 +556,34 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             qd.R = 0;
             qd.d = FastDiv{0, 0, 0};
             while (__any_sync(0xFFFFFFFFu, active)) {
-                bool done = false;
-                if (active) {
-                    if (fresh) {
-                        q = ws.qs[k];
-                        if (q == 0xFFFFu) {
-                            done = true;   // past the end of the segment
+                if (active && fresh) {
+                    q = ws.qs[k];
+                    cur = ws.item[k];
+                    if (q != 0xFFFFu) {
+                        if (kFast) {
+                            c = recip[q];
                         } else {
-                            cur = ws.item[k];
-                            if (kFast) {
-                                c = recip[q];
-                            } else {
-                                qd.R = R[q];
-                                qd.d = divR[q];
-                            }
-                            fresh = false;
+                            qd.R = R[q];
+                            qd.d = divR[q];
                         }
                     }
-                    if (!done) {
-                        uint32_t v;
-                        bool fin;
-                        if constexpr (kFast) {
-                            uint32_t c32 = cur;
-                            fin = t_step32(c32, q, c, g, v);
-                            cur = c32;
-                        } else {
-                            uint64_t c64 = cur;
-                            fin = t_step(c64, q, qd, g, v);
-                            cur = c64;
-                        }
-                        if (fin) {
-                            ws.item[k] = v;
-                            done = true;
-                        }
-                    }
+                    fresh = false;
                 }
+                __syncwarp();
+                const bool live = active && q != 0xFFFFu;   // 0xFFFF: past the segment end
+                uint32_t v = 0;
+                bool fin = false;
+                if constexpr (kFast) {
+                    uint32_t c32 = cur;
+                    if (live) fin = t_step32(c32, q, c, g, v);
+                    cur = c32;
+                } else {
+                    uint64_t c64 = cur;
+                    if (live) fin = t_step(c64, q, qd, g, v);
+                    cur = c64;
+                }
+                if (fin) ws.item[k] = v;
+                const bool done = active && (fin || !live);
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
                 if (done) {
                     k = next + __popc(dm & lt);

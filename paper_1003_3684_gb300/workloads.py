@@ -23,6 +23,8 @@ CONFIGS = {
     # blocks of 2^20, 5 edges each, inter-block fraction 0.1
     "pba_n2p30_b1024_m5": dict(kind="pba", n=2**30, m=5, blocks=1024, n0=6, faction_width=1,
                                inter_frac=0.1, seed=3),
+    # 4096 independent graphs of uneven sizes in one persistent launch
+    "batch_4096_mixed": dict(kind="batch", n_jobs=4096, seed=0),
 }
 
 
