@@ -100,6 +100,33 @@ pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t
                   void* stream);
 
 /* ------------------------------------------------------------------------
+ * gen_pba without a caller-supplied workspace (the paper has no
+ * counterpart; this is a library convenience).
+ *
+ * For callers that cannot allocate device memory: code inside a host
+ * application whose allocator owns the whole device and forbids outside
+ * cudaMalloc calls, plugins handed device buffers but no allocation API, and
+ * latency-critical paths that must avoid cudaMalloc/cudaFree and the
+ * device-wide synchronisation they cause. Same arguments and output as
+ * gen_pba, minus d_ws/ws_bytes; the library allocates nothing.
+ *
+ * Scratch: a fixed device array of pg_pba_noalloc_scratch_bytes() (32 MiB)
+ * compiled into the library, held by every GPU that loads it until the
+ * process exits. A graph whose workspace (pg_pba_workspace_size) exceeds it
+ * is rejected with PG_ENOMEM before anything is launched; blocks = 1 needs
+ * no scratch. The first call on each device looks up the array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture. All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, or other host threads) race and give
+ * wrong results, so order them on one stream. Each call clears what must
+ * start at zero.
+ * ---------------------------------------------------------------------- */
+size_t pg_pba_noalloc_scratch_bytes(void);
+pg_status gen_pba_noalloc(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                          uint32_t faction_width, double inter_frac, uint64_t seed, pg_idwidth w,
+                          void* d_edges, uint64_t cap_edges, uint64_t* n_edges_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * Kronecker generator (Sec. 3, PK method; Fig. 2).
  *
  * h_initiator  host, n0*n0 doubles, row-major, all >= 0 with a positive sum.

@@ -187,6 +187,26 @@ pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t
     return from_cuda(launch_pba(g, w == PG_ID64, d_edges, d_ws, s));
 }
 
+}  // extern "C"
+
+namespace pgen {
+
+// Argument checks and launch geometry of gen_pba, for other entry points.
+int pba_setup(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t faction_width,
+              double inter_frac, uint64_t seed, int id64, PbaGeom* g, uint64_t* n_edges)
+{
+    const PbaCheck c = check_pba(n, m, blocks, n0, faction_width, inter_frac,
+                                 id64 ? PG_ID64 : PG_ID32);
+    if (c.st != PG_OK) return c.st;
+    *g = make_geom(c.n_b, c.N_e, m, blocks, n0, faction_width, inter_frac, seed);
+    *n_edges = c.edges;
+    return PG_OK;
+}
+
+}  // namespace pgen
+
+extern "C" {
+
 uint64_t pg_kron_edge_count(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
                             pg_kron_mode mode)
 {
