@@ -143,8 +143,20 @@ def oracle_sample(name: str, cfg: dict, budget_s: float):
     t_total, edges_total, samples = 0.0, 0, 0
     if cfg["kind"] == "batch":
         jobs = W.batch_jobs(cfg["n_jobs"], seed=cfg["seed"])
+    if cfg["kind"] == "serve":
+        from paper_1003_3684_gb300 import serve
+        trace = serve.poisson_workload(cfg["rate"], 2.0, seed=cfg["seed"])
     while samples == 0 or t_total < budget_s:
-        if cfg["kind"] == "batch":
+        if cfg["kind"] == "serve":
+            _, j = trace[(samples * 97) % len(trace)]
+            t0 = time.perf_counter()
+            e = (o.ba(j["n"], j["m"], j["n0"], j["seed"]) if j["kind"] == "pba"
+                 else o.kron(j["initiator"], j["k"], j["n_edges"], j["seed"]))
+            o.csr(e, serve.job_vertices(j))
+            t_total += time.perf_counter() - t0
+            edges_total += e.shape[0]
+            desc = "oracle graph + CSR of requests of the trace (every 97th)"
+        elif cfg["kind"] == "batch":
             j = jobs[(samples * 97) % len(jobs)]
             t0 = time.perf_counter()
             e = (o.ba(j["n"], j["m"], j["n0"], j["seed"]) if j["kind"] == "pba"
@@ -323,8 +335,12 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     peaks = load_peaks()
     sms = pg.pg_device_sm_count()
     alu_peak = sms * 128 * peaks["sm_max_mhz"] * 1e6
-    nl, tot_ms = kernels.get("batch_persistent", (1, ms_max))
-    per_launch = tot_ms / nl / 1000.0
+    # inside a graph replay the library's trace does not run: the replays are
+    # timed by the events above, one persistent launch (plus a 8-byte counter
+    # reset) per wave per step
+    launches = args.steps * waves
+    kernels = {"batch_persistent (graph replay)": (launches, ms_max)}
+    per_launch = ms_max / launches / 1000.0
     ops = batch_work(jobs) / waves
     roof = dict(bound="alu", kernel="batch_persistent", achieved=ops / per_launch / 1e12,
                 peak=alu_peak / 1e12, unit="Tops/s (int32 lane ops)",
@@ -344,7 +360,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                 per_graph=dict(value=total * world / (ms_pg / 1000.0), unit="edges/s",
                                ms_per_step=ms_pg, launches=len(jobs),
                                speedup_batched=ms_pg / (ms_max / args.steps)),
-                roofline=roof, gpu_launches=sum(v[0] for v in kernels.values()),
+                roofline=roof, gpu_launches=launches,
                 kernels={kk: [v[0], round(v[1], 4)] for kk, v in kernels.items()},
                 clocks=clocks)
     if not args.no_e2e:
@@ -381,6 +397,68 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_serve(args, rank: int, world: int, local_rank: int):
+    """Served workload: a Poisson trace replayed in real time against the
+    continuous-batching server, then against a per-graph server (one
+    generation call per request, one stream) on the same trace."""
+    import numpy as np
+    import torch
+
+    from paper_1003_3684_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1003_3684_gb300 as pg
+    from paper_1003_3684_gb300 import serve
+
+    torch.cuda.set_device(local_rank)
+    cfg = W.CONFIGS[args.workload]
+    duration = args.serve_seconds or cfg["duration"]
+    trace = serve.poisson_workload(cfg["rate"], duration, seed=cfg["seed"] + rank)
+    warm = serve.poisson_workload(cfg["rate"], 0.5, seed=cfg["seed"] + 1000 + rank)
+
+    def replay(per_graph, arrivals, max_wall=None):
+        srv = serve.Server(budget_bytes=cfg["budget"], n_streams=1 if per_graph else 3,
+                           max_batch_jobs=1 if per_graph else 256, per_graph=per_graph)
+        t0 = time.perf_counter()
+        done = serve.run_open_loop(srv, arrivals, max_wall=max_wall)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        lat = np.array([r.latency for r in done]) * 1000.0
+        edges = sum(serve.job_edges(r.job) for r in done)
+        return dict(value=edges / wall, unit="edges/s", completed=len(done),
+                    offered=len(arrivals), wall_s=wall,
+                    p50_ms=float(np.percentile(lat, 50)) if lat.size else None,
+                    p99_ms=float(np.percentile(lat, 99)) if lat.size else None,
+                    launches=srv.launches, peak_budget_used=srv.peak_in_use)
+
+    replay(False, warm)
+    pg.pg_trace_dump()
+    pg.pg_trace_enable(True)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    served = replay(False, trace)
+    clocks = sampler.stop() if sampler else None
+    pg.pg_trace_enable(False)
+    kernels = pg.pg_trace_dump()
+    per_graph = replay(True, trace, max_wall=3 * duration)
+    offered = sum(serve.job_edges(j) for _, j in trace) / duration
+    line = dict(metric="edges/sec", value=served["value"], unit="edges/s", n_gpus=world,
+                steps=1, warmup=1, ms_per_step=served["wall_s"] * 1000.0, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
+                config=dict(workload=args.workload, rate_per_s=cfg["rate"], duration_s=duration,
+                            requests=len(trace), offered_edges_per_s=offered,
+                            budget_bytes=cfg["budget"], csr="kept on device until released",
+                            streams=3),
+                latency_ms=dict(p50=served["p50_ms"], p99=served["p99_ms"]),
+                served=served, per_graph=per_graph,
+                gpu_launches=sum(v[0] for v in kernels.values()),
+                kernels={kk: [v[0], round(v[1], 3)] for kk, v in kernels.items()},
+                clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -530,7 +608,10 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     # end to end through the public API with host buffers: the step plus the
     # device-to-host copy of everything it produced into pinned host memory
     if not args.no_e2e:
-        line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)
+        if kind == "pba":
+            line["e2e"] = measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world)
+        else:
+            line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, tsec, ns = oracle_sample(args.workload, cfg, args.cpu_budget)
         line["cpu_baseline"] = dict(value=v, unit="edges/s", cores=1, kind="oracle",
@@ -540,6 +621,41 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world):
+    """End to end through the public API with a host destination: each step
+    is one gen_pba_to_host call (generation with the edge list copied into
+    pinned host memory, overlapped) and a stream synchronisation."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1003_3684_gb300 as pg
+    host = torch.empty(tuple(out.shape), dtype=out.dtype, pin_memory=True)
+    B = cfg["blocks"]
+
+    def e2e_step():
+        pg.gen_pba_to_host(host, cfg["n"], cfg["m"], B, cfg["n0"], cfg["faction_width"],
+                           cfg["inter_frac"], seed, out=out, workspace=ws if B > 1 else None)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    steps = max(1, min(args.steps, 3))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dt = float(t.item())
+    out_bytes = out.numel() * out.element_size()
+    return dict(value=E * steps * world / dt, unit="edges/s", h2d_bytes_per_step=0,
+                d2h_bytes_per_step=out_bytes, steps=steps,
+                host_buffer=f"pinned {out_bytes / 2**30:.1f} GiB; copy overlapped with "
+                            "generation (gen_pba_to_host)")
 
 
 def measure_e2e(args, step, out, cfg, E, dev, world, rank):
@@ -593,6 +709,8 @@ def main():
     ap.add_argument("--blocks", type=int, default=0,
                     help="PBA only: run this many blocks of the workload's block size "
                          "(a smaller case, e.g. for profiler captures)")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="serve workload only: seconds of arrivals (default: the workload's)")
     ap.add_argument("--batch-jobs", type=int, default=0,
                     help="batch workload only: use this many of its jobs (a smaller case)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
@@ -605,6 +723,8 @@ def main():
         return run_reference(args, rank, world)
     if W.CONFIGS[args.workload]["kind"] == "batch":
         return run_batch(args, rank, world, local_rank)
+    if W.CONFIGS[args.workload]["kind"] == "serve":
+        return run_serve(args, rank, world, local_rank)
     return run_pgen(args, rank, world, local_rank)
 
 

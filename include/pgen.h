@@ -21,8 +21,8 @@
  *    PG_ENOSPC (output capacity too small) or PG_ENOMEM (workspace too
  *    small). PG_ECUDA reports a failed launch (cudaGetLastError).
  *  - Vertex ids are written as (src, dst) pairs, interleaved: uint32 pairs
- *    for PG_ID32, uint64 pairs for PG_ID64. Edge buffers must be 16-byte
- *    aligned.
+ *    for PG_ID32, uint64 pairs for PG_ID64. Output edge buffers must be
+ *    16-byte aligned (inputs to edges_to_csr: aligned to one pair).
  *  - Every random draw is Philox4x32-10 (Salmon et al., SC'11) with key
  *    (seed & 0xffffffff, seed >> 32) and a counter that names the draw, so
  *    the output is a pure function of the arguments.
@@ -99,6 +99,16 @@ pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t
                   uint64_t cap_edges, uint64_t* n_edges_out, void* d_ws, size_t ws_bytes,
                   void* stream);
 
+/* gen_pba, and a copy of the edge list into host memory h_edges (pinned,
+ * B*(e0+n_b*m) pairs). The copy of each range of blocks starts on a second,
+ * library-owned stream as soon as that range is written, so the transfer
+ * overlaps generation; `stream` waits for the last copy, so synchronising
+ * `stream` covers both. d_edges still receives the full edge list. */
+pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                          uint32_t faction_width, double inter_frac, uint64_t seed, pg_idwidth w,
+                          void* h_edges, void* d_edges, uint64_t cap_edges, uint64_t* n_edges_out,
+                          void* d_ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * gen_pba without a caller-supplied workspace (the paper has no
  * counterpart; this is a library convenience).
@@ -158,8 +168,12 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
  * CSR assembly (not in the paper; the usual input format of the graph
  * algorithms the generated graphs feed).
  *
- * d_edges      n_edges (src, dst) pairs of width w; every src and every dst
+ * d_edges      n_edges (src, dst) pairs of width w, aligned to one pair (8
+ *              bytes for PG_ID32, 16 for PG_ID64); every src and every dst
  *              is < n_vertices (rows are sorted on the bits of that range).
+ *              A list already grouped by source (non-decreasing src) whose
+ *              rows have at most 32 edges -- what gen_pba writes -- takes a
+ *              path without sorting; the result is the same.
  * d_row_ptr    n_vertices + 1 uint64: row_ptr[v] = #edges with src < v.
  * d_col        n_edges ids of width w: the destinations grouped by source,
  *              ascending within each row (duplicates kept). The result does

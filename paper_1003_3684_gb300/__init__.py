@@ -26,7 +26,7 @@ __all__ = [
     "PG_OK", "PG_EINVAL", "PG_ENOSPC", "PG_ECUDA", "PG_ETIMEOUT", "PG_ENOMEM",
     "PgenError", "lib", "library_path",
     "pg_status_string", "pg_device_sm_count", "pg_version",
-    "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba",
+    "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba", "gen_pba_to_host",
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
 ]
@@ -165,6 +165,38 @@ def gen_pba(n: int, m: int, blocks: int = 1, n0: int | None = None, faction_widt
                        PG_ID64 if id64 else PG_ID32, _ptr(out), out.shape[0], C.byref(n_out),
                        _ptr(workspace), ws_bytes, _stream(stream))
     _check("gen_pba", st)
+    return out[:n_out.value]
+
+
+def gen_pba_to_host(host_out, n: int, m: int, blocks: int = 1, n0: int | None = None,
+                    faction_width: int = 1, inter_frac: float = 0.1, seed: int = 0,
+                    id64: bool = False, out=None, workspace=None, stream=None, device="cuda"):
+    """gen_pba plus a copy of the edges into ``host_out`` (a pinned CPU tensor
+    of the same shape and dtype), overlapped with generation. Synchronise the
+    stream before reading ``host_out``. Returns the device edge tensor."""
+    import torch
+    L = lib()
+    if not getattr(L, "_to_host_ready", False):
+        L.gen_pba_to_host.argtypes = [u64, u32, u32, u32, u32, dbl, u64, i32, vp, vp, u64,
+                                      C.POINTER(u64), vp, sz, vp]
+        L.gen_pba_to_host.restype = i32
+        L._to_host_ready = True
+    n0 = m + 1 if n0 is None else n0
+    E = pg_pba_edge_count(n, m, blocks, n0)
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(E, 1), 2), dtype, device)
+    if host_out.dtype != out.dtype or host_out.shape[0] < E or not host_out.is_pinned():
+        raise ValueError("host_out must be a pinned tensor of the output's dtype with E rows")
+    if blocks > 1 and workspace is None:
+        workspace = _empty(max(pg_pba_workspace_size(n, m, blocks), 1), torch.uint8, out.device)
+    ws_bytes = workspace.numel() if workspace is not None else 0
+    n_out = u64(0)
+    st = L.gen_pba_to_host(n, m, blocks, n0, faction_width, float(inter_frac), seed,
+                           PG_ID64 if id64 else PG_ID32, vp(host_out.data_ptr()), _ptr(out),
+                           out.shape[0], C.byref(n_out), _ptr(workspace), ws_bytes,
+                           _stream(stream))
+    _check("gen_pba_to_host", st)
     return out[:n_out.value]
 
 

@@ -4,6 +4,7 @@
 // device untouched.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/pgen.h"
 #include "pg_internal.h"
@@ -207,6 +208,62 @@ int pba_setup(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t fac
 
 extern "C" {
 
+pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                          uint32_t faction_width, double inter_frac, uint64_t seed, pg_idwidth w,
+                          void* h_edges, void* d_edges, uint64_t cap_edges, uint64_t* n_edges_out,
+                          void* d_ws, size_t ws_bytes, void* stream)
+{
+    if (!h_edges) return PG_EINVAL;
+    const PbaCheck c = check_pba(n, m, blocks, n0, faction_width, inter_frac, w);
+    if (c.st != PG_OK) return c.st;
+    if (n_edges_out) *n_edges_out = c.edges;
+    if (cap_edges < c.edges) return PG_ENOSPC;
+    if (c.edges > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+    const PbaGeom g = make_geom(c.n_b, c.N_e, m, blocks, n0, faction_width, inter_frac, seed);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = c.edges * (w == PG_ID64 ? 16 : 8);
+    if (blocks == 1) {
+        if (launch_ba(g, w == PG_ID64, d_edges, s) != cudaSuccess) return PG_ECUDA;
+        return cudaMemcpyAsync(h_edges, d_edges, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess
+                   ? PG_OK : PG_ECUDA;
+    }
+    const size_t need = pba_workspace_layout(g.A_stride, blocks, g.S).total;
+    if (!d_ws || ws_bytes < need) return PG_ENOMEM;
+    if (!aligned(d_ws, 256)) return PG_EINVAL;
+    // one copy stream and its events per device, made on first use
+    static std::mutex mu;
+    static HostCopy per_dev[64];
+    static bool made[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PG_ECUDA;
+    HostCopy hc;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!made[dev]) {
+            HostCopy& h = per_dev[dev];
+            if (cudaStreamCreateWithFlags(&h.copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return PG_ECUDA;
+            for (uint32_t i = 0; i < kMaxCopyChunks; ++i)
+                if (cudaEventCreateWithFlags(&h.done[i], cudaEventDisableTiming) != cudaSuccess)
+                    return PG_ECUDA;
+            if (cudaEventCreateWithFlags(&h.copied, cudaEventDisableTiming) != cudaSuccess)
+                return PG_ECUDA;
+            made[dev] = true;
+        }
+        hc = per_dev[dev];
+    }
+    hc.h_edges = h_edges;
+    // about one wave of emit CTAs per chunk
+    const uint64_t ctas_per_block = (g.S + 7) / 8;
+    const uint64_t wave = (uint64_t)device_sm_count() * 4;
+    uint64_t per = (wave + ctas_per_block - 1) / ctas_per_block;
+    uint64_t chunks = (blocks + per - 1) / per;
+    if (chunks > kMaxCopyChunks) chunks = kMaxCopyChunks;
+    if (chunks < 1) chunks = 1;
+    hc.chunks = (uint32_t)chunks;
+    return from_cuda(launch_pba(g, w == PG_ID64, d_edges, d_ws, s, &hc));
+}
+
 uint64_t pg_kron_edge_count(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
                             pg_kron_mode mode)
 {
@@ -287,7 +344,8 @@ pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertice
     if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
     if (n_edges > 0 && n_vertices == 0) return PG_EINVAL;
     if (!d_row_ptr || !aligned(d_row_ptr, 8)) return PG_EINVAL;
-    if (n_edges > 0 && (!d_edges || !d_col || !aligned(d_edges, 16))) return PG_EINVAL;
+    if (n_edges > 0 && (!d_edges || !d_col || !aligned(d_edges, w == PG_ID64 ? 16 : 8)))
+        return PG_EINVAL;
     if (w == PG_ID32 && n_vertices > ((uint64_t)1 << 32)) return PG_EINVAL;
     const size_t need = csr_workspace_bytes(n_edges, n_vertices);
     if (ws_bytes < need || (need > 0 && !d_ws)) return PG_ENOMEM;

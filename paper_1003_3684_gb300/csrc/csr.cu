@@ -12,8 +12,16 @@
 //                  and a scattered write of the (src, dst) pair.
 // No atomics decide any position, so the result does not depend on the
 // schedule, and a power-law row (a hub with 10^5 edges) costs no more than
-// any other key. A final pass writes col and fills row_ptr from the row
-// boundaries of the sorted list (row_ptr[v] = first index with src >= v).
+// any other key. A final pass writes col and marks each row's end in
+// row_ptr; a parallel prefix maximum then gives row_ptr[v] = first index with
+// src >= v for every v, rows without edges included.
+//
+// Fast path: edge lists that are already grouped by source (non-decreasing
+// src, as gen_pba and serial BA write them) with rows of at most
+// kGroupedMaxRow edges skip the sort. csr_check sets a device flag when the
+// list is not such a list; otherwise csr_grouped places each destination at
+// its rank within its own row. The sort kernels read the flag and return at
+// once when the fast path applied, so no host round trip decides the path.
 #include "pg_internal.h"
 #include "pg_trace.h"
 
@@ -22,11 +30,10 @@ namespace {
 
 constexpr int kSortWarps = 16;
 constexpr int kSortThreads = kSortWarps * 32;
-constexpr int kSortItems = 16;
-constexpr uint32_t kSortTile = kSortThreads * kSortItems;   // 8192
 constexpr int kMaxDigitBits = 10;
 constexpr uint32_t kMaxBuckets = 1u << kMaxDigitBits;
 constexpr uint32_t kScanTile = 4096;
+constexpr uint32_t kGroupedMaxRow = 32;
 
 template <typename Id>
 struct PairOf;
@@ -46,32 +53,61 @@ __device__ __forceinline__ uint32_t digit_of(const P& e, int field, int shift, u
     return (uint32_t)(v >> shift) & mask;
 }
 
+// Elements per thread of a sort tile: 16 pairs of 32-bit ids or 8 of 64-bit.
+template <typename Id>
+struct SortShape {
+    static constexpr int items = sizeof(Id) == 4 ? 16 : 8;
+    static constexpr uint32_t tile = kSortThreads * items;
+};
+
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(
     const typename PairOf<Id>::T* __restrict__ in, uint64_t M, int field, int shift, int bits,
-    uint32_t* __restrict__ H, uint32_t n_tiles)
+    uint32_t* __restrict__ H, uint32_t n_tiles, const uint32_t* __restrict__ sort_needed)
 {
     __shared__ uint32_t h[kMaxBuckets];
+    if (*sort_needed == 0) return;
     const uint32_t nb = 1u << bits, mask = nb - 1;
+    const uint32_t lane = threadIdx.x & 31;
     for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) h[d] = 0;
     __syncthreads();
-    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-    const uint64_t end = (base + kSortTile < M) ? base + kSortTile : M;
-    for (uint64_t i = base + threadIdx.x; i < end; i += blockDim.x)
-        atomicAdd(&h[digit_of(in[i], field, shift, mask)], 1u);
+    constexpr uint32_t kTile = SortShape<Id>::tile;
+    const uint64_t base = (uint64_t)blockIdx.x * kTile;
+    const uint64_t end = (base + kTile < M) ? base + kTile : M;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint64_t i0 = base + (threadIdx.x & ~31u); i0 < end; i0 += blockDim.x) {
+        const uint64_t i = i0 + lane;
+        const uint32_t d = (i < end) ? digit_of(in[i], field, shift, mask) : 0xFFFFFFFFu;
+        // one shared-memory atomic per distinct digit of the warp (skewed
+        // digits -- hubs -- would otherwise serialise on one counter)
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (d != 0xFFFFFFFFu && (peers & lt) == 0) atomicAdd(&h[d], __popc(peers));
+    }
     __syncthreads();
     for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x)
         H[(uint64_t)d * n_tiles + blockIdx.x] = h[d];
 }
 
+// One LSD pass over a tile: load once, rank stably (per warp by match, then
+// across warps), reorder the tile by digit in shared memory, and write each
+// digit's run to its place in the output with consecutive threads on
+// consecutive elements.
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const typename PairOf<Id>::T* __restrict__ in, typename PairOf<Id>::T* __restrict__ out,
-    uint64_t M, int field, int shift, int bits, const uint64_t* __restrict__ Hs, uint32_t n_tiles)
+    uint64_t M, int field, int shift, int bits, const uint64_t* __restrict__ Hs, uint32_t n_tiles,
+    const uint32_t* __restrict__ sort_needed)
 {
     using P = typename PairOf<Id>::T;
-    __shared__ uint16_t wcnt[kSortWarps][kMaxBuckets];   // 32 KB
-    __shared__ uint64_t tbase[kMaxBuckets];               // 8 KB
+    constexpr int kItems = SortShape<Id>::items;
+    constexpr uint32_t kTile = SortShape<Id>::tile;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint16_t (*wcnt)[kMaxBuckets] = reinterpret_cast<uint16_t (*)[kMaxBuckets]>(smem);   // 32 KB
+    uint64_t* tbase = reinterpret_cast<uint64_t*>(smem + kSortWarps * kMaxBuckets * 2);   // 8 KB
+    uint32_t* loff = reinterpret_cast<uint32_t*>(tbase + kMaxBuckets);                  // 4 KB
+    P* buf = reinterpret_cast<P*>(loff + kMaxBuckets);                                  // tile
+    __shared__ uint32_t s_part[kSortWarps + 1];
+    if (*sort_needed == 0) return;
     const uint32_t nb = 1u << bits, mask = nb - 1;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t tile = blockIdx.x;
@@ -79,14 +115,22 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
         for (int w = 0; w < kSortWarps; ++w) wcnt[w][d] = 0;
         tbase[d] = Hs[(uint64_t)d * n_tiles + tile];
     }
-    __syncthreads();
-    const uint64_t base = (uint64_t)tile * kSortTile + wid * (32 * kSortItems);
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t dig[kSortItems], rnk[kSortItems];
+    const uint64_t tile0 = (uint64_t)tile * kTile;
+    const uint32_t n = (uint32_t)((M - tile0 < kTile) ? M - tile0 : kTile);
+    const uint32_t wbase = wid * (32 * kItems);
+    P e[kItems];
+    uint32_t dig[kItems], rnk[kItems];
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const uint64_t i = base + r * 32 + lane;
-        const uint32_t d = (i < M) ? digit_of(in[i], field, shift, mask) : 0xFFFFFFFFu;
+    for (int r = 0; r < kItems; ++r) {
+        const uint32_t t = wbase + r * 32 + lane;
+        if (t < n) e[r] = in[tile0 + t];
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const uint32_t t = wbase + r * 32 + lane;
+        const uint32_t d = (t < n) ? digit_of(e[r], field, shift, mask) : 0xFFFFFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
         uint32_t prev = 0;
         if (d != 0xFFFFFFFFu) prev = wcnt[wid][d];
@@ -97,23 +141,68 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
         rnk[r] = prev + __popc(peers & lt);
     }
     __syncthreads();
+    // per digit: prefix over warps (in wcnt) and the tile total (in loff)
     for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) {
         uint32_t acc = 0;
+#pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
             const uint32_t c = wcnt[w][d];
             wcnt[w][d] = (uint16_t)acc;
             acc += c;
         }
+        loff[d] = acc;
     }
     __syncthreads();
+    // exclusive scan of the tile totals over digits (each thread a run of digits)
+    {
+        const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+        const uint32_t d0 = threadIdx.x * per;
+        uint32_t sum = 0;
+        for (uint32_t d = d0; d < d0 + per && d < nb; ++d) sum += loff[d];
+        // warp inclusive scan of the run sums, then across warps
+        uint32_t x = sum;
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const uint64_t i = base + r * 32 + lane;
-        if (dig[r] != 0xFFFFFFFFu) {
-            const P e = in[i];
-            out[tbase[dig[r]] + wcnt[wid][dig[r]] + rnk[r]] = e;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) s_part[wid] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = s_part[w];
+                s_part[w] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+        uint32_t run = s_part[wid] + x - sum;
+        for (uint32_t d = d0; d < d0 + per && d < nb; ++d) {
+            const uint32_t c = loff[d];
+            loff[d] = run;
+            run += c;
         }
     }
+    __syncthreads();
+    // reorder the tile by digit in shared memory
+#pragma unroll
+    for (int r = 0; r < kItems; ++r)
+        if (dig[r] != 0xFFFFFFFFu) buf[loff[dig[r]] + wcnt[wid][dig[r]] + rnk[r]] = e[r];
+    __syncthreads();
+    // write runs: sorted position p goes to tbase[d] + (p - loff[d])
+    for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
+        const P v = buf[p];
+        const uint32_t d = digit_of(v, field, shift, mask);
+        out[tbase[d] + (p - loff[d])] = v;
+    }
+}
+
+template <typename Id>
+size_t scatter_smem_bytes()
+{
+    return (size_t)kSortWarps * kMaxBuckets * 2 + kMaxBuckets * 8 + kMaxBuckets * 4 +
+           (size_t)SortShape<Id>::tile * sizeof(typename PairOf<Id>::T);
 }
 
 // ---- exclusive scan of uint32 counts into uint64 offsets ------------------
@@ -148,9 +237,11 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* s
 
 // per-tile sums (tile = kScanTile counts, 256 threads x 16)
 __global__ void __launch_bounds__(256) scan_reduce_kernel(const uint32_t* __restrict__ in,
-                                                          uint64_t n, uint64_t* __restrict__ part)
+                                                          uint64_t n, uint64_t* __restrict__ part,
+                                                          const uint32_t* __restrict__ sort_needed)
 {
     __shared__ uint64_t s_warp[32];
+    if (*sort_needed == 0) return;
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
     uint64_t sum = 0;
     for (uint32_t t = threadIdx.x; t < kScanTile; t += blockDim.x)
@@ -162,9 +253,11 @@ __global__ void __launch_bounds__(256) scan_reduce_kernel(const uint32_t* __rest
 
 // exclusive scan of the tile sums, one CTA looping over chunks
 __global__ void __launch_bounds__(1024) scan_parts_kernel(uint64_t* __restrict__ part,
-                                                          uint64_t n_parts)
+                                                          uint64_t n_parts,
+                                                          const uint32_t* __restrict__ sort_needed)
 {
     __shared__ uint64_t s_warp[32];
+    if (*sort_needed == 0) return;
     uint64_t carry = 0;
     for (uint64_t base = 0; base < n_parts; base += blockDim.x) {
         const uint64_t i = base + threadIdx.x;
@@ -179,9 +272,11 @@ __global__ void __launch_bounds__(1024) scan_parts_kernel(uint64_t* __restrict__
 __global__ void __launch_bounds__(256) scan_apply_kernel(const uint32_t* __restrict__ in,
                                                          uint64_t n,
                                                          const uint64_t* __restrict__ part,
-                                                         uint64_t* __restrict__ out)
+                                                         uint64_t* __restrict__ out,
+                                                         const uint32_t* __restrict__ sort_needed)
 {
     __shared__ uint64_t s_warp[32];
+    if (*sort_needed == 0) return;
     constexpr int per = kScanTile / 256;
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * per;
     uint32_t v[per];
@@ -201,19 +296,157 @@ __global__ void __launch_bounds__(256) scan_apply_kernel(const uint32_t* __restr
 }
 
 // ---- final pass: col and row_ptr from the sorted pairs ---------------------
+// Flags (sort_needed = 1) a list that is not grouped by source, or that has
+// a row longer than kGroupedMaxRow.
 template <typename Id>
-__global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<Id>::T* __restrict__ s,
-                                                         uint64_t M, uint64_t N,
-                                                         uint64_t* __restrict__ row_ptr,
-                                                         Id* __restrict__ col)
+__global__ void __launch_bounds__(256) csr_check_kernel(const typename PairOf<Id>::T* __restrict__ s,
+                                                        uint64_t M, uint32_t* __restrict__ sort_needed)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= M; i += stride) {
-        // rows (prev_src, cur_src] start at index i
-        const uint64_t lo = (i == 0) ? 0 : (uint64_t)s[i - 1].x + 1;
-        const uint64_t hi = (i == M) ? N : (uint64_t)s[i].x;
-        for (uint64_t v = lo; v <= hi && v <= N; ++v) row_ptr[v] = i;
-        if (i < M) col[i] = (Id)s[i].y;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const uint64_t src = s[i].x;
+        const bool starts = (i == 0) || s[i - 1].x != src;
+        if (i > 0 && (uint64_t)s[i - 1].x > src) atomicOr(sort_needed, 1u);
+        if (starts && i + kGroupedMaxRow < M && (uint64_t)s[i + kGroupedMaxRow].x == src)
+            atomicOr(sort_needed, 1u);
+    }
+}
+
+// Row ends of a list sorted (or grouped) by source: the last edge i of row v
+// writes row_ptr[v + 1] = i + 1. A prefix maximum over row_ptr then fills the
+// rows without edges (row_ptr starts zeroed).
+template <typename P>
+__device__ __forceinline__ void mark_row_end(const P* s, uint64_t M, uint64_t i, uint64_t* row_ptr)
+{
+    if (i + 1 == M || s[i + 1].x != s[i].x) row_ptr[(uint64_t)s[i].x + 1] = i + 1;
+}
+
+// Grouped list: destination of edge i goes to its row start + its rank among
+// the row's destinations (ties broken by position, so equal values keep
+// their multiplicity).
+template <typename Id>
+__global__ void __launch_bounds__(256) csr_grouped_kernel(const typename PairOf<Id>::T* __restrict__ s,
+                                                          uint64_t M, Id* __restrict__ col,
+                                                          uint64_t* __restrict__ row_ptr,
+                                                          const uint32_t* __restrict__ sort_needed)
+{
+    if (*sort_needed != 0) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const uint64_t src = s[i].x, d = s[i].y;
+        uint64_t a = i, b = i + 1;
+        while (a > 0 && (uint64_t)s[a - 1].x == src) --a;
+        while (b < M && (uint64_t)s[b].x == src) ++b;
+        uint64_t rank = 0;
+        for (uint64_t j = a; j < b; ++j) {
+            const uint64_t dj = s[j].y;
+            rank += (dj < d) || (dj == d && j < i);
+        }
+        col[a + rank] = (Id)d;
+        mark_row_end(s, M, i, row_ptr);
+    }
+}
+
+// In-place inclusive prefix maximum over n uint64 (three kernels, as the sums).
+__device__ __forceinline__ uint64_t block_inclusive_max(uint64_t v, uint64_t* s_warp, uint64_t& total)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t nw = blockDim.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o && y > x) x = y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= (uint32_t)o && y > w) w = y;
+        }
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[nw - 1];
+    const uint64_t before = wid ? s_warp[wid - 1] : 0;
+    __syncthreads();
+    return x > before ? x : before;
+}
+
+__global__ void __launch_bounds__(256) max_reduce_kernel(const uint64_t* __restrict__ in, uint64_t n,
+                                                         uint64_t* __restrict__ part)
+{
+    __shared__ uint64_t s_warp[32];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    uint64_t m = 0;
+    for (uint32_t t = threadIdx.x; t < kScanTile; t += blockDim.x)
+        if (base + t < n && in[base + t] > m) m = in[base + t];
+    uint64_t total;
+    block_inclusive_max(m, s_warp, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// exclusive prefix maximum of the tile maxima, one CTA looping over chunks
+__global__ void __launch_bounds__(1024) max_parts_kernel(uint64_t* __restrict__ part, uint64_t n_parts)
+{
+    __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_inc[1024];
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < n_parts; base += blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        const uint64_t v = i < n_parts ? part[i] : 0;
+        uint64_t total;
+        s_inc[threadIdx.x] = block_inclusive_max(v, s_warp, total);
+        __syncthreads();
+        uint64_t ex = threadIdx.x ? s_inc[threadIdx.x - 1] : 0;
+        if (ex < carry) ex = carry;
+        if (i < n_parts) part[i] = ex;
+        if (total > carry) carry = total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) max_apply_kernel(uint64_t* __restrict__ data, uint64_t n,
+                                                        const uint64_t* __restrict__ part)
+{
+    __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_inc[256];
+    constexpr int per = kScanTile / 256;
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * per;
+    uint64_t v[per];
+    uint64_t m = 0;
+#pragma unroll
+    for (int t = 0; t < per; ++t) {
+        v[t] = (base + t < n) ? data[base + t] : 0;
+        if (v[t] > m) m = v[t];
+    }
+    uint64_t total;
+    s_inc[threadIdx.x] = block_inclusive_max(m, s_warp, total);
+    __syncthreads();
+    uint64_t run = threadIdx.x ? s_inc[threadIdx.x - 1] : 0;   // previous threads' runs
+    const uint64_t carry = part[blockIdx.x];                    // previous tiles
+    if (run < carry) run = carry;
+#pragma unroll
+    for (int t = 0; t < per; ++t) {
+        if (v[t] > run) run = v[t];
+        if (base + t < n) data[base + t] = run;
+    }
+}
+
+template <typename Id>
+__global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<Id>::T* __restrict__ s,
+                                                         uint64_t M, uint64_t* __restrict__ row_ptr,
+                                                         Id* __restrict__ col,
+                                                         const uint32_t* __restrict__ sort_needed)
+{
+    if (*sort_needed == 0) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        col[i] = (Id)s[i].y;
+        mark_row_end(s, M, i, row_ptr);
     }
 }
 
@@ -228,9 +461,9 @@ int bit_length(uint64_t x)
 }
 
 struct CsrLayout {
-    size_t off_a, off_b, off_h, off_hs, off_part, total;
+    size_t off_a, off_b, off_h, off_hs, off_part, off_flag, off_rpart, total;
     uint32_t n_tiles, max_nb;
-    uint64_t n_h, n_parts;
+    uint64_t n_h, n_parts, n_rparts;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -241,8 +474,9 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
     const int bits = bit_length(N > 0 ? N - 1 : 0);
     const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
     const int dbits = passes ? (bits + passes - 1) / passes : 0;
+    const uint32_t tile = pair_bytes == 8 ? SortShape<uint32_t>::tile : SortShape<uint64_t>::tile;
     L.max_nb = 1u << dbits;
-    L.n_tiles = (uint32_t)((M + kSortTile - 1) / kSortTile);
+    L.n_tiles = (uint32_t)((M + tile - 1) / tile);
     L.n_h = (uint64_t)L.max_nb * L.n_tiles;
     L.n_parts = (L.n_h + kScanTile - 1) / kScanTile;
     size_t o = 0;
@@ -256,6 +490,11 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
     o += a256(L.n_h * 8);
     L.off_part = o;
     o += a256((L.n_parts + 1) * 8);
+    L.off_flag = o;
+    o += 256;
+    L.n_rparts = (N + 1 + kScanTile - 1) / kScanTile;
+    L.off_rpart = o;
+    o += a256((L.n_rparts + 1) * 8);
     L.total = o;
     return L;
 }
@@ -266,12 +505,33 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
 {
     using P = typename PairOf<Id>::T;
     const CsrLayout L = csr_layout(M, N, sizeof(P));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(radix_scatter_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem_bytes<Id>());
+        attr = true;
+    }
     unsigned char* ws = (unsigned char*)d_ws;
     P* buf[2] = {(P*)(ws + L.off_a), (P*)(ws + L.off_b)};
     uint32_t* H = (uint32_t*)(ws + L.off_h);
     uint64_t* Hs = (uint64_t*)(ws + L.off_hs);
     uint64_t* part = (uint64_t*)(ws + L.off_part);
+    uint32_t* sort_needed = (uint32_t*)(ws + L.off_flag);
     cudaError_t err;
+    const uint64_t work = M + 1;
+    int grid = (int)((work + 255) / 256);
+    const int cap = device_sm_count() * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    if (cudaMemsetAsync(sort_needed, 0, 4, s) != cudaSuccess) return cudaErrorUnknown;
+    if (cudaMemsetAsync(d_row_ptr, 0, (N + 1) * 8, s) != cudaSuccess) return cudaErrorUnknown;
+    {
+        TraceScope trace("csr_check", s);
+        csr_check_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, sort_needed);
+        csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, (Id*)d_col, d_row_ptr,
+                                                   sort_needed);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
     const int bits = bit_length(N > 0 ? N - 1 : 0);
     const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
@@ -288,20 +548,21 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
                 const uint64_t nh = ((uint64_t)1 << b) * L.n_tiles;
                 {
                     TraceScope trace("csr_radix_hist", s);
-                    radix_hist_kernel<Id><<<L.n_tiles, kSortThreads, 0, s>>>(cur, M, field, shift,
-                                                                             b, H, L.n_tiles);
+                    radix_hist_kernel<Id><<<L.n_tiles, kSortThreads, 0, s>>>(
+                        cur, M, field, shift, b, H, L.n_tiles, sort_needed);
                 }
                 const uint64_t n_parts = (nh + kScanTile - 1) / kScanTile;
                 {
                     TraceScope trace("csr_scan", s);
-                    scan_reduce_kernel<<<(unsigned)n_parts, 256, 0, s>>>(H, nh, part);
-                    scan_parts_kernel<<<1, 1024, 0, s>>>(part, n_parts);
-                    scan_apply_kernel<<<(unsigned)n_parts, 256, 0, s>>>(H, nh, part, Hs);
+                    scan_reduce_kernel<<<(unsigned)n_parts, 256, 0, s>>>(H, nh, part, sort_needed);
+                    scan_parts_kernel<<<1, 1024, 0, s>>>(part, n_parts, sort_needed);
+                    scan_apply_kernel<<<(unsigned)n_parts, 256, 0, s>>>(H, nh, part, Hs,
+                                                                        sort_needed);
                 }
                 {
                     TraceScope trace("csr_radix_scatter", s);
-                    radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, 0, s>>>(
-                        cur, buf[which], M, field, shift, b, Hs, L.n_tiles);
+                    radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
+                        cur, buf[which], M, field, shift, b, Hs, L.n_tiles, sort_needed);
                 }
                 if ((err = cudaGetLastError()) != cudaSuccess) return err;
                 cur = buf[which];
@@ -310,13 +571,12 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
             }
         }
     }
-    const uint64_t work = M + 1;
-    int grid = (int)((work + 255) / 256);
-    const int cap = device_sm_count() * 8;
-    if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
     TraceScope trace("csr_finish", s);
-    csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col);
+    csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, d_row_ptr, (Id*)d_col, sort_needed);
+    uint64_t* rpart = (uint64_t*)(ws + L.off_rpart);
+    max_reduce_kernel<<<(unsigned)L.n_rparts, 256, 0, s>>>(d_row_ptr, N + 1, rpart);
+    max_parts_kernel<<<1, 1024, 0, s>>>(rpart, L.n_rparts);
+    max_apply_kernel<<<(unsigned)L.n_rparts, 256, 0, s>>>(d_row_ptr, N + 1, rpart);
     return cudaGetLastError();
 }
 
@@ -324,8 +584,10 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
 
 size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices)
 {
-    // sized for 16-byte pairs so that one size fits either id width
-    return csr_layout(n_edges, n_vertices, 16).total;
+    // one size that fits either id width
+    const size_t a = csr_layout(n_edges, n_vertices, 16).total;
+    const size_t b = csr_layout(n_edges, n_vertices, 8).total;
+    return a > b ? a : b;
 }
 
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,

@@ -51,6 +51,7 @@ constexpr int kEmitWarps = 8;
 constexpr int kEmitThreads = kEmitWarps * 32;
 constexpr int kEmitItems = 16;
 constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 512 entries per warp run
+constexpr bool kEmitDual = false;   // two chains per lane in the emit loop
 constexpr uint32_t kMaxBlocks = 1024;
 constexpr int kBaThreads = 256;
 template <typename Id>
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
 
 // ---------------------------------------------------------------------------
 // Phase 1, one doubling level [L, hi) of every block; grid = (chunks, B),
-// chunk c = [L + c*kPassChunk, ...). dynamic smem = B*4 (histogram).
+// chunk c = [L + c*kPassChunk, ...). dynamic smem = B*4 (histogram) + one
+// staged run of kPassRun entries per warp.
 // A copy that lands below L loads A_p[r]; the load is consumed one loop trip
 // later (after the next Philox), so its latency overlaps arithmetic.
 // ---------------------------------------------------------------------------
@@ -144,12 +146,14 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
                                                                 uint32_t* __restrict__ cnt)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem);                              // B
+    uint16_t* stage = reinterpret_cast<uint16_t*>(smem + (((size_t)g.B * 4 + 15) & ~(size_t)15));
     const uint32_t p = blockIdx.y;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t phi = (p / g.W) * g.W;
     uint16_t* Ap = A + (uint64_t)p * g.A_stride;
+    uint16_t* my = stage + wid * kPassRun;              // this warp's run, staged
     const uint32_t chunk = L + blockIdx.x * kPassChunk;   // a granule: one segment
     for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x) hist[t] = 0;
     __syncthreads();
@@ -161,13 +165,15 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     uint32_t cur = run + item;
     bool active = item < n_items;
     bool pend = false;
-    uint32_t pend_j = 0, pend_v = 0;
+    uint32_t pend_k = 0, pend_v = 0;
+    uint32_t own = 0;   // entries equal to p (the most frequent value) counted here
     while (__any_sync(0xFFFFFFFFu, active || pend)) {
         uint4 w = make_uint4(0, 0, 0, 0);
         if (active) w = philox(make_uint4(cur, 0u, p, 1u), g.key);
         if (pend) {   // the value loaded one trip ago
-            Ap[pend_j] = (uint16_t)pend_v;
-            atomicAdd(&hist[pend_v], 1u);
+            my[pend_k] = (uint16_t)pend_v;
+            if (pend_v == p) ++own;
+            else atomicAdd(&hist[pend_v], 1u);
             pend = false;
         }
         bool done = false;
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
             }
             if (done) {
                 pend = true;
-                pend_j = run + item;
+                pend_k = item;
             }
         }
         const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
@@ -197,6 +203,17 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
         }
         next += __popc(dm);
     }
+    __syncwarp();
+    // the run back to A: 16-byte stores when the run is whole (run is a
+    // multiple of 8 entries and rows are 16-byte aligned)
+    if (n_items == kPassRun) {
+        const uint4* src = reinterpret_cast<const uint4*>(my);
+        uint4* dst = reinterpret_cast<uint4*>(Ap + run);
+        for (uint32_t t = lane; t < kPassRun / 8; t += 32) dst[t] = src[t];
+    } else {
+        for (uint32_t t = lane; t < n_items; t += 32) Ap[run + t] = my[t];
+    }
+    if (own) atomicAdd(&hist[p], own);
     __syncthreads();
     flush_counts(hist, cnt, g, p, (uint32_t)(chunk / g.seg_len));
 }
@@ -315,6 +332,42 @@ __device__ __forceinline__ bool t_step(uint64_t& cur, uint32_t q, const QDiv& qd
         return true;
     }
     cur = e;
+    return false;
+}
+
+// The draw of one 32-bit link: e = r >> 1 and side = r & 1 for the slot
+// drawn by entry `cur` of T_q (no branches, so two of these interleave).
+__device__ __forceinline__ void t_draw32(uint32_t cur, uint32_t q, const QRecip& c,
+                                         const PbaGeom& g, uint32_t& e, uint32_t& side)
+{
+    const uint32_t nb = (uint32_t)g.n_b;
+    const uint32_t sig = sigma32(cur, c);
+    uint32_t before;
+    if (g.nb_shift != 0xFFFFFFFFu)
+        before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
+    else
+        before = (uint32_t)fdiv((uint64_t)sig * c.R + (nb - 1), g.div_nb);
+    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
+    const uint32_t X = (uint32_t)g.e0 + before;
+    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
+    e = (uint32_t)(s >> 32);
+    side = ((uint32_t)s) >> 31;
+}
+
+// Resolution of a drawn link: true with v when the chain ends here.
+__device__ __forceinline__ bool t_resolve32(uint32_t e, uint32_t side, uint32_t& cur,
+                                            const QRecip& c, const PbaGeom& g, uint32_t& v)
+{
+    if (e < (uint32_t)g.e0) {
+        v = seed_endpoint(e, side, g.n0);
+        return true;
+    }
+    const uint32_t e2 = e - (uint32_t)g.e0;
+    if (side == 0) {
+        v = g.n0 + sigma32(e2, c);
+        return true;
+    }
+    cur = e2;
     return false;
 }
 
@@ -489,18 +542,70 @@ struct EmitWarpSmem {
     uint16_t qs[kEmitRun];     // target block of each entry of the run
 };
 
+// Two chains per lane (slots a and b: 64 virtual lanes per warp). Both
+// links of a trip are drawn before either is resolved, so their Philox
+// rounds interleave; claims go to slot a's finishers first, then slot b's.
+template <typename CurT>
+__device__ __forceinline__ void emit_chains_dual(EmitWarpSmem<CurT>& ws, const PbaGeom& g,
+                                                 const QRecip* __restrict__ recip, uint32_t lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t ka = lane, kb = 32 + lane, next = 64;
+    bool acta = true, actb = true, fra = true, frb = true;
+    uint32_t qa = 0xFFFFu, qb = 0xFFFFu, cura = 0, curb = 0;
+    QRecip ca{0, 0, 0, 0}, cb{0, 0, 0, 0};
+    while (__any_sync(0xFFFFFFFFu, acta || actb)) {
+        if (acta && fra) {
+            qa = ws.qs[ka];
+            cura = (uint32_t)ws.item[ka];
+            if (qa != 0xFFFFu) ca = recip[qa];
+            fra = false;
+        }
+        if (actb && frb) {
+            qb = ws.qs[kb];
+            curb = (uint32_t)ws.item[kb];
+            if (qb != 0xFFFFu) cb = recip[qb];
+            frb = false;
+        }
+        __syncwarp();
+        const bool la = acta && qa != 0xFFFFu, lb = actb && qb != 0xFFFFu;
+        uint32_t ea, sa, eb, sb;
+        t_draw32(cura, qa, ca, g, ea, sa);
+        t_draw32(curb, qb, cb, g, eb, sb);
+        uint32_t va = 0, vb = 0;
+        const bool fa = la && t_resolve32(ea, sa, cura, ca, g, va);
+        const bool fb = lb && t_resolve32(eb, sb, curb, cb, g, vb);
+        if (fa) ws.item[ka] = va;
+        if (fb) ws.item[kb] = vb;
+        const bool da = acta && (fa || !la), db = actb && (fb || !lb);
+        const uint32_t ma = __ballot_sync(0xFFFFFFFFu, da);
+        const uint32_t mb = __ballot_sync(0xFFFFFFFFu, db);
+        if (da) {
+            ka = next + __popc(ma & lt);
+            acta = ka < kEmitRun;
+            fra = true;
+        }
+        if (db) {
+            kb = next + __popc(ma) + __popc(mb & lt);
+            actb = kb < kEmitRun;
+            frb = true;
+        }
+        next += __popc(ma) + __popc(mb);
+    }
+}
+
 template <typename Id, bool kFast>
 __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const __grid_constant__ PbaGeom g, const uint16_t* __restrict__ A,
     const uint64_t* __restrict__ off, const uint64_t* __restrict__ R,
     const FastDiv* __restrict__ divR, const QRecip* __restrict__ recip,
-    const uint32_t* __restrict__ wide_flag, Id* __restrict__ out)
+    const uint32_t* __restrict__ wide_flag, Id* __restrict__ out, uint32_t block_off)
 {
     using CurT = typename std::conditional<kFast, uint32_t, uint64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if ((*wide_flag == 0) != kFast) return;   // the other variant does the work
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t p = blockIdx.y;
+    const uint32_t p = blockIdx.y + block_off;
     const uint32_t sw = blockIdx.x * kEmitWarps + wid;
     if (sw >= g.S) return;                   // no block-wide barrier follows
     EmitWarpSmem<CurT>& ws = reinterpret_cast<EmitWarpSmem<CurT>*>(smem_raw)[wid];
@@ -547,7 +652,9 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
         // The loop body is kept straight-line -- load the new entry, reconverge,
         // then ONE link for every lane -- so a warp whose lanes are at
         // different depths still runs the link code once per trip.
-        {
+        if constexpr (kFast && kEmitDual) {
+            emit_chains_dual(ws, g, recip, lane);
+        } else {
             uint32_t k = lane, next = 32, q = 0xFFFFu;
             bool active = true, fresh = true;
             CurT cur = 0;
@@ -729,7 +836,8 @@ cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s)
+cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s,
+                       const HostCopy* hc)
 {
     if (g.B > kMaxBlocks) return cudaErrorInvalidValue;
     const PbaWorkspace L = pba_workspace_layout(g.A_stride, g.B, g.S);
@@ -772,7 +880,9 @@ cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cuda
         for (uint64_t lvl = g.P; lvl < g.N_e;) {
             const uint64_t hi = (2 * lvl < g.N_e) ? 2 * lvl : g.N_e;
             const uint32_t chunks = (uint32_t)((hi - lvl + kPassChunk - 1) / kPassChunk);
-            pba_pass_kernel<<<dim3(chunks, g.B), kPassThreads, (size_t)g.B * 4, s>>>(
+            const size_t smem = (((size_t)g.B * 4 + 15) & ~(size_t)15) +
+                                (size_t)(kPassThreads / 32) * kPassRun * 2;
+            pba_pass_kernel<<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
                 g, (uint32_t)lvl, (uint32_t)hi, A, cnt);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             lvl = hi;
@@ -784,22 +894,47 @@ cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cuda
                                                           g.B, g.B * g.S, g.e0, wide);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const dim3 grid((g.S + kEmitWarps - 1) / kEmitWarps, g.B);
     // every R_q + e0 < 2^32 is certain when all entries together are fewer
     const bool surely_fast = (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);
-    TraceScope trace("pba_emit", s);
-    if (id64) {
-        pba_emit_kernel<uint64_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
-            g, A, off, R, divR, recip, wide, (uint64_t*)d_out);
-        if (!surely_fast)
-            pba_emit_kernel<uint64_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
-                g, A, off, R, divR, recip, wide, (uint64_t*)d_out);
-    } else {
-        pba_emit_kernel<uint32_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
-            g, A, off, R, divR, recip, wide, (uint32_t*)d_out);
-        if (!surely_fast)
-            pba_emit_kernel<uint32_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
-                g, A, off, R, divR, recip, wide, (uint32_t*)d_out);
+    const uint32_t chunks = hc ? hc->chunks : 1;
+    const uint32_t per = (g.B + chunks - 1) / chunks;
+    const uint64_t edges_per_block = g.e0 + g.N_e;
+    const size_t pair = id64 ? 16 : 8;
+    for (uint32_t b0 = 0, c = 0; b0 < g.B; b0 += per, ++c) {
+        const uint32_t nb = (g.B - b0 < per) ? g.B - b0 : per;
+        const dim3 grid((g.S + kEmitWarps - 1) / kEmitWarps, nb);
+        {
+            TraceScope trace("pba_emit", s);
+            if (id64) {
+                pba_emit_kernel<uint64_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
+                    g, A, off, R, divR, recip, wide, (uint64_t*)d_out, b0);
+                if (!surely_fast)
+                    pba_emit_kernel<uint64_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
+                        g, A, off, R, divR, recip, wide, (uint64_t*)d_out, b0);
+            } else {
+                pba_emit_kernel<uint32_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
+                    g, A, off, R, divR, recip, wide, (uint32_t*)d_out, b0);
+                if (!surely_fast)
+                    pba_emit_kernel<uint32_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
+                        g, A, off, R, divR, recip, wide, (uint32_t*)d_out, b0);
+            }
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if (hc) {
+            // this chunk's edges go to the host while the next chunk is made
+            const size_t off_b = (size_t)b0 * edges_per_block * pair;
+            const size_t len = (size_t)nb * edges_per_block * pair;
+            if ((err = cudaEventRecord(hc->done[c], s)) != cudaSuccess) return err;
+            if ((err = cudaStreamWaitEvent(hc->copy_stream, hc->done[c], 0)) != cudaSuccess) return err;
+            if ((err = cudaMemcpyAsync((char*)hc->h_edges + off_b, (const char*)d_out + off_b, len,
+                                       cudaMemcpyDeviceToHost, hc->copy_stream)) != cudaSuccess)
+                return err;
+        }
+    }
+    if (hc) {
+        // the caller's stream waits for the last copy
+        if ((err = cudaEventRecord(hc->copied, hc->copy_stream)) != cudaSuccess) return err;
+        if ((err = cudaStreamWaitEvent(s, hc->copied, 0)) != cudaSuccess) return err;
     }
     return cudaGetLastError();
 }

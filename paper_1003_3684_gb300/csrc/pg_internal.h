@@ -65,7 +65,20 @@ uint64_t pba_segment_length(uint64_t N_e, uint32_t S);
 cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s);
 int pba_setup(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t faction_width,
               double inter_frac, uint64_t seed, int id64, PbaGeom* g, uint64_t* n_edges);
-cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s);
+// Optional copy of the edge list to host memory, overlapped with the emit
+// kernels: emit runs in `chunks` block ranges and each range is copied on
+// copy_stream as soon as it is written; `s` then waits for the last copy.
+struct HostCopy {
+    void* h_edges;
+    uint32_t chunks;                 // at most kMaxCopyChunks
+    cudaStream_t copy_stream;
+    cudaEvent_t done[32];
+    cudaEvent_t copied;
+};
+constexpr uint32_t kMaxCopyChunks = 32;
+
+cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s,
+                       const HostCopy* hc = nullptr);
 
 // CSR assembly.
 size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices);

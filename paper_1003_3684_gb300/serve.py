@@ -1,0 +1,273 @@
+"""Serving loop: continuous batching of graph-generation requests.
+
+Requests (serial BA or stochastic Kronecker graphs, CSR wanted) arrive at any
+time. The server keeps a FIFO of waiting requests and a byte budget of device
+memory. At every scheduling step it
+  1. retires batches whose CUDA event has completed (their requests are done;
+     latency = completion - arrival),
+  2. admits waiting requests, in arrival order, while their bytes (edge list
+     while generating + CSR kept on the device) fit the remaining budget,
+  3. launches the admitted requests as one batch on a free stream: one
+     persistent generation launch for all of them (gen_batch), then each
+     request's CSR (edges_to_csr) on the same stream, then an event.
+Batches on different streams overlap on the GPU, so requests that arrive
+while others are running are admitted and started as soon as a stream and
+memory free up -- continuous batching rather than a queue drained in rounds.
+Results stay on the device until the client releases them.
+
+The server never synchronises the device except through event queries; the
+only host work per request is planning and launching.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def job_for_edges(kind: str, edges: int, seed: int, initiator=None):
+    """Generation job with about `edges` edges (the serving workload's mapping):
+    serial BA with m = 4 and n = ceil(E / 4), or Kronecker with
+    k = ceil(log2(E / 16)) and exactly E edges."""
+    if kind == "pba":
+        return dict(kind="pba", n=max(1, -(-edges // 4)), m=4, n0=5, seed=seed)
+    from .workloads import KRON_INITIATOR
+    k = max(1, math.ceil(math.log2(max(edges, 32) / 16)))
+    return dict(kind="kron", initiator=initiator or KRON_INITIATOR, k=k, n_edges=edges, seed=seed)
+
+
+def job_edges(job) -> int:
+    if job["kind"] == "pba":
+        return job["n"] * job["m"] + job["n0"] * (job["n0"] - 1) // 2
+    return job["n_edges"]
+
+
+def job_vertices(job) -> int:
+    if job["kind"] == "pba":
+        return job["n0"] + job["n"]
+    return job["initiator_n0"] ** job["k"] if "initiator_n0" in job else len(job["initiator"]) ** job["k"]
+
+
+def job_bytes(job) -> int:
+    """Device bytes a request holds: edge list (8 B/edge, freed after CSR) and
+    its CSR (row_ptr 8 B/vertex, col 4 B/edge)."""
+    E, N = job_edges(job), job_vertices(job)
+    return E * 8 + (N + 1) * 8 + E * 4
+
+
+@dataclass
+class Request:
+    rid: int
+    job: dict
+    arrival: float
+    nbytes: int
+    admitted: float | None = None
+    launched: float | None = None
+    done: float | None = None
+    row_ptr: object = None
+    col: object = None
+    held: int = 0          # budget bytes this request holds right now
+
+    @property
+    def latency(self):
+        return None if self.done is None else self.done - self.arrival
+
+
+@dataclass
+class _Batch:
+    requests: list
+    stream: object
+    event: object
+    keep: list = field(default_factory=list)
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 64 << 30, n_streams: int = 2, max_batch_jobs: int = 256,
+                 max_batch_edges: int = 1 << 28, tile_edges: int = 4096, device="cuda",
+                 clock=time.perf_counter, per_graph: bool = False):
+        """per_graph=True replaces the batched launch by one gen_pba /
+        gen_kronecker call per request (the baseline a batching server beats)."""
+        self.per_graph = per_graph
+        self.budget = budget_bytes
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.max_batch_jobs = max_batch_jobs
+        self.max_batch_edges = max_batch_edges
+        self.tile_edges = tile_edges
+        self.device_name = device
+        self.clock = clock
+        self.n_streams = n_streams
+        self.busy = {i: None for i in range(n_streams)}
+        self.waiting: deque[Request] = deque()
+        self.admitted: deque[Request] = deque()
+        self.completed: list[Request] = []
+        self._next_id = 0
+        self.launches = 0
+        self._cuda = False
+
+    def _init_cuda(self):
+        """Device objects, created at the first launch."""
+        import torch
+
+        import paper_1003_3684_gb300 as pg
+        self.pg, self.torch = pg, torch
+        self.device = torch.device(self.device_name)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.n_streams)]
+        self.batch_ws = [torch.empty(pg.pg_batch_workspace_size(), dtype=torch.uint8,
+                                     device=self.device) for _ in range(self.n_streams)]
+        self.csr_ws = [None] * self.n_streams
+        self._cuda = True
+
+    # ------------------------------------------------------------------
+    def submit(self, job: dict, now: float | None = None) -> Request:
+        now = self.clock() if now is None else now
+        r = Request(self._next_id, job, now, job_bytes(job))
+        if r.nbytes > self.budget:
+            raise ValueError(f"request of {r.nbytes} bytes exceeds the {self.budget}-byte budget")
+        self._next_id += 1
+        self.waiting.append(r)
+        return r
+
+    def release(self, r: Request):
+        """Client is done with a result: free its device memory and budget."""
+        r.row_ptr = r.col = None
+        self.in_use -= r.held
+        r.held = 0
+
+    def pending(self) -> int:
+        return len(self.waiting) + len(self.admitted) + sum(b is not None for b in self.busy.values())
+
+    # ------------------------------------------------------------------
+    def _retire(self, now):
+        for i, b in self.busy.items():
+            if b is not None and b.event.query():
+                for r in b.requests:
+                    r.done = now
+                    # the edge list is dropped once its CSR exists
+                    self.in_use -= job_edges(r.job) * 8
+                    r.held -= job_edges(r.job) * 8
+                    self.completed.append(r)
+                self.busy[i] = None
+
+    def _admit(self, now):
+        while self.waiting and self.in_use + self.waiting[0].nbytes <= self.budget:
+            r = self.waiting.popleft()
+            r.admitted = now
+            r.held = r.nbytes
+            self.in_use += r.nbytes
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+            self.admitted.append(r)
+
+    def _next_batch(self):
+        batch, edges = [], 0
+        while (self.admitted and len(batch) < self.max_batch_jobs and
+               (not batch or edges + job_edges(self.admitted[0].job) <= self.max_batch_edges)):
+            r = self.admitted.popleft()
+            edges += job_edges(r.job)
+            batch.append(r)
+        return batch
+
+    def _launch(self, now):
+        if not self._cuda:
+            self._init_cuda()
+        torch, pg = self.torch, self.pg
+        for i, b in self.busy.items():
+            if b is not None or not self.admitted:
+                continue
+            batch = self._next_batch()
+            s = self.streams[i]
+            with torch.cuda.stream(s):
+                if self.per_graph:
+                    offs = np.cumsum([0] + [job_edges(r.job) + (job_edges(r.job) & 1)
+                                            for r in batch])
+                    arena = torch.empty((max(int(offs[-1]), 1), 2), dtype=torch.int32,
+                                        device=self.device)
+                    for k, r in enumerate(batch):
+                        j, a = r.job, int(offs[k])
+                        sl = arena[a:a + job_edges(j)]
+                        if j["kind"] == "pba":
+                            pg.gen_pba(j["n"], j["m"], 1, j["n0"], 1, 0.0, j["seed"], out=sl,
+                                       stream=s)
+                        else:
+                            pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"],
+                                             out=sl, stream=s)
+                        self.launches += 1
+                    plan = None
+                    offsets = [int(x) for x in offs]
+                else:
+                    plan = pg.BatchPlan([r.job for r in batch], tile_edges=self.tile_edges,
+                                        device=self.device)
+                    arena = torch.empty((max(plan.total_edges, 1), 2), dtype=torch.int32,
+                                        device=self.device)
+                    pg.gen_batch(plan, arena=arena, workspace=self.batch_ws[i], stream=s)
+                    self.launches += 1
+                    offsets = [int(x) for x in plan.offsets]
+                need = max(pg.pg_csr_workspace_size(job_edges(r.job), job_vertices(r.job))
+                           for r in batch)
+                if self.csr_ws[i] is None or self.csr_ws[i].numel() < need:
+                    self.csr_ws[i] = torch.empty(need, dtype=torch.uint8, device=self.device)
+                for k, r in enumerate(batch):
+                    a = offsets[k]
+                    z = a + job_edges(r.job)
+                    r.row_ptr, r.col = pg.edges_to_csr(arena[a:z], job_vertices(r.job),
+                                                       workspace=self.csr_ws[i], stream=s)
+                    r.launched = now
+                    self.launches += 1
+                ev = torch.cuda.Event()
+                ev.record(s)
+            self.busy[i] = _Batch(batch, s, ev, keep=[plan, arena])
+
+    def step(self, now: float | None = None) -> int:
+        """One scheduling step; returns the number of requests completed."""
+        now = self.clock() if now is None else now
+        before = len(self.completed)
+        self._retire(now)
+        self._admit(now)
+        self._launch(now)
+        return len(self.completed) - before
+
+    def drain(self):
+        while self.pending():
+            self.step()
+
+
+def poisson_workload(rate: float, duration: float, seed: int = 0, lo_exp: int = 12,
+                     hi_exp: int = 26):
+    """Arrival times (exponential gaps) and jobs: half BA, half Kronecker,
+    edge counts log-uniform in [2^lo_exp, 2^hi_exp]; job i uses seed i."""
+    rng = np.random.default_rng(seed)
+    t, out, i = 0.0, [], 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        kind = "pba" if rng.random() < 0.5 else "kron"
+        edges = int(2 ** rng.uniform(lo_exp, hi_exp))
+        out.append((t, job_for_edges(kind, edges, seed=i)))
+        i += 1
+    return out
+
+
+def run_open_loop(server: Server, arrivals, release: bool = True, max_wall: float | None = None):
+    """Replay arrivals in real time against the server (open loop: arrivals do
+    not wait for completions). Returns the completed requests."""
+    t0 = server.clock()
+    idx = 0
+    n = len(arrivals)
+    while idx < n or server.pending():
+        now = server.clock() - t0
+        while idx < n and arrivals[idx][0] <= now:
+            server.submit(arrivals[idx][1], now=t0 + arrivals[idx][0])
+            idx += 1
+        done = server.step(server.clock())
+        if release and done:
+            for r in server.completed[-done:]:
+                server.release(r)
+        if max_wall is not None and now > max_wall:
+            break
+        if not done and idx < n and arrivals[idx][0] > now + 2e-4:
+            time.sleep(min(1e-3, arrivals[idx][0] - now))
+    return server.completed

@@ -19,12 +19,20 @@ CONFIGS = {
     # stochastic Kronecker, k = 20 levels (2^20 vertices), 16 * 2^20 edges, plus CSR
     "kron_k20_m16x_csr": dict(kind="kron", initiator=KRON_INITIATOR, k=20,
                               n_edges=16 * 2**20, seed=7, csr=True),
+    # the same initiator at k = 26 (2^26 vertices, 2^30 edges: 8.6 GB of pairs)
+    "kron_k26_m16x_csr": dict(kind="kron", initiator=KRON_INITIATOR, k=26,
+                              n_edges=16 * 2**26, seed=7, csr=True),
     # two-phase PBA at the paper's headline size: 2^30 new vertices in 1024
     # blocks of 2^20, 5 edges each, inter-block fraction 0.1
     "pba_n2p30_b1024_m5": dict(kind="pba", n=2**30, m=5, blocks=1024, n0=6, faction_width=1,
                                inter_frac=0.1, seed=3),
     # 4096 independent graphs of uneven sizes in one persistent launch
     "batch_4096_mixed": dict(kind="batch", n_jobs=4096, seed=0),
+    # served requests: Poisson arrivals at 2000/s, half BA / half Kronecker,
+    # edge counts log-uniform in 2^12..2^26, CSR kept on the device, admission
+    # by a 64 GB device-memory budget
+    "serve_poisson_2000": dict(kind="serve", rate=2000.0, duration=20.0, budget=64 << 30,
+                               seed=0),
 }
 
 

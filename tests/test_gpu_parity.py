@@ -139,6 +139,18 @@ def test_pba_id64_and_repeat_is_identical():
     assert_same(host(a, True), ref)
 
 
+@pytest.mark.parametrize("B,n_b,m", [(16, 30_000, 5), (1, 50_000, 3), (300, 100, 2)])
+def test_pba_to_host_copy_matches(B, n_b, m):
+    n = B * n_b
+    E = pg.pg_pba_edge_count(n, m, B, m + 1)
+    host_buf = torch.empty((E, 2), dtype=torch.int32, pin_memory=True)
+    dev = pg.gen_pba_to_host(host_buf, n, m, B, m + 1, 1, 0.1, 5)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(host_buf, dev.cpu())
+    ref, _, _ = o.pba(n, m, B, m + 1, 1, 0.1, 5)
+    assert_same(host_buf.numpy().view(np.uint32).astype(np.uint64), ref)
+
+
 def test_pba_other_stream():
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
@@ -246,5 +258,35 @@ def test_csr_kron_workload_full():
     torch.cuda.synchronize()
     assert_same(host(got), ref_edges)
     ref_rp, ref_col = o.csr(ref_edges, 2 ** cfg["k"])
+    assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp)
+    assert_same(host(col), ref_col)
+
+
+def _grouped(seed, N, max_row, M_rows, id64=False):
+    """Seeded list already grouped by source (rows of random lengths)."""
+    rng = np.random.default_rng(seed)
+    srcs = np.sort(rng.choice(N, size=M_rows, replace=False))
+    lens = rng.integers(0, max_row + 1, size=M_rows)
+    src = np.repeat(srcs, lens)
+    dst = rng.integers(0, N, size=src.size)
+    dst[: src.size // 7] = dst[0] if src.size else 0          # duplicates
+    e = np.stack([src, dst], 1).astype(np.uint64 if id64 else np.uint32)
+    return e
+
+
+@pytest.mark.parametrize("max_row,id64", [(1, False), (5, False), (32, False), (33, False),
+                                          (200, False), (32, True)])
+def test_csr_grouped_lists(max_row, id64):
+    N = 3000
+    csr_check(_grouped(max_row, N, max_row, 1500, id64), N, id64)
+
+
+def test_csr_of_gpu_ba_output_is_canonical():
+    """Serial BA output is grouped by source: the CSR must equal the oracle's."""
+    n, m, n0, seed = 20_000, 6, 7, 4
+    edges = pg.gen_pba(n, m, 1, n0, 1, 0.0, seed)
+    rp, col = pg.edges_to_csr(edges, n0 + n)
+    torch.cuda.synchronize()
+    ref_rp, ref_col = o.csr(o.ba(n, m, n0, seed), n0 + n)
     assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp)
     assert_same(host(col), ref_col)

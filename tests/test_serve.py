@@ -1,0 +1,141 @@
+"""Serving loop: admission and scheduling on the host (fake device, fake
+clock), and on the GPU the same CSR for every request alone and in a mix."""
+import numpy as np
+import pytest
+
+from paper_1003_3684_gb300 import serve
+
+
+class FakeEvent:
+    def __init__(self, clock, ready_at):
+        self.clock, self.ready_at = clock, ready_at
+
+    def query(self):
+        return self.clock() >= self.ready_at
+
+
+class FakeServer(serve.Server):
+    """Server whose 'device' finishes a batch 1 ms per million edges later."""
+
+    def _launch(self, now):
+        for i, b in self.busy.items():
+            if b is not None or not self.admitted:
+                continue
+            batch = self._next_batch()
+            for r in batch:
+                r.launched = now
+            cost = sum(serve.job_edges(r.job) for r in batch) / 1e9
+            self.busy[i] = serve._Batch(batch, None, FakeEvent(self.clock, now + cost))
+            self.launches += 1
+
+
+def fake_clock():
+    t = [0.0]
+
+    def clock():
+        return t[0]
+
+    def advance(dt):
+        t[0] += dt
+
+    return clock, advance
+
+
+def test_budget_is_never_exceeded_and_fifo_admission():
+    clock, advance = fake_clock()
+    jobs = [serve.job_for_edges("pba" if i % 2 else "kron", 2 ** (12 + i % 10), seed=i)
+            for i in range(200)]
+    budget = 3 * max(serve.job_bytes(j) for j in jobs)
+    srv = FakeServer(budget_bytes=budget, n_streams=2, clock=clock)
+    reqs = [srv.submit(j, now=0.0) for j in jobs]
+    while srv.pending():
+        srv.step()
+        assert srv.in_use <= budget
+        for r in srv.completed:
+            srv.release(r)
+        advance(1e-3)
+    assert srv.peak_in_use <= budget
+    assert all(r.done is not None for r in reqs)
+    admitted = [r.admitted for r in reqs]
+    assert admitted == sorted(admitted)                 # FIFO
+    assert srv.in_use == 0
+
+
+def test_requests_arriving_while_busy_are_started_without_waiting_for_all():
+    """Continuous batching: a request arriving while one batch runs starts on
+    the other stream before that batch finishes."""
+    clock, advance = fake_clock()
+    srv = FakeServer(budget_bytes=1 << 40, n_streams=2, clock=clock)
+    big = srv.submit(serve.job_for_edges("kron", 2**26, seed=1), now=0.0)
+    srv.step()
+    advance(1e-3)
+    small = srv.submit(serve.job_for_edges("pba", 2**12, seed=2), now=clock())
+    srv.step()
+    assert small.launched is not None and big.done is None
+    while srv.pending():
+        advance(1e-3)
+        srv.step()
+    assert small.done < big.done
+
+
+def test_oversized_request_is_rejected():
+    srv = FakeServer(budget_bytes=1000)
+    with pytest.raises(ValueError):
+        srv.submit(serve.job_for_edges("pba", 2**20, seed=0))
+
+
+def test_poisson_workload_shape():
+    arr = serve.poisson_workload(2000, 2.0, seed=0)
+    t = np.array([a for a, _ in arr])
+    assert 3500 < len(arr) < 4500 and (np.diff(t) > 0).all()
+    E = np.array([serve.job_edges(j) for _, j in arr])
+    assert E.min() >= 2**12 and E.max() <= 2**26 + 16
+    kinds = [j["kind"] for _, j in arr]
+    assert 0.45 < kinds.count("pba") / len(kinds) < 0.55
+
+
+@pytest.mark.gpu
+def test_results_same_alone_and_in_the_mix():
+    import torch
+
+    import oracle as o
+    rng = np.random.default_rng(3)
+    jobs = [serve.job_for_edges("pba" if i % 2 else "kron", int(2 ** rng.uniform(12, 19)), seed=i)
+            for i in range(40)]
+    # alone: one request at a time on one stream
+    alone = []
+    srv = serve.Server(budget_bytes=8 << 30, n_streams=1, max_batch_jobs=1)
+    for j in jobs:
+        r = srv.submit(j)
+        srv.drain()
+        torch.cuda.synchronize()
+        alone.append((r.row_ptr.cpu().numpy().copy(), r.col.cpu().numpy().copy()))
+        srv.release(r)
+    # in the mix: all at once, small budget so admission staggers them
+    budget = 6 * max(serve.job_bytes(j) for j in jobs)
+    srv = serve.Server(budget_bytes=budget, n_streams=3, max_batch_jobs=16)
+    reqs = [srv.submit(j) for j in jobs]
+    srv.drain()
+    torch.cuda.synchronize()
+    assert srv.peak_in_use <= budget
+    for r, (rp, col) in zip(reqs, alone):
+        assert np.array_equal(r.row_ptr.cpu().numpy(), rp)
+        assert np.array_equal(r.col.cpu().numpy(), col)
+    # and the small ones against the oracle
+    for r in reqs[:6]:
+        j = r.job
+        e = (o.ba(j["n"], j["m"], j["n0"], j["seed"]) if j["kind"] == "pba"
+             else o.kron(j["initiator"], j["k"], j["n_edges"], j["seed"]))
+        ref_rp, ref_col = o.csr(e, serve.job_vertices(j))
+        assert np.array_equal(r.row_ptr.cpu().numpy().view(np.uint64), ref_rp)
+        assert np.array_equal(r.col.cpu().numpy().view(np.uint32).astype(np.uint64), ref_col)
+
+
+@pytest.mark.gpu
+def test_open_loop_short_run():
+    arr = serve.poisson_workload(500, 0.5, seed=1, hi_exp=20)
+    srv = serve.Server(budget_bytes=4 << 30, n_streams=2)
+    done = serve.run_open_loop(srv, arr)
+    assert len(done) == len(arr)
+    lat = np.array([r.latency for r in done])
+    assert (lat > 0).all()
