@@ -46,6 +46,47 @@ KERNEL_WORK = {
 }
 
 
+# Sorting kernels of the CSR step: HBM-bound; unit = one edge per launch, bytes
+# = what one launch must move at least (a radix pass reads and writes every
+# pair; the histogram pass and the sortedness check read every pair once).
+CSR_WORK = {
+    "csr_radix_scatter": dict(ops=0, bytes=16),
+    "csr_radix_hist": dict(ops=0, bytes=8),
+    "csr_check": dict(ops=0, bytes=8),
+    "csr_finish": dict(ops=0, bytes=12),
+}
+
+
+def dram_traffic_table():
+    """DRAM bytes per unit measured by ncu, from profiles/dram_traffic.md.
+
+    Each row names the kernel, the source file it is compiled from and that
+    file's sha256 prefix at capture time; a row whose file has changed since
+    is ignored (the counters no longer describe the kernel that runs).
+    """
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    table = {}
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return table
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) < 4 or not cells[0].startswith("`"):
+            continue
+        kernel, src, sha = cells[0].strip("`"), cells[1].strip("`"), cells[2].strip("`")
+        try:
+            per_unit = float(cells[3])
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                cur = hashlib.sha256(fh.read()).hexdigest()[:12]
+        except (OSError, ValueError):
+            continue
+        if cur == sha:
+            table[kernel] = per_unit
+    return table
+
+
 def kron_work(k: int, id_bytes: int = 4):
     # ceil(k/4) Philox calls + per level: 3 threshold compares + 2 shift-ors
     return dict(ops=PHILOX_OPS * ((k + 3) // 4) + 5 * k, bytes=2 * id_bytes)
@@ -518,6 +559,9 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                 pg.edges_to_csr(out, N, row_ptr=row_ptr, col=col, workspace=ws)
         units = {"kron_descent_n0_2": M}
         work = {"kron_descent_n0_2": kron_work(k)}
+        if cfg.get("csr"):
+            units.update({kk: M for kk in CSR_WORK})
+            work.update(CSR_WORK)
         out_bytes = M * 8 + ((N + 1) * 8 + M * 4 if cfg.get("csr") else 0)
         cfg_json = dict(workload=args.workload, initiator=cfg["initiator"], k=k, n_edges=M,
                         seed=cfg["seed"], csr=bool(cfg.get("csr")), edges_per_step=M,
@@ -574,15 +618,17 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
         byte_rate = u * work[dom]["bytes"] / per_launch_s
         t_alu = u * work[dom]["ops"] / alu_peak
         t_hbm = u * work[dom]["bytes"] / hbm_peak
+        per_unit = dram_traffic_table().get(dom)
+        traffic = per_unit * u if per_unit is not None else None
         if t_alu >= t_hbm:
             roof = dict(bound="alu", kernel=dom, achieved=ops_rate / 1e12, peak=alu_peak / 1e12,
-                        unit="Tops/s (int32 lane ops)", frac=ops_rate / alu_peak, traffic=None,
+                        unit="Tops/s (int32 lane ops)", frac=ops_rate / alu_peak, traffic=traffic,
                         hbm=dict(achieved=byte_rate / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
                                  frac=byte_rate / hbm_peak),
                         peak_source=f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz")
         else:
             roof = dict(bound="hbm", kernel=dom, achieved=byte_rate / 1e9, peak=peaks["hbm_gbs"],
-                        unit="GB/s", frac=byte_rate / hbm_peak, traffic=None,
+                        unit="GB/s", frac=byte_rate / hbm_peak, traffic=traffic,
                         peak_source=f"{peaks['source']} MEASURED_PEAKS hbm_gbs")
         roof["ms_per_launch"] = per_launch_s * 1000.0
         roof["units_per_launch"] = u
