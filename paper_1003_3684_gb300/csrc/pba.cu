@@ -168,33 +168,26 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     uint32_t pend_k = 0, pend_v = 0;
     uint32_t own = 0;   // entries equal to p (the most frequent value) counted here
     while (__any_sync(0xFFFFFFFFu, active || pend)) {
-        uint4 w = make_uint4(0, 0, 0, 0);
-        if (active) w = philox(make_uint4(cur, 0u, p, 1u), g.key);
+        // every lane draws (an idle lane's draw is discarded), so the trip is
+        // straight-line code apart from the deferred store and count
+        const uint4 w = philox(make_uint4(cur, 0u, p, 1u), g.key);
         if (pend) {   // the value loaded one trip ago
             my[pend_k] = (uint16_t)pend_v;
-            if (pend_v == p) ++own;
-            else atomicAdd(&hist[pend_v], 1u);
-            pend = false;
+            if (pend_v != p) atomicAdd(&hist[pend_v], 1u);
         }
-        bool done = false;
-        if (active) {
-            if (coin_on && w.z < g.coin_thr) {
-                pend_v = fresh_block(w.w, g.B, g.W, phi);
-                done = true;
-            } else {
-                const uint32_t r = uniform32(w.x, w.y, cur);
-                if (r < L) {
-                    pend_v = __ldg(Ap + r);
-                    done = true;
-                } else {
-                    cur = r;
-                }
-            }
-            if (done) {
-                pend = true;
-                pend_k = item;
-            }
+        own += (pend && pend_v == p) ? 1u : 0u;
+        const bool coin = coin_on && w.z < g.coin_thr;
+        const uint32_t r = uniform32(w.x, w.y, cur);
+        const bool hit = !coin && r < L;
+        const bool done = active && (coin || hit);
+        uint32_t v = fresh_block(w.w, g.B, g.W, phi);
+        if (active && hit) v = __ldg(Ap + r);
+        if (done) {
+            pend_v = v;
+            pend_k = item;
         }
+        pend = done;
+        if (active && !done) cur = r;
         const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
         if (done) {
             item = next + __popc(dm & lt);
@@ -400,6 +393,35 @@ __device__ __forceinline__ bool t_step32(uint32_t& cur, uint32_t q, const QRecip
     }
     cur = e2;
     return false;
+}
+
+// The same link with one rarely taken branch (a seed slot): the side-0 value
+// is computed on every link and selected, so lanes of a warp that stop and
+// lanes that continue run the same instructions.
+__device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip& c,
+                                         const PbaGeom& g, uint32_t& v)
+{
+    const uint32_t nb = (uint32_t)g.n_b;
+    const uint32_t sig = sigma32(cur, c);
+    uint32_t before;
+    if (g.nb_shift != 0xFFFFFFFFu)
+        before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
+    else
+        before = (uint32_t)fdiv((uint64_t)sig * c.R + (nb - 1), g.div_nb);
+    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
+    const uint32_t e0 = (uint32_t)g.e0;
+    const uint32_t X = e0 + before;
+    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
+    const uint32_t e = (uint32_t)(s >> 32);
+    const uint32_t side = ((uint32_t)s) >> 31;
+    const uint32_t e2 = e - e0;
+    const bool seed = e < e0;
+    uint32_t vs = 0;
+    if (seed) vs = seed_endpoint(e, side, g.n0);
+    v = seed ? vs : g.n0 + sigma32(e2, c);
+    const bool fin = seed || side == 0;
+    cur = fin ? cur : e2;
+    return fin;
 }
 
 // Serial BA (blocks = 1): sigma(i) = i div m, E = sigma * m.
@@ -627,14 +649,17 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     }
     __syncwarp();
 
-    for (uint64_t base = lo; base < hi; base += kEmitRun) {
-        // rank: the run's block ids are loaded before the first match
-        uint32_t qv[kEmitItems];
+    // block ids of the first run; later runs are loaded one run ahead, while
+    // the chains of the current run execute
+    uint32_t qv[kEmitItems];
 #pragma unroll
-        for (int r = 0; r < kEmitItems; ++r) {
-            const uint64_t j = base + r * 32 + lane;
-            qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
-        }
+    for (int r = 0; r < kEmitItems; ++r) {
+        const uint64_t j = lo + r * 32 + lane;
+        qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
+    }
+    for (uint64_t base = lo; base < hi; base += kEmitRun) {
+        const uint32_t n = (uint32_t)((hi - base < kEmitRun) ? hi - base : kEmitRun);
+        // rank
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
             const uint32_t q = qv[r];
@@ -648,12 +673,44 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             ws.qs[r * 32 + lane] = (uint16_t)q;
         }
         __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r) {
+            const uint64_t j = base + kEmitRun + r * 32 + lane;
+            qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
+        }
         // chains: a lane that finishes an entry takes the next unclaimed one.
         // The loop body is kept straight-line -- load the new entry, reconverge,
         // then ONE link for every lane -- so a warp whose lanes are at
         // different depths still runs the link code once per trip.
         if constexpr (kFast && kEmitDual) {
             emit_chains_dual(ws, g, recip, lane);
+        } else if constexpr (kFast) {
+            // items [0, n); a lane that finishes an entry stores its value and
+            // claims the next unclaimed item (claims are in lane order)
+            uint32_t k = lane, next = 32, q = 0, cur = 0;
+            bool active = k < n;
+            QRecip c{0, 0, 0, 0};
+            if (active) {
+                q = ws.qs[k];
+                cur = (uint32_t)ws.item[k];
+                c = recip[q];
+            }
+            while (__any_sync(0xFFFFFFFFu, active)) {
+                uint32_t v;
+                const bool done = t_link32(cur, q, c, g, v) && active;
+                if (done) ws.item[k] = v;
+                const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+                if (done) {
+                    k = next + __popc(dm & lt);
+                    active = k < n;
+                    if (active) {
+                        q = ws.qs[k];
+                        cur = (uint32_t)ws.item[k];
+                        c = recip[q];
+                    }
+                }
+                next += __popc(dm);
+            }
         } else {
             uint32_t k = lane, next = 32, q = 0xFFFFu;
             bool active = true, fresh = true;
@@ -701,7 +758,6 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             }
         }
         __syncwarp();
-        const uint32_t n = (uint32_t)((hi - base < kEmitRun) ? hi - base : kEmitRun);
         auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
             s_ = src_base + fdiv32((uint32_t)(base + t2), g.div_m32);
             d_ = (uint64_t)ws.qs[t2] * g.span + (uint32_t)ws.item[t2];
