@@ -60,6 +60,7 @@ def lib():
             L.or_pba_endpoints.argtypes = [u32, u64, u64, u32, u64, u64, P]
             L.or_pba_substitute.argtypes = [P, u64, u32, P, P, P]
             L.or_pba.argtypes = [u64, u32, u32, u32, u32, dbl, u64, P, P, P]
+            L.or_pba_factions.argtypes = [u64, u32, u32, u32, P, P, dbl, u64, P, P, P]
             L.or_kron_thresholds.argtypes = [P, u32, P]
             L.or_kron_pick.argtypes = [P, u32, u32]
             L.or_kron_pick.restype = u32
@@ -67,7 +68,7 @@ def lib():
             L.or_kron_det.argtypes = [P, u32, u32, P, u64, P, P]
             L.or_csr.argtypes = [P, u64, u64, P, P]
             for name in ("or_ba", "or_pba_count", "or_pba_phase1_general", "or_pba_phase1", "or_pba_endpoints",
-                         "or_pba_substitute", "or_pba", "or_kron_thresholds", "or_kron",
+                         "or_pba_substitute", "or_pba", "or_pba_factions", "or_kron_thresholds", "or_kron",
                          "or_kron_det", "or_csr"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -163,6 +164,26 @@ def pba(n: int, m: int, B: int, n0: int, W: int, f: float, seed: int):
     cnt = np.zeros((B, B), dtype=np.uint64)
     fresh = np.zeros(1, dtype=np.uint64)
     _check(lib().or_pba(n, m, B, n0, W, f, seed, _ptr(out), _ptr(cnt), _ptr(fresh)), "pba")
+    return out[:n_edges], cnt, int(fresh[0])
+
+
+def pba_factions(n: int, m: int, B: int, n0: int, lists, f: float, seed: int):
+    """Two-phase PBA with explicit faction lists (lists[p]: block p's list).
+
+    Returns (edges, counts (B,B), fresh) like pba().
+    """
+    if len(lists) != B:
+        raise ValueError("one faction list per block")
+    foff = np.zeros(B + 1, dtype=np.uint32)
+    foff[1:] = np.cumsum([len(x) for x in lists])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, np.uint32) for x in lists])
+                                if B else np.zeros(1, np.uint32), dtype=np.uint32)
+    n_edges = B * (seed_edges(n0) + (n // B) * m)
+    out = np.zeros((max(n_edges, 1), 2), dtype=np.uint64)
+    cnt = np.zeros((B, B), dtype=np.uint64)
+    fresh = np.zeros(1, dtype=np.uint64)
+    _check(lib().or_pba_factions(n, m, B, n0, _ptr(foff), _ptr(flat), f, seed, _ptr(out),
+                                 _ptr(cnt), _ptr(fresh)), "pba_factions")
     return out[:n_edges], cnt, int(fresh[0])
 
 

@@ -297,11 +297,17 @@ int or_pba_substitute(const uint32_t* A, uint64_t len, uint32_t B, const uint64_
 /* b*(n0+n_b) .. b*(n0+n_b)+n0+n_b-1; its seed clique is the first n0.      */
 /* counts_out (B*B, row p = requester) and fresh_out may be NULL.           */
 /* ------------------------------------------------------------------------ */
-int or_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, double f,
-           uint64_t seed, uint64_t* out, uint64_t* counts_out, uint64_t* fresh_out)
+/* Two-phase PBA with explicit faction lists (Sec. 3, PBA method; Fig. 1):   */
+/* block p's list is flist[foff[p] .. foff[p+1]), the members of every       */
+/* faction p belongs to, in order (at least one entry, each < B).            */
+int or_pba_factions(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, const uint32_t* foff,
+                    const uint32_t* flist, double f, uint64_t seed, uint64_t* out,
+                    uint64_t* counts_out, uint64_t* fresh_out)
 {
-    if (m < 1 || n0 < 2 || B < 1 || W < 1 || B % W != 0 || n % B != 0) return 1;
+    if (m < 1 || n0 < 2 || B < 1 || n % B != 0) return 1;
     if (!(f >= 0.0 && f <= 1.0)) return 1;
+    for (uint32_t p = 0; p < B; ++p)
+        if (foff[p + 1] <= foff[p]) return 1;
     uint64_t n_b = n / B;
     uint64_t N_e = n_b * m;
     uint64_t e0 = seed_edge_count(n0);
@@ -323,7 +329,8 @@ int or_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, double f
     uint64_t fresh_total = 0;
     for (uint32_t p = 0; p < B; ++p) {
         uint64_t fr = 0;
-        rc = or_pba_phase1(p, B, W, N_e, f, seed, A + (uint64_t)p * N_e, c + (uint64_t)p * B, &fr);
+        rc = or_pba_phase1_general(p, B, flist + foff[p], foff[p + 1] - foff[p], N_e, f, seed,
+                                   A + (uint64_t)p * N_e, c + (uint64_t)p * B, &fr);
         if (rc) goto done;
         fresh_total += fr;
     }
@@ -362,6 +369,25 @@ done:
     if (T)
         for (uint32_t q = 0; q < B; ++q) free(T[q]);
     free(A); free(c); free(R); free(start); free(T); free(dst); free(ea); free(eb);
+    return rc;
+}
+
+/* Aligned factions of width W (reading R5): block p's list is the W blocks */
+/* of its group, phi = (p div W)*W, ..., phi + W - 1.                       */
+int or_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, double f,
+           uint64_t seed, uint64_t* out, uint64_t* counts_out, uint64_t* fresh_out)
+{
+    if (B < 1 || W < 1 || B % W != 0) return 1;
+    uint32_t* foff = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)B + 1));
+    uint32_t* flist = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)B * W);
+    if (!foff || !flist) { free(foff); free(flist); return 2; }
+    for (uint32_t p = 0; p < B; ++p) {
+        foff[p] = p * W;
+        for (uint32_t t = 0; t < W; ++t) flist[(size_t)p * W + t] = (p / W) * W + t;
+    }
+    foff[B] = B * W;
+    int rc = or_pba_factions(n, m, B, n0, foff, flist, f, seed, out, counts_out, fresh_out);
+    free(foff); free(flist);
     return rc;
 }
 

@@ -23,6 +23,9 @@ int or_pba_endpoints(uint32_t q, uint64_t R_q, uint64_t n_b, uint32_t n0, uint64
                      uint64_t len, uint32_t* T);
 int or_pba_substitute(const uint32_t* A, uint64_t len, uint32_t B, const uint64_t* start,
                       const uint32_t* const* T, uint32_t* out);
+int or_pba_factions(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, const uint32_t* foff,
+                    const uint32_t* flist, double f, uint64_t seed, uint64_t* out,
+                    uint64_t* counts_out, uint64_t* fresh_out);
 int or_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, double f,
            uint64_t seed, uint64_t* out, uint64_t* counts_out, uint64_t* fresh_out);
 

@@ -240,6 +240,73 @@ def test_pba_invariants(B, W, f):
         assert fresh == 0
 
 
+# Overlapping factions in the manner of Fig. 1: F0 = {0,1}, F1 = {1,2,3},
+# F2 = {3,4}, F3 = {4,5,0}; a block's list concatenates the factions it is in.
+FACTION_LISTS = [[0, 1, 4, 5, 0], [0, 1, 1, 2, 3], [1, 2, 3], [1, 2, 3, 3, 4], [3, 4, 4, 5, 0],
+                 [4, 5, 0]]
+
+
+def test_pba_factions_closure_without_inter_faction_picks():
+    """f = 0: phase 1 only copies earlier entries, so block p's targets stay
+    inside its own list (copies of the list itself)."""
+    B, n_b, m, n0 = 6, 500, 3, 4
+    e, cnt, fresh = o.pba_factions(B * n_b, m, B, n0, FACTION_LISTS, 0.0, seed=13)
+    span, per, e0 = n0 + n_b, n0 * (n0 - 1) // 2 + n_b * m, n0 * (n0 - 1) // 2
+    assert fresh == 0
+    for p in range(B):
+        q = e[p * per + e0:(p + 1) * per, 1].astype(np.int64) // span
+        assert set(q.tolist()) <= set(FACTION_LISTS[p])
+        assert set(np.nonzero(cnt[p])[0].tolist()) <= set(FACTION_LISTS[p])
+
+
+def test_pba_factions_exact_counts_when_every_pick_is_fresh():
+    """f = 1: entries below s_p copy the list, every later entry is a fresh
+    pick outside the list, so the counts of listed blocks are their
+    multiplicities in the list."""
+    B, n_b, m, n0 = 6, 300, 2, 3
+    _, cnt, fresh = o.pba_factions(B * n_b, m, B, n0, FACTION_LISTS, 1.0, seed=2)
+    N_e = n_b * m
+    assert fresh == sum(N_e - len(L) for L in FACTION_LISTS)
+    for p, L in enumerate(FACTION_LISTS):
+        listed = np.bincount(L, minlength=B)
+        inside = np.isin(np.arange(B), L)
+        assert np.array_equal(cnt[p][inside], listed[inside].astype(np.uint64))
+        assert int(cnt[p][~inside].sum()) == N_e - len(L)
+
+
+def test_pba_factions_invariants():
+    B, n_b, m, n0 = 6, 400, 3, 4
+    e, cnt, _ = o.pba_factions(B * n_b, m, B, n0, FACTION_LISTS, 0.3, seed=71)
+    e = e.astype(np.int64)
+    span, e0 = n0 + n_b, n0 * (n0 - 1) // 2
+    per = e0 + n_b * m
+    R = cnt.sum(axis=0).astype(np.int64)
+    assert cnt.sum(axis=1).tolist() == [n_b * m] * B
+    indeg = np.zeros(B, np.int64)
+    for p in range(B):
+        gen = e[p * per + e0:(p + 1) * per]
+        assert np.array_equal(gen[:, 0], p * span + n0 + np.arange(n_b * m) // m)
+        np.add.at(indeg, gen[:, 1] // span, 1)
+        # the first entries copy the list
+        L = FACTION_LISTS[p]
+        assert (gen[:len(L), 1] // span).tolist() == L
+    assert indeg.tolist() == R.tolist()
+
+
+def test_pba_factions_duplicate_self_list_is_independent_ba():
+    """Lists [p, p] and f = 0 keep every block on itself: the graph equals B
+    independent serial BA runs, as with width-1 factions."""
+    n, m, B, n0, seed = 4 * 250, 2, 4, 3, 5
+    e, cnt, _ = o.pba_factions(n, m, B, n0, [[p, p] for p in range(B)], 0.0, seed)
+    ref, rcnt, _ = o.pba(n, m, B, n0, 1, 0.0, seed)
+    assert np.array_equal(e, ref) and np.array_equal(cnt, rcnt)
+
+
+def test_pba_factions_rejects_empty_list():
+    with pytest.raises(Exception):
+        o.pba_factions(40, 2, 2, 3, [[0], []], 0.1, 1)
+
+
 def test_pba_fresh_count_binomial():
     B, W, f, n_b, m = 16, 2, 0.1, 2000, 2
     total = 0
