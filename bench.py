@@ -630,6 +630,13 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             roof = dict(bound="hbm", kernel=dom, achieved=byte_rate / 1e9, peak=peaks["hbm_gbs"],
                         unit="GB/s", frac=byte_rate / hbm_peak, traffic=traffic,
                         peak_source=f"{peaks['source']} MEASURED_PEAKS hbm_gbs")
+        if roof["bound"] == "alu":
+            # the same fraction against the measured Philox ceiling of this GPU
+            rate = pg.philox_rate()
+            meas = rate * PHILOX_OPS
+            roof["alu_measured"] = dict(philox_per_s=rate, peak=meas / 1e12,
+                                        unit="Tops/s (int32 lane ops)", frac=ops_rate / meas,
+                                        source="pg_philox_probe: Philox4x32-10 calls/s x 60 ops")
         roof["ms_per_launch"] = per_launch_s * 1000.0
         roof["units_per_launch"] = u
         roof["ops_per_unit"] = work[dom]["ops"]

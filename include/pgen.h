@@ -57,6 +57,16 @@ const char* pg_status_string(pg_status s);
 int pg_device_sm_count(void);
 const char* pg_version(void);
 
+/* Throughput probe (not part of the method): launches one kernel in which
+ * each of pg_philox_probe_threads() threads (8 CTAs of 256 per SM) makes
+ * calls_per_thread Philox4x32-10 calls and writes one folded word to
+ * d_out[thread] (out_words >= pg_philox_probe_threads()). Time it with
+ * events on `stream`: threads * calls / seconds is the device's Philox rate,
+ * the measured ceiling of the integer-bound kernels. */
+size_t pg_philox_probe_threads(void);
+pg_status pg_philox_probe(uint32_t calls_per_thread, uint32_t* d_out, size_t out_words,
+                          void* stream);
+
 /* ------------------------------------------------------------------------
  * Parallel Barabasi-Albert generator (Sec. 3, PBA method; Fig. 1).
  *
@@ -108,6 +118,64 @@ pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
                           uint32_t faction_width, double inter_frac, uint64_t seed, pg_idwidth w,
                           void* h_edges, void* d_edges, uint64_t cap_edges, uint64_t* n_edges_out,
                           void* d_ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * PBA with general faction lists (Sec. 3, PBA method: a block's factions
+ * need not be aligned groups and may overlap, as F0..F2 of Fig. 1).
+ *
+ * pg_pba_faction_table (host only, no CUDA call) packs the lists into the
+ * device layout: block p's list is h_members[h_offsets[p] .. h_offsets[p+1])
+ * (blocks + 1 offsets), the members of every faction p belongs to, in
+ * order: 1 to 1024 entries, each < blocks, repeats allowed. h_table
+ * receives pg_pba_faction_table_size(blocks) bytes (one 4112-byte record
+ * per block: list size, size of the complement, the list, and the blocks
+ * outside the list in ascending order). PG_EINVAL for a bad list, PG_ENOSPC
+ * when table_bytes is too small. The caller copies the table to device
+ * memory (16-byte aligned) by any means it likes.
+ *
+ * gen_pba_factions is gen_pba with that table in place of faction_width:
+ * entry t < s_p of block p's phase-1 list is the t-th entry of p's list;
+ * a later entry is, with probability inter_frac, the x-th block outside
+ * p's list (x = floor(w3 * (blocks outside) / 2^32)), otherwise a copy of
+ * a uniform earlier entry. A block whose list names every block makes no
+ * inter-faction picks. Aligned width-W lists give gen_pba's output exactly.
+ * Same workspace, output layout and vertex ids as gen_pba; blocks = 1 is
+ * serial BA (the only possible list names block 0).
+ * ---------------------------------------------------------------------- */
+size_t pg_pba_faction_table_size(uint32_t blocks);
+pg_status pg_pba_faction_table(uint32_t blocks, const uint32_t* h_offsets,
+                               const uint32_t* h_members, void* h_table, size_t table_bytes);
+pg_status gen_pba_factions(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                           const void* d_faction_table, double inter_frac, uint64_t seed,
+                           pg_idwidth w, void* d_edges, uint64_t cap_edges,
+                           uint64_t* n_edges_out, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * PBA in parts: the edges of any range of blocks, on demand (the paper has
+ * no counterpart; it excludes writing the graph out from its timings).
+ *
+ * pg_pba_prepare runs phase 1, the count exchange and its scan, and leaves
+ * their results in d_ws (pg_pba_workspace_size bytes). Factions: aligned
+ * width faction_width, or the device table of gen_pba_factions when
+ * d_faction_table is not NULL (faction_width is then ignored).
+ * gen_pba_blocks then writes the edges of blocks [b_begin, b_end), block
+ * b_begin's first edge at d_edges[0]: (b_end - b_begin) * (e0 + n_b*m)
+ * edges, each equal to the same edge of gen_pba / gen_pba_factions with
+ * the same arguments. It reads the workspace only, so any number of ranges
+ * may follow one prepare -- in any order, into buffers much smaller than
+ * the whole graph (stream a graph to host or disk range by range, or
+ * regenerate a lost range after a restart from the arguments alone). The
+ * workspace must not change between the two calls; n, m, blocks, n0 and
+ * seed must match. blocks = 1 (serial BA) needs no prepare: the only range
+ * is [0, 1).
+ * ---------------------------------------------------------------------- */
+pg_status pg_pba_prepare(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                         uint32_t faction_width, const void* d_faction_table, double inter_frac,
+                         uint64_t seed, void* d_ws, size_t ws_bytes, void* stream);
+pg_status gen_pba_blocks(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint64_t seed,
+                         pg_idwidth w, uint32_t b_begin, uint32_t b_end, void* d_edges,
+                         uint64_t cap_edges, uint64_t* n_edges_out, const void* d_ws,
+                         size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * gen_pba without a caller-supplied workspace (the paper has no
@@ -164,6 +232,16 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
                         uint64_t seed, pg_kron_mode mode, pg_idwidth w, void* d_edges,
                         uint64_t cap_edges, uint64_t* n_edges_out, void* stream);
 
+/* Edges [e_begin, e_end) of the graph gen_kronecker makes with the same
+ * arguments (e_end <= n_edges, or <= e0^k when deterministic), written to
+ * d_edges[0 .. e_end - e_begin). Every edge depends only on its index, so
+ * ranges may be generated in any order, on any device, and concatenate to
+ * the whole list. */
+pg_status gen_kronecker_range(const double* h_initiator, uint32_t n0, uint32_t k,
+                              uint64_t n_edges, uint64_t seed, pg_kron_mode mode, pg_idwidth w,
+                              uint64_t e_begin, uint64_t e_end, void* d_edges,
+                              uint64_t cap_edges, void* stream);
+
 /* ------------------------------------------------------------------------
  * CSR assembly (not in the paper; the usual input format of the graph
  * algorithms the generated graphs feed).
@@ -178,9 +256,12 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
  * d_col        n_edges ids of width w: the destinations grouped by source,
  *              ascending within each row (duplicates kept). The result does
  *              not depend on scheduling.
- * d_ws         workspace of pg_csr_workspace_size() bytes, 256-byte aligned.
- * An id >= n_vertices is not checked on the device; it is the caller's
- * contract (the generators above always satisfy it).
+ * d_ws         workspace of pg_csr_workspace_size() bytes, 256-byte aligned
+ *              (two copies of the list plus per-tile digit counts).
+ * Every id must be < n_vertices (the generators above always satisfy it).
+ * The device does not report a violation, but it never indexes memory with
+ * such an id: an edge whose src is out of range is dropped, and the rows
+ * and col entries it would have touched are unspecified.
  * ---------------------------------------------------------------------- */
 size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices);
 pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices,

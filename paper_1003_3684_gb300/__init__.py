@@ -22,11 +22,15 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
+
 __all__ = [
     "PG_OK", "PG_EINVAL", "PG_ENOSPC", "PG_ECUDA", "PG_ETIMEOUT", "PG_ENOMEM",
     "PgenError", "lib", "library_path",
     "pg_status_string", "pg_device_sm_count", "pg_version",
     "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba", "gen_pba_to_host",
+    "pba_faction_table", "gen_pba_factions", "pg_pba_prepare", "gen_pba_blocks",
+    "gen_kronecker_range", "philox_rate",
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
 ]
@@ -168,6 +172,55 @@ def gen_pba(n: int, m: int, blocks: int = 1, n0: int | None = None, faction_widt
     return out[:n_out.value]
 
 
+def pba_faction_table(lists) -> np.ndarray:
+    """Packs per-block faction lists (lists[p]: block p's list) into the
+    device table of gen_pba_factions (host work only). Returns a uint8 array."""
+    L = lib()
+    if not getattr(L, "_fac_ready", False):
+        L.pg_pba_faction_table_size.argtypes = [u32]
+        L.pg_pba_faction_table_size.restype = sz
+        L.pg_pba_faction_table.argtypes = [u32, vp, vp, vp, sz]
+        L.pg_pba_faction_table.restype = i32
+        L.gen_pba_factions.argtypes = [u64, u32, u32, u32, vp, dbl, u64, i32, vp, u64,
+                                       C.POINTER(u64), vp, sz, vp]
+        L.gen_pba_factions.restype = i32
+        L._fac_ready = True
+    B = len(lists)
+    offs = np.zeros(B + 1, np.uint32)
+    offs[1:] = np.cumsum([len(x) for x in lists])
+    members = np.ascontiguousarray(np.concatenate([np.asarray(x, np.uint32) for x in lists])
+                                   if B else np.zeros(1, np.uint32), dtype=np.uint32)
+    size = L.pg_pba_faction_table_size(B)
+    table = np.zeros(max(size, 16), np.uint8)
+    _check("pg_pba_faction_table",
+           L.pg_pba_faction_table(B, offs.ctypes.data, members.ctypes.data, table.ctypes.data, size))
+    return table
+
+
+def gen_pba_factions(n: int, m: int, factions, n0: int | None = None, inter_frac: float = 0.1,
+                     seed: int = 0, id64: bool = False, out=None, workspace=None, stream=None,
+                     device="cuda"):
+    """Two-phase PBA with general faction lists: ``factions[p]`` lists the
+    members of every faction block p belongs to (blocks = len(factions))."""
+    import torch
+    blocks = len(factions)
+    n0 = m + 1 if n0 is None else n0
+    table = torch.from_numpy(pba_faction_table(factions)).to(device)
+    E = pg_pba_edge_count(n, m, blocks, n0)
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(E, 1), 2), dtype, device)
+    if blocks > 1 and workspace is None:
+        workspace = _empty(max(pg_pba_workspace_size(n, m, blocks), 1), torch.uint8, out.device)
+    ws_bytes = workspace.numel() if workspace is not None else 0
+    n_out = u64(0)
+    st = lib().gen_pba_factions(n, m, blocks, n0, _ptr(table), float(inter_frac), seed,
+                                PG_ID64 if id64 else PG_ID32, _ptr(out), out.shape[0],
+                                C.byref(n_out), _ptr(workspace), ws_bytes, _stream(stream))
+    _check("gen_pba_factions", st)
+    return out[:n_out.value]
+
+
 def gen_pba_to_host(host_out, n: int, m: int, blocks: int = 1, n0: int | None = None,
                     faction_width: int = 1, inter_frac: float = 0.1, seed: int = 0,
                     id64: bool = False, out=None, workspace=None, stream=None, device="cuda"):
@@ -231,6 +284,104 @@ def gen_kronecker(initiator, k: int, n_edges: int = 0, seed: int = 0, determinis
                              C.byref(n_out), _stream(stream))
     _check("gen_kronecker", st)
     return out[:n_out.value]
+
+
+def _range_lib():
+    L = lib()
+    if not getattr(L, "_range_ready", False):
+        L.gen_kronecker_range.argtypes = [vp, u32, u32, u64, u64, i32, i32, u64, u64, vp, u64, vp]
+        L.gen_kronecker_range.restype = i32
+        L.pg_pba_prepare.argtypes = [u64, u32, u32, u32, u32, vp, dbl, u64, vp, sz, vp]
+        L.pg_pba_prepare.restype = i32
+        L.gen_pba_blocks.argtypes = [u64, u32, u32, u32, u64, i32, u32, u32, vp, u64,
+                                     C.POINTER(u64), vp, sz, vp]
+        L.gen_pba_blocks.restype = i32
+        L._range_ready = True
+    return L
+
+
+def gen_kronecker_range(initiator, k: int, n_edges: int, e_begin: int, e_end: int, seed: int = 0,
+                        deterministic: bool = False, id64: bool = False, out=None, stream=None,
+                        device="cuda"):
+    """Edges [e_begin, e_end) of gen_kronecker's graph, as an (e_end - e_begin, 2) tensor."""
+    import torch
+    P = _initiator(initiator)
+    count = e_end - e_begin
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(count, 1), 2), dtype, device)
+    st = _range_lib().gen_kronecker_range(
+        P.ctypes.data_as(vp), P.shape[0], k, n_edges, seed,
+        PG_KRON_DETERMINISTIC if deterministic else PG_KRON_STOCHASTIC,
+        PG_ID64 if id64 else PG_ID32, e_begin, e_end, _ptr(out), out.shape[0], _stream(stream))
+    _check("gen_kronecker_range", st)
+    return out[:max(count, 0)]
+
+
+def pg_pba_prepare(n: int, m: int, blocks: int, n0: int | None = None, faction_width: int = 1,
+                   inter_frac: float = 0.1, seed: int = 0, factions=None, workspace=None,
+                   stream=None, device="cuda"):
+    """Phase 1 and the count scan of PBA into a workspace tensor (returned);
+    gen_pba_blocks then emits any block range from it. ``factions`` (lists
+    per block) replaces faction_width when given."""
+    import torch
+    n0 = m + 1 if n0 is None else n0
+    if workspace is None:
+        workspace = _empty(max(pg_pba_workspace_size(n, m, blocks), 1), torch.uint8, device)
+    table = None
+    if factions is not None:
+        table = torch.from_numpy(pba_faction_table(factions)).to(workspace.device)
+    st = _range_lib().pg_pba_prepare(n, m, blocks, n0, faction_width, _ptr(table),
+                                     float(inter_frac), seed, _ptr(workspace), workspace.numel(),
+                                     _stream(stream))
+    _check("pg_pba_prepare", st)
+    return workspace
+
+
+def gen_pba_blocks(workspace, n: int, m: int, blocks: int, b_begin: int, b_end: int,
+                   n0: int | None = None, seed: int = 0, id64: bool = False, out=None,
+                   stream=None):
+    """Edges of blocks [b_begin, b_end) from a prepared workspace."""
+    import torch
+    n0 = m + 1 if n0 is None else n0
+    per = pg_pba_edge_count(n, m, blocks, n0) // max(blocks, 1)
+    count = (b_end - b_begin) * per
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(count, 1), 2), dtype, workspace.device)
+    n_out = u64(0)
+    st = _range_lib().gen_pba_blocks(n, m, blocks, n0, seed, PG_ID64 if id64 else PG_ID32,
+                                     b_begin, b_end, _ptr(out), out.shape[0], C.byref(n_out),
+                                     _ptr(workspace), workspace.numel(), _stream(stream))
+    _check("gen_pba_blocks", st)
+    return out[:n_out.value]
+
+
+def philox_rate(calls_per_thread: int = 2048, reps: int = 3, device="cuda") -> float:
+    """Measured Philox4x32-10 calls per second of the device (best of reps,
+    CUDA events on the current stream), from the library's probe kernel."""
+    import torch
+    L = lib()
+    if not getattr(L, "_probe_ready", False):
+        L.pg_philox_probe_threads.restype = sz
+        L.pg_philox_probe.argtypes = [u32, vp, sz, vp]
+        L.pg_philox_probe.restype = i32
+        L._probe_ready = True
+    n = int(L.pg_philox_probe_threads())
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream(out.device)
+    best = None
+    for i in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _check("pg_philox_probe", L.pg_philox_probe(calls_per_thread, _ptr(out), n,
+                                                    vp(stream.cuda_stream)))
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        if i > 0 and (best is None or ms < best):      # the first launch is a warm-up
+            best = ms
+    return n * calls_per_thread / (best / 1000.0)
 
 
 def pg_csr_workspace_size(n_edges: int, n_vertices: int) -> int:

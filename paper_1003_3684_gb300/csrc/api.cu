@@ -4,6 +4,7 @@
 // device untouched.
 #include <cmath>
 #include <cstring>
+#include <vector>
 #include <mutex>
 
 #include "../../include/pgen.h"
@@ -188,6 +189,105 @@ pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t
     return from_cuda(launch_pba(g, w == PG_ID64, d_edges, d_ws, s));
 }
 
+size_t pg_pba_faction_table_size(uint32_t blocks)
+{
+    if (blocks < 1 || blocks > 1024) return 0;
+    return (size_t)blocks * kFacStride * sizeof(uint16_t);
+}
+
+pg_status pg_pba_faction_table(uint32_t blocks, const uint32_t* h_offsets,
+                               const uint32_t* h_members, void* h_table, size_t table_bytes)
+{
+    if (blocks < 1 || blocks > 1024 || !h_offsets || !h_members || !h_table) return PG_EINVAL;
+    for (uint32_t p = 0; p < blocks; ++p) {
+        if (h_offsets[p + 1] <= h_offsets[p] || h_offsets[p + 1] - h_offsets[p] > kFacSlots)
+            return PG_EINVAL;
+        for (uint32_t t = h_offsets[p]; t < h_offsets[p + 1]; ++t)
+            if (h_members[t] >= blocks) return PG_EINVAL;
+    }
+    if (table_bytes < pg_pba_faction_table_size(blocks)) return PG_ENOSPC;
+    uint16_t* tab = (uint16_t*)h_table;
+    std::memset(tab, 0, pg_pba_faction_table_size(blocks));
+    std::vector<uint8_t> inside(blocks);
+    for (uint32_t p = 0; p < blocks; ++p) {
+        uint16_t* rec = tab + (size_t)p * kFacStride;
+        const uint32_t a = h_offsets[p], s = h_offsets[p + 1] - a;
+        std::fill(inside.begin(), inside.end(), 0);
+        for (uint32_t t = 0; t < s; ++t) {
+            rec[kFacHeader + t] = (uint16_t)h_members[a + t];
+            inside[h_members[a + t]] = 1;
+        }
+        uint32_t n_out = 0;
+        for (uint32_t b = 0; b < blocks; ++b)
+            if (!inside[b]) rec[kFacHeader + kFacSlots + n_out++] = (uint16_t)b;
+        rec[0] = (uint16_t)s;
+        rec[1] = (uint16_t)n_out;
+    }
+    return PG_OK;
+}
+
+pg_status gen_pba_factions(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                           const void* d_faction_table, double inter_frac, uint64_t seed,
+                           pg_idwidth w, void* d_edges, uint64_t cap_edges,
+                           uint64_t* n_edges_out, void* d_ws, size_t ws_bytes, void* stream)
+{
+    const PbaCheck c = check_pba(n, m, blocks, n0, 1, inter_frac, w);
+    if (c.st != PG_OK) return c.st;
+    if (n_edges_out) *n_edges_out = c.edges;
+    if (cap_edges < c.edges) return PG_ENOSPC;
+    if (c.edges > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+    if (!d_faction_table || !aligned(d_faction_table, 16)) return PG_EINVAL;
+    PbaGeom g = make_geom(c.n_b, c.N_e, m, blocks, n0, 1, inter_frac, seed);
+    cudaStream_t s = (cudaStream_t)stream;
+    // one block: every list holds only block 0, so phase 1 is trivial
+    if (blocks == 1) return from_cuda(launch_ba(g, w == PG_ID64, d_edges, s));
+    g.ftab = (const uint16_t*)d_faction_table;
+    const size_t need = pba_workspace_layout(g.A_stride, blocks, g.S).total;
+    if (!d_ws || ws_bytes < need) return PG_ENOMEM;
+    if (!aligned(d_ws, 256)) return PG_EINVAL;
+    return from_cuda(launch_pba(g, w == PG_ID64, d_edges, d_ws, s));
+}
+
+pg_status pg_pba_prepare(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
+                         uint32_t faction_width, const void* d_faction_table, double inter_frac,
+                         uint64_t seed, void* d_ws, size_t ws_bytes, void* stream)
+{
+    const uint32_t W = d_faction_table ? 1 : faction_width;
+    const PbaCheck c = check_pba(n, m, blocks, n0, W, inter_frac, PG_ID64);
+    if (c.st != PG_OK) return c.st;
+    if (blocks == 1) return PG_OK;              // serial BA has no phase 1
+    if (d_faction_table && !aligned(d_faction_table, 16)) return PG_EINVAL;
+    PbaGeom g = make_geom(c.n_b, c.N_e, m, blocks, n0, W, inter_frac, seed);
+    g.ftab = (const uint16_t*)d_faction_table;
+    const size_t need = pba_workspace_layout(g.A_stride, blocks, g.S).total;
+    if (!d_ws || ws_bytes < need) return PG_ENOMEM;
+    if (!aligned(d_ws, 256)) return PG_EINVAL;
+    return from_cuda(launch_pba_phase1(g, d_ws, (cudaStream_t)stream));
+}
+
+pg_status gen_pba_blocks(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint64_t seed,
+                         pg_idwidth w, uint32_t b_begin, uint32_t b_end, void* d_edges,
+                         uint64_t cap_edges, uint64_t* n_edges_out, const void* d_ws,
+                         size_t ws_bytes, void* stream)
+{
+    const PbaCheck c = check_pba(n, m, blocks, n0, 1, 0.0, w);
+    if (c.st != PG_OK) return c.st;
+    if (b_begin > b_end || b_end > blocks) return PG_EINVAL;
+    const uint64_t per = c.edges / blocks;
+    const uint64_t count = (uint64_t)(b_end - b_begin) * per;
+    if (n_edges_out) *n_edges_out = count;
+    if (cap_edges < count) return PG_ENOSPC;
+    if (count == 0) return PG_OK;
+    if (!d_edges || !aligned(d_edges, 16)) return PG_EINVAL;
+    const PbaGeom g = make_geom(c.n_b, c.N_e, m, blocks, n0, 1, 0.0, seed);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (blocks == 1) return from_cuda(launch_ba(g, w == PG_ID64, d_edges, s));
+    const size_t need = pba_workspace_layout(g.A_stride, blocks, g.S).total;
+    if (!d_ws || ws_bytes < need) return PG_ENOMEM;
+    if (!aligned(d_ws, 256)) return PG_EINVAL;
+    return from_cuda(launch_pba_emit(g, w == PG_ID64, d_edges, d_ws, b_begin, b_end, s));
+}
+
 }  // extern "C"
 
 namespace pgen {
@@ -275,9 +375,16 @@ uint64_t pg_kron_edge_count(const double* h_initiator, uint32_t n0, uint32_t k, 
     return (total >> 63) ? 0 : (uint64_t)total;
 }
 
-pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
-                        uint64_t seed, pg_kron_mode mode, pg_idwidth w, void* d_edges,
-                        uint64_t cap_edges, uint64_t* n_edges_out, void* stream)
+}  // extern "C"
+
+namespace {
+
+// gen_kronecker and gen_kronecker_range: edges [e_begin, e_end) of the graph
+// (e_end = ~0: to the last edge) into d_edges[0 ...].
+pg_status kron_common(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
+                      uint64_t seed, pg_kron_mode mode, pg_idwidth w, uint64_t e_begin,
+                      uint64_t e_end, void* d_edges, uint64_t cap_edges, uint64_t* n_edges_out,
+                      void* stream)
 {
     if (!h_initiator || k < 1 || k > 64 || (w != PG_ID32 && w != PG_ID64)) return PG_EINVAL;
     if (mode != PG_KRON_STOCHASTIC && mode != PG_KRON_DETERMINISTIC) return PG_EINVAL;
@@ -304,10 +411,13 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
         while (c + 1 < cells && T[c] == 0) ++c;
         p.n_zero = c;
         for (; c + 1 < cells && T[c] < ((uint64_t)1 << 32); ++c) p.u[p.n_u++] = (uint32_t)(T[c] - 1);
-        if (n_edges_out) *n_edges_out = n_edges;
-        if (cap_edges < n_edges) return PG_ENOSPC;
-        if (n_edges > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
-        return from_cuda(launch_kron_stochastic(p, w == PG_ID64, d_edges, 0, n_edges, s));
+        if (e_end == ~(uint64_t)0) e_end = n_edges;
+        if (e_begin > e_end || e_end > n_edges) return PG_EINVAL;
+        const uint64_t count = e_end - e_begin;
+        if (n_edges_out) *n_edges_out = count;
+        if (cap_edges < count) return PG_ENOSPC;
+        if (count > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+        return from_cuda(launch_kron_stochastic(p, w == PG_ID64, d_edges, e_begin, count, s));
     }
 
     KronDetParams p;
@@ -326,10 +436,35 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
     p.k = k;
     p.e0 = e0;
     p.div_e0 = make_fastdiv(e0);
-    if (n_edges_out) *n_edges_out = (uint64_t)total;
-    if (cap_edges < (uint64_t)total) return PG_ENOSPC;
-    if (!d_edges || !aligned(d_edges, 16)) return PG_EINVAL;
-    return from_cuda(launch_kron_det(p, w == PG_ID64, d_edges, (uint64_t)total, s));
+    if (e_end == ~(uint64_t)0) e_end = (uint64_t)total;
+    if (e_begin > e_end || e_end > (uint64_t)total) return PG_EINVAL;
+    const uint64_t count = e_end - e_begin;
+    if (n_edges_out) *n_edges_out = count;
+    if (cap_edges < count) return PG_ENOSPC;
+    if (count > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+    return from_cuda(launch_kron_det(p, w == PG_ID64, d_edges, e_begin, count, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint64_t n_edges,
+                        uint64_t seed, pg_kron_mode mode, pg_idwidth w, void* d_edges,
+                        uint64_t cap_edges, uint64_t* n_edges_out, void* stream)
+{
+    return kron_common(h_initiator, n0, k, n_edges, seed, mode, w, 0, ~(uint64_t)0, d_edges,
+                       cap_edges, n_edges_out, stream);
+}
+
+pg_status gen_kronecker_range(const double* h_initiator, uint32_t n0, uint32_t k,
+                              uint64_t n_edges, uint64_t seed, pg_kron_mode mode, pg_idwidth w,
+                              uint64_t e_begin, uint64_t e_end, void* d_edges,
+                              uint64_t cap_edges, void* stream)
+{
+    if (e_end == ~(uint64_t)0) return PG_EINVAL;
+    return kron_common(h_initiator, n0, k, n_edges, seed, mode, w, e_begin, e_end, d_edges,
+                       cap_edges, nullptr, stream);
 }
 
 size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices)

@@ -1,7 +1,14 @@
 // CSR assembly of a generated edge list.
 //
-// The rows must hold their destinations in ascending order, so the edge list
-// is sorted by the key (src, dst) with a least-significant-digit radix sort:
+// Rows hold their destinations in ascending order (duplicates kept), so the
+// result is unique for a given multiset of edges.
+//
+// Grouped lists (non-decreasing src, as gen_pba and serial BA write them,
+// rows of at most kGroupedMaxRow edges): csr_check finds the list grouped and
+// csr_grouped places each destination at its rank within its own row and
+// marks each row's end in row_ptr.
+//
+// Any other list: least-significant-digit radix sort of the (src, dst) keys,
 // first the digits of dst, then those of src, up to 10 bits per pass. Each
 // pass is three kernels:
 //   radix_hist     per-tile digit counts, stored digit-major H[d][tile];
@@ -12,16 +19,13 @@
 //                  and a scattered write of the (src, dst) pair.
 // No atomics decide any position, so the result does not depend on the
 // schedule, and a power-law row (a hub with 10^5 edges) costs no more than
-// any other key. A final pass writes col and marks each row's end in
-// row_ptr; a parallel prefix maximum then gives row_ptr[v] = first index with
-// src >= v for every v, rows without edges included.
+// any other key. A final pass writes col and marks row ends. Both paths then
+// take a parallel prefix maximum over row_ptr, which fills the rows without
+// edges. The sort kernels read the sortedness flag and return at once when
+// the grouped path applied, so no host round trip decides the path.
 //
-// Fast path: edge lists that are already grouped by source (non-decreasing
-// src, as gen_pba and serial BA write them) with rows of at most
-// kGroupedMaxRow edges skip the sort. csr_check sets a device flag when the
-// list is not such a list; otherwise csr_grouped places each destination at
-// its rank within its own row. The sort kernels read the flag and return at
-// once when the fast path applied, so no host round trip decides the path.
+// Ids at or above n_vertices are never used as an index (such edges are
+// dropped), so a bad list cannot make a kernel write out of bounds.
 #include "pg_internal.h"
 #include "pg_trace.h"
 
@@ -303,22 +307,25 @@ __global__ void __launch_bounds__(256) csr_check_kernel(const typename PairOf<Id
                                                         uint64_t M, uint32_t* __restrict__ sort_needed)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;                 // one atomic per warp, not one per pair
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         const uint64_t src = s[i].x;
         const bool starts = (i == 0) || s[i - 1].x != src;
-        if (i > 0 && (uint64_t)s[i - 1].x > src) atomicOr(sort_needed, 1u);
-        if (starts && i + kGroupedMaxRow < M && (uint64_t)s[i + kGroupedMaxRow].x == src)
-            atomicOr(sort_needed, 1u);
+        bad |= i > 0 && (uint64_t)s[i - 1].x > src;
+        bad |= starts && i + kGroupedMaxRow < M && (uint64_t)s[i + kGroupedMaxRow].x == src;
     }
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(sort_needed, 1u);
 }
 
 // Row ends of a list sorted (or grouped) by source: the last edge i of row v
 // writes row_ptr[v + 1] = i + 1. A prefix maximum over row_ptr then fills the
 // rows without edges (row_ptr starts zeroed).
 template <typename P>
-__device__ __forceinline__ void mark_row_end(const P* s, uint64_t M, uint64_t i, uint64_t* row_ptr)
+__device__ __forceinline__ void mark_row_end(const P* s, uint64_t M, uint64_t N, uint64_t i,
+                                             uint64_t* row_ptr)
 {
-    if (i + 1 == M || s[i + 1].x != s[i].x) row_ptr[(uint64_t)s[i].x + 1] = i + 1;
+    const uint64_t v = s[i].x;
+    if (v < N && (i + 1 == M || s[i + 1].x != s[i].x)) row_ptr[v + 1] = i + 1;
 }
 
 // Grouped list: destination of edge i goes to its row start + its rank among
@@ -326,7 +333,7 @@ __device__ __forceinline__ void mark_row_end(const P* s, uint64_t M, uint64_t i,
 // their multiplicity).
 template <typename Id>
 __global__ void __launch_bounds__(256) csr_grouped_kernel(const typename PairOf<Id>::T* __restrict__ s,
-                                                          uint64_t M, Id* __restrict__ col,
+                                                          uint64_t M, uint64_t N, Id* __restrict__ col,
                                                           uint64_t* __restrict__ row_ptr,
                                                           const uint32_t* __restrict__ sort_needed)
 {
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(256) csr_grouped_kernel(const typename PairOf<
             rank += (dj < d) || (dj == d && j < i);
         }
         col[a + rank] = (Id)d;
-        mark_row_end(s, M, i, row_ptr);
+        mark_row_end(s, M, N, i, row_ptr);
     }
 }
 
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(256) max_apply_kernel(uint64_t* __restrict__ d
 
 template <typename Id>
 __global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<Id>::T* __restrict__ s,
-                                                         uint64_t M, uint64_t* __restrict__ row_ptr,
+                                                         uint64_t M, uint64_t N, uint64_t* __restrict__ row_ptr,
                                                          Id* __restrict__ col,
                                                          const uint32_t* __restrict__ sort_needed)
 {
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<I
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         col[i] = (Id)s[i].y;
-        mark_row_end(s, M, i, row_ptr);
+        mark_row_end(s, M, N, i, row_ptr);
     }
 }
 
@@ -528,7 +535,7 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
     {
         TraceScope trace("csr_check", s);
         csr_check_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, sort_needed);
-        csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, (Id*)d_col, d_row_ptr,
+        csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, N, (Id*)d_col, d_row_ptr,
                                                    sort_needed);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -572,7 +579,7 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
         }
     }
     TraceScope trace("csr_finish", s);
-    csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, d_row_ptr, (Id*)d_col, sort_needed);
+    csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed);
     uint64_t* rpart = (uint64_t*)(ws + L.off_rpart);
     max_reduce_kernel<<<(unsigned)L.n_rparts, 256, 0, s>>>(d_row_ptr, N + 1, rpart);
     max_parts_kernel<<<1, 1024, 0, s>>>(rpart, L.n_rparts);

@@ -174,7 +174,8 @@ __device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint
 
 template <typename Id>
 __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ KronDetParams p,
-                                                       Id* __restrict__ out, uint64_t n_edges)
+                                                       Id* __restrict__ out, uint64_t e_begin,
+                                                       uint64_t n_edges)
 {
     __shared__ uint16_t ab[kMaxDetSeedEdges];
     for (uint32_t t = threadIdx.x; t < p.e0; t += blockDim.x) ab[t] = p.ab[t];
@@ -184,10 +185,10 @@ __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ K
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
         const uint64_t e = 2 * t;
         uint64_t r0, c0;
-        kron_det_edge(p, ab, e, r0, c0);
+        kron_det_edge(p, ab, e_begin + e, r0, c0);
         if (e + 1 < n_edges) {
             uint64_t r1, c1;
-            kron_det_edge(p, ab, e + 1, r1, c1);
+            kron_det_edge(p, ab, e_begin + e + 1, r1, c1);
             Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
             Pair2<Id>::store1(out, e, r0, c0);
@@ -236,18 +237,18 @@ cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, u
     return cudaGetLastError();
 }
 
-cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t n_edges,
-                            cudaStream_t s)
+cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t e_begin,
+                            uint64_t n_edges, cudaStream_t s)
 {
     if (n_edges == 0) return cudaSuccess;
     const uint64_t pairs = (n_edges + 1) / 2;
     TraceScope trace("kron_det", s);
     if (id64) {
         auto k = kron_det_kernel<uint64_t>;
-        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, n_edges);
+        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
     } else {
         auto k = kron_det_kernel<uint32_t>;
-        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, n_edges);
+        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
     }
     return cudaGetLastError();
 }

@@ -71,6 +71,43 @@ __device__ __forceinline__ uint32_t fresh_block(uint32_t w3, uint32_t B, uint32_
     return x < phi ? x : x + W;
 }
 
+// The factions of block p: an aligned group of W blocks starting at phi, or
+// (kTable) the block's record of the faction table. An inter-faction pick
+// takes the x-th block outside the list, x uniform below the number of such
+// blocks; for an aligned group that is fresh_block.
+template <bool kTable>
+struct Faction {
+    const uint16_t* rec;
+    uint32_t s, n_out, phi;
+    bool coin;
+    __device__ __forceinline__ Faction(const PbaGeom& g, uint32_t p)
+    {
+        if constexpr (kTable) {
+            rec = g.ftab + (size_t)p * kFacStride;
+            s = rec[0];
+            n_out = rec[1];
+            phi = 0;
+            coin = g.coin_thr > 0 && n_out > 0;
+        } else {
+            rec = nullptr;
+            s = g.W;
+            n_out = g.B - g.W;
+            phi = (p / g.W) * g.W;
+            coin = g.coin_on != 0;
+        }
+    }
+    __device__ __forceinline__ uint32_t member(uint32_t t) const
+    {
+        if constexpr (kTable) return rec[kFacHeader + t];
+        else return phi + t;
+    }
+    __device__ __forceinline__ uint32_t fresh(uint32_t w3, const PbaGeom& g) const
+    {
+        if constexpr (kTable) return rec[kFacHeader + kFacSlots + __umulhi(w3, n_out)];
+        else return fresh_block(w3, g.B, g.W, phi);
+    }
+};
+
 // Adds a smem histogram of B counters to cnt row (p, sgm), skipping zeros.
 __device__ __forceinline__ void flush_counts(const uint32_t* hist, uint32_t* cnt,
                                              const PbaGeom& g, uint32_t p, uint32_t sgm)
@@ -84,6 +121,7 @@ __device__ __forceinline__ void flush_counts(const uint32_t* hist, uint32_t* cnt
 // Phase 1, prefix [0, P) of each block, built in shared memory.
 // grid = B, block = kPrefixThreads, dynamic smem = P*2 (rounded to 16) + B*4.
 // ---------------------------------------------------------------------------
+template <bool kTable>
 __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
     const __grid_constant__ PbaGeom g, uint16_t* __restrict__ A, uint32_t* __restrict__ cnt)
 {
@@ -91,10 +129,10 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
     uint16_t* sA = reinterpret_cast<uint16_t*>(smem);
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((g.P * 2 + 15) & ~15u));
     const uint32_t p = blockIdx.x;
-    const uint32_t phi = (p / g.W) * g.W;
+    const Faction<kTable> F(g, p);
     const uint32_t P = g.P;
-    const uint32_t s = g.W < P ? g.W : P;
-    for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) sA[t] = (uint16_t)(phi + t);
+    const uint32_t s = F.s < P ? F.s : P;
+    for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) sA[t] = (uint16_t)F.member(t);
     __syncthreads();
     for (uint32_t L = s; L < P;) {
         const uint32_t hi = (2 * L < P) ? 2 * L : P;
@@ -102,8 +140,8 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
             uint32_t cur = j, v;
             for (;;) {
                 const uint4 w = philox(make_uint4(cur, 0u, p, 1u), g.key);
-                if (g.coin_on && w.z < g.coin_thr) {
-                    v = fresh_block(w.w, g.B, g.W, phi);
+                if (F.coin && w.z < g.coin_thr) {
+                    v = F.fresh(w.w, g);
                     break;
                 }
                 const uint32_t r = uniform32(w.x, w.y, cur);
@@ -140,6 +178,7 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
 // A copy that lands below L loads A_p[r]; the load is consumed one loop trip
 // later (after the next Philox), so its latency overlaps arithmetic.
 // ---------------------------------------------------------------------------
+template <bool kTable>
 __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_constant__ PbaGeom g,
                                                                 uint32_t L, uint32_t hi,
                                                                 uint16_t* __restrict__ A,
@@ -151,7 +190,7 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     const uint32_t p = blockIdx.y;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t phi = (p / g.W) * g.W;
+    const Faction<kTable> F(g, p);
     uint16_t* Ap = A + (uint64_t)p * g.A_stride;
     uint16_t* my = stage + wid * kPassRun;              // this warp's run, staged
     const uint32_t chunk = L + blockIdx.x * kPassChunk;   // a granule: one segment
@@ -160,7 +199,7 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
 
     const uint32_t run = chunk + wid * kPassRun;
     const uint32_t n_items = run < hi ? ((hi - run < kPassRun) ? hi - run : kPassRun) : 0;
-    const bool coin_on = g.coin_on != 0;
+    const bool coin_on = F.coin;
     uint32_t next = 32, item = lane;
     uint32_t cur = run + item;
     bool active = item < n_items;
@@ -180,7 +219,12 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
         const uint32_t r = uniform32(w.x, w.y, cur);
         const bool hit = !coin && r < L;
         const bool done = active && (coin || hit);
-        uint32_t v = fresh_block(w.w, g.B, g.W, phi);
+        uint32_t v = 0;
+        if constexpr (kTable) {
+            if (active && coin) v = F.fresh(w.w, g);   // a table read only for a pick
+        } else {
+            v = F.fresh(w.w, g);
+        }
         if (active && hit) v = __ldg(Ap + r);
         if (done) {
             pend_v = v;
@@ -621,7 +665,8 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const __grid_constant__ PbaGeom g, const uint16_t* __restrict__ A,
     const uint64_t* __restrict__ off, const uint64_t* __restrict__ R,
     const FastDiv* __restrict__ divR, const QRecip* __restrict__ recip,
-    const uint32_t* __restrict__ wide_flag, Id* __restrict__ out, uint32_t block_off)
+    const uint32_t* __restrict__ wide_flag, Id* __restrict__ out, uint32_t block_off,
+    uint32_t out_block0)
 {
     using CurT = typename std::conditional<kFast, uint32_t, uint64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -636,7 +681,7 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const uint16_t* Ap = A + (uint64_t)p * g.A_stride;
     const uint64_t lo = (uint64_t)sw * g.seg_len;
     const uint64_t hi = (lo + g.seg_len < g.N_e) ? lo + g.seg_len : g.N_e;
-    const uint64_t out_block = (uint64_t)p * (g.e0 + g.N_e);
+    const uint64_t out_block = (uint64_t)(p - out_block0) * (g.e0 + g.N_e);
     const uint64_t src_base = (uint64_t)p * g.span + g.n0;
 
     const uint64_t* offrow = off + ((uint64_t)p * g.S + sw) * B;
@@ -892,44 +937,69 @@ cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s,
-                       const HostCopy* hc)
+namespace {
+
+struct PbaBuffers {
+    uint16_t* A;
+    uint32_t* cnt;
+    uint64_t *off, *R;
+    FastDiv* divR;
+    QRecip* recip;
+    uint32_t* wide;
+};
+
+PbaBuffers pba_buffers(const PbaGeom& g, void* d_ws)
 {
-    if (g.B > kMaxBlocks) return cudaErrorInvalidValue;
     const PbaWorkspace L = pba_workspace_layout(g.A_stride, g.B, g.S);
     unsigned char* ws = (unsigned char*)d_ws;
-    uint16_t* A = (uint16_t*)(ws + L.off_A);
-    uint32_t* cnt = (uint32_t*)(ws + L.off_cnt);
-    uint64_t* off = (uint64_t*)(ws + L.off_off);
-    uint64_t* R = (uint64_t*)(ws + L.off_R);
-    FastDiv* divR = (FastDiv*)(ws + L.off_magic);
-    QRecip* recip = (QRecip*)(ws + L.off_recip);
-    uint32_t* wide = (uint32_t*)(ws + L.off_flag);
-    cudaError_t err;
+    return PbaBuffers{(uint16_t*)(ws + L.off_A), (uint32_t*)(ws + L.off_cnt),
+                      (uint64_t*)(ws + L.off_off), (uint64_t*)(ws + L.off_R),
+                      (FastDiv*)(ws + L.off_magic), (QRecip*)(ws + L.off_recip),
+                      (uint32_t*)(ws + L.off_flag)};
+}
 
-    const size_t smem_fast = kEmitWarps * sizeof(EmitWarpSmem<uint32_t>);
-    const size_t smem_wide = kEmitWarps * sizeof(EmitWarpSmem<uint64_t>);
-    static bool attrs_set = false;
-    if (!attrs_set) {
-        cudaFuncSetAttribute(pba_prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kPrefixMax * 2 + kMaxBlocks * 4));
-        cudaFuncSetAttribute(pba_emit_kernel<uint32_t, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast);
-        cudaFuncSetAttribute(pba_emit_kernel<uint64_t, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast);
-        cudaFuncSetAttribute(pba_emit_kernel<uint32_t, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide);
-        cudaFuncSetAttribute(pba_emit_kernel<uint64_t, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide);
-        attrs_set = true;
-    }
-    cudaMemsetAsync(cnt, 0, (size_t)g.B * g.S * g.B * 4, s);
-    cudaMemsetAsync(wide, 0, 4, s);
+constexpr size_t kSmemFast = kEmitWarps * sizeof(EmitWarpSmem<uint32_t>);
+constexpr size_t kSmemWide = kEmitWarps * sizeof(EmitWarpSmem<uint64_t>);
+
+void set_pba_attributes()
+{
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(pba_prefix_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kPrefixMax * 2 + kMaxBlocks * 4));
+    cudaFuncSetAttribute(pba_prefix_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kPrefixMax * 2 + kMaxBlocks * 4));
+    cudaFuncSetAttribute(pba_emit_kernel<uint32_t, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast);
+    cudaFuncSetAttribute(pba_emit_kernel<uint64_t, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast);
+    cudaFuncSetAttribute(pba_emit_kernel<uint32_t, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide);
+    cudaFuncSetAttribute(pba_emit_kernel<uint64_t, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide);
+    done = true;
+}
+
+}  // namespace
+
+// Phase 1, counts and their scan: everything the emission of any block
+// range reads, left in the workspace.
+cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
+{
+    if (g.B > kMaxBlocks) return cudaErrorInvalidValue;
+    set_pba_attributes();
+    const PbaBuffers W = pba_buffers(g, d_ws);
+    cudaError_t err;
+    if ((err = cudaMemsetAsync(W.cnt, 0, (size_t)g.B * g.S * g.B * 4, s)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(W.wide, 0, 4, s)) != cudaSuccess) return err;
     if (g.N_e > 0) {
         {
             TraceScope trace("pba_prefix", s);
             const size_t smem = ((size_t)g.P * 2 + 15) / 16 * 16 + (size_t)g.B * 4;
-            pba_prefix_kernel<<<g.B, kPrefixThreads, smem, s>>>(g, A, cnt);
+            if (g.ftab)
+                pba_prefix_kernel<true><<<g.B, kPrefixThreads, smem, s>>>(g, W.A, W.cnt);
+            else
+                pba_prefix_kernel<false><<<g.B, kPrefixThreads, smem, s>>>(g, W.A, W.cnt);
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         TraceScope trace("pba_phase1", s);
@@ -938,47 +1008,64 @@ cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cuda
             const uint32_t chunks = (uint32_t)((hi - lvl + kPassChunk - 1) / kPassChunk);
             const size_t smem = (((size_t)g.B * 4 + 15) & ~(size_t)15) +
                                 (size_t)(kPassThreads / 32) * kPassRun * 2;
-            pba_pass_kernel<<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
-                g, (uint32_t)lvl, (uint32_t)hi, A, cnt);
+            if (g.ftab)
+                pba_pass_kernel<true><<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
+                    g, (uint32_t)lvl, (uint32_t)hi, W.A, W.cnt);
+            else
+                pba_pass_kernel<false><<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
+                    g, (uint32_t)lvl, (uint32_t)hi, W.A, W.cnt);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             lvl = hi;
         }
     }
     {
         TraceScope trace("pba_scan", s);
-        pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(cnt, off, R, divR, recip, (uint32_t)g.n_b,
-                                                          g.B, g.B * g.S, g.e0, wide);
+        pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(W.cnt, W.off, W.R, W.divR, W.recip,
+                                                          (uint32_t)g.n_b, g.B, g.B * g.S, g.e0,
+                                                          W.wide);
     }
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
+// Edges of blocks [b_begin, b_end), block b_begin's first edge at d_out[0].
+cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void* d_ws,
+                            uint32_t b_begin, uint32_t b_end, cudaStream_t s, const HostCopy* hc)
+{
+    if (g.B > kMaxBlocks || b_begin > b_end || b_end > g.B) return cudaErrorInvalidValue;
+    if (b_begin == b_end) return cudaSuccess;
+    set_pba_attributes();
+    const PbaBuffers W = pba_buffers(g, const_cast<void*>(d_ws));
+    cudaError_t err;
     // every R_q + e0 < 2^32 is certain when all entries together are fewer
     const bool surely_fast = (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);
+    const uint32_t nblk = b_end - b_begin;
     const uint32_t chunks = hc ? hc->chunks : 1;
-    const uint32_t per = (g.B + chunks - 1) / chunks;
+    const uint32_t per = (nblk + chunks - 1) / chunks;
     const uint64_t edges_per_block = g.e0 + g.N_e;
     const size_t pair = id64 ? 16 : 8;
-    for (uint32_t b0 = 0, c = 0; b0 < g.B; b0 += per, ++c) {
-        const uint32_t nb = (g.B - b0 < per) ? g.B - b0 : per;
+    for (uint32_t b0 = b_begin, c = 0; b0 < b_end; b0 += per, ++c) {
+        const uint32_t nb = (b_end - b0 < per) ? b_end - b0 : per;
         const dim3 grid((g.S + kEmitWarps - 1) / kEmitWarps, nb);
         {
             TraceScope trace("pba_emit", s);
             if (id64) {
-                pba_emit_kernel<uint64_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
-                    g, A, off, R, divR, recip, wide, (uint64_t*)d_out, b0);
+                pba_emit_kernel<uint64_t, true><<<grid, kEmitThreads, kSmemFast, s>>>(
+                    g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint64_t*)d_out, b0, b_begin);
                 if (!surely_fast)
-                    pba_emit_kernel<uint64_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
-                        g, A, off, R, divR, recip, wide, (uint64_t*)d_out, b0);
+                    pba_emit_kernel<uint64_t, false><<<grid, kEmitThreads, kSmemWide, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint64_t*)d_out, b0, b_begin);
             } else {
-                pba_emit_kernel<uint32_t, true><<<grid, kEmitThreads, smem_fast, s>>>(
-                    g, A, off, R, divR, recip, wide, (uint32_t*)d_out, b0);
+                pba_emit_kernel<uint32_t, true><<<grid, kEmitThreads, kSmemFast, s>>>(
+                    g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint32_t*)d_out, b0, b_begin);
                 if (!surely_fast)
-                    pba_emit_kernel<uint32_t, false><<<grid, kEmitThreads, smem_wide, s>>>(
-                        g, A, off, R, divR, recip, wide, (uint32_t*)d_out, b0);
+                    pba_emit_kernel<uint32_t, false><<<grid, kEmitThreads, kSmemWide, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint32_t*)d_out, b0, b_begin);
             }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (hc) {
             // this chunk's edges go to the host while the next chunk is made
-            const size_t off_b = (size_t)b0 * edges_per_block * pair;
+            const size_t off_b = (size_t)(b0 - b_begin) * edges_per_block * pair;
             const size_t len = (size_t)nb * edges_per_block * pair;
             if ((err = cudaEventRecord(hc->done[c], s)) != cudaSuccess) return err;
             if ((err = cudaStreamWaitEvent(hc->copy_stream, hc->done[c], 0)) != cudaSuccess) return err;
@@ -993,6 +1080,14 @@ cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cuda
         if ((err = cudaStreamWaitEvent(s, hc->copied, 0)) != cudaSuccess) return err;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s,
+                       const HostCopy* hc)
+{
+    cudaError_t err = launch_pba_phase1(g, d_ws, s);
+    if (err != cudaSuccess) return err;
+    return launch_pba_emit(g, id64, d_out, d_ws, 0, g.B, s, hc);
 }
 
 }  // namespace pgen

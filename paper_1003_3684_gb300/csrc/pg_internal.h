@@ -35,8 +35,8 @@ struct KronDetParams {
 
 cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, uint64_t e_begin,
                                    uint64_t n_edges, cudaStream_t s);
-cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t n_edges,
-                            cudaStream_t s);
+cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t e_begin,
+                            uint64_t n_edges, cudaStream_t s);
 
 // PBA (two-phase preferential attachment) geometry.
 struct PbaGeom {
@@ -51,7 +51,15 @@ struct PbaGeom {
     uint32_t nb_shift;             // log2(n_b) when n_b is a power of two, else 0xffffffff
     FastDiv div_m, div_nb;
     FastDiv32 div_m32;             // j div m for j < 2^32
+    const uint16_t* ftab;          // faction table (device), or null: aligned width-W factions
 };
+
+// Faction table: one record of kFacStride uint16 per block: [0] list size s
+// (1..1024), [1] complement size, [2..7] zero, then the list (1024 slots) and
+// the blocks outside it in ascending order (1024 slots).
+constexpr uint32_t kFacHeader = 8;
+constexpr uint32_t kFacSlots = 1024;
+constexpr uint32_t kFacStride = kFacHeader + 2 * kFacSlots;
 
 // Workspace layout for B > 1 (all offsets 256-byte aligned).
 struct PbaWorkspace {
@@ -77,6 +85,10 @@ struct HostCopy {
 };
 constexpr uint32_t kMaxCopyChunks = 32;
 
+cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s);
+cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void* d_ws,
+                            uint32_t b_begin, uint32_t b_end, cudaStream_t s,
+                            const HostCopy* hc = nullptr);
 cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cudaStream_t s,
                        const HostCopy* hc = nullptr);
 

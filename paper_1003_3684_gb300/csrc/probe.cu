@@ -1,0 +1,53 @@
+// Integer throughput probe: Philox4x32-10 calls per second on this device.
+//
+// The generators are bound by 32-bit integer issue (Philox rounds and index
+// arithmetic), not by memory. Their roofline denominator is derived from the
+// SM count, 128 int32 lanes per SM and the clock; this kernel measures what
+// the same Philox code reaches when nothing else runs, so a kernel's
+// fraction can also be read against a measured ceiling.
+#include "../../include/pgen.h"
+#include "pg_common.cuh"
+#include "pg_internal.h"
+
+namespace pgen {
+namespace {
+
+constexpr int kProbeThreads = 256;
+
+// Every thread makes `calls` independent Philox calls (four interleaved
+// chains) and folds the words into one result, so no call is dead code.
+__global__ void __launch_bounds__(kProbeThreads) philox_probe_kernel(uint32_t* __restrict__ out,
+                                                                      uint32_t calls, Key key)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t i = 0; i < calls; ++i) {
+        const uint4 w = philox(make_uint4(tid, i, 7u, 3u), key);
+        acc ^= w.x ^ w.y ^ w.z ^ w.w;
+    }
+    out[tid] = acc;
+}
+
+}  // namespace
+}  // namespace pgen
+
+extern "C" {
+
+size_t pg_philox_probe_threads(void)
+{
+    return (size_t)pgen::device_sm_count() * 8 * pgen::kProbeThreads;
+}
+
+pg_status pg_philox_probe(uint32_t calls_per_thread, uint32_t* d_out, size_t out_words,
+                          void* stream)
+{
+    const size_t threads = pg_philox_probe_threads();
+    if (!d_out || out_words < threads || calls_per_thread == 0) return PG_EINVAL;
+    const pgen::Key key = pgen::make_key(0x9E3779B97F4A7C15ull);
+    pgen::philox_probe_kernel<<<(unsigned)(threads / pgen::kProbeThreads), pgen::kProbeThreads, 0,
+                                (cudaStream_t)stream>>>(d_out, calls_per_thread, key);
+    return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
+}
+
+}  // extern "C"

@@ -111,3 +111,52 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(pg, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         pg.lib()
+
+
+def test_faction_table_layout_on_host(L):
+    """pg_pba_faction_table (host only): list size, complement size, the list,
+    and the blocks outside it in ascending order, one 4112-byte record each."""
+    import numpy as np
+
+    import paper_1003_3684_gb300 as pg
+    lists = [[0, 1, 4, 5, 0], [0, 1, 1, 2, 3], [1, 2, 3], [1, 2, 3, 3, 4], [3, 4, 4, 5, 0],
+             [4, 5, 0]]
+    tab = pg.pba_faction_table(lists).view(np.uint16)
+    assert tab.size == 6 * 2056
+    for p, li in enumerate(lists):
+        rec = tab[p * 2056:(p + 1) * 2056]
+        outside = [b for b in range(6) if b not in li]
+        assert rec[0] == len(li) and rec[1] == len(outside)
+        assert rec[8:8 + len(li)].tolist() == li
+        assert rec[8 + 1024:8 + 1024 + len(outside)].tolist() == outside
+
+
+@pytest.mark.parametrize("lists", [
+    [[0], []],                  # empty list
+    [[0, 2], [1]],              # member out of range
+    [[0] * 1025, [1]],          # longer than 1024 entries
+])
+def test_faction_table_rejects_bad_lists(L, lists):
+    import paper_1003_3684_gb300 as pg
+    with pytest.raises(pg.PgenError):
+        pg.pba_faction_table(lists)
+
+
+def test_range_entry_points_reject_bad_ranges(L):
+    import numpy as np
+
+    import paper_1003_3684_gb300 as pg
+    R = pg._range_lib()
+    P = np.array([0.5, 0.2, 0.2, 0.1])
+    # e_end beyond the edge count, and e_begin after e_end
+    assert R.gen_kronecker_range(P.ctypes.data, 2, 5, 100, 1, 0, 0, 0, 101, None, 1000, None) == pg.PG_EINVAL
+    assert R.gen_kronecker_range(P.ctypes.data, 2, 5, 100, 1, 0, 0, 50, 40, None, 1000, None) == pg.PG_EINVAL
+    # capacity below the range
+    assert R.gen_kronecker_range(P.ctypes.data, 2, 5, 100, 1, 0, 0, 10, 40, None, 29, None) == pg.PG_ENOSPC
+    # block range outside [0, blocks]
+    cnt = C.c_uint64(0)
+    assert R.gen_pba_blocks(4000, 2, 4, 3, 1, 0, 3, 5, None, 10**9, C.byref(cnt), None, 0, None) == pg.PG_EINVAL
+    assert R.gen_pba_blocks(4000, 2, 4, 3, 1, 0, 3, 2, None, 10**9, C.byref(cnt), None, 0, None) == pg.PG_EINVAL
+    # an empty range is valid and launches nothing
+    assert R.gen_pba_blocks(4000, 2, 4, 3, 1, 0, 2, 2, None, 0, C.byref(cnt), None, 0, None) == pg.PG_OK
+    assert cnt.value == 0

@@ -217,6 +217,109 @@ def test_pba_headline_size_sampled():
 
 
 # --------------------------------------------------------------------------
+# PBA with general faction lists
+# --------------------------------------------------------------------------
+
+FIG1_STYLE_LISTS = [[0, 1, 4, 5, 0], [0, 1, 1, 2, 3], [1, 2, 3], [1, 2, 3, 3, 4],
+                    [3, 4, 4, 5, 0], [4, 5, 0]]
+
+
+def _random_lists(B, seed):
+    """Overlapping factions of random sizes; each block's list concatenates
+    the factions it belongs to (some lists omit the block itself, one list
+    names every block, one repeats entries)."""
+    rng = np.random.default_rng(seed)
+    factions = [sorted(rng.choice(B, size=int(rng.integers(1, 6)), replace=False).tolist())
+                for _ in range(B // 2)]
+    lists = []
+    for p in range(B):
+        mine = [F for F in factions if p in F] or [factions[p % len(factions)]]
+        lists.append([b for F in mine for b in F])
+    lists[1] = list(range(B))                  # no block outside: no picks
+    lists[2] = lists[2] + lists[2]             # repeated entries
+    return lists
+
+
+@pytest.mark.parametrize("lists,n_b,m,n0,f,seed,id64", [
+    (FIG1_STYLE_LISTS, 3000, 3, 4, 0.3, 71, False),
+    (FIG1_STYLE_LISTS, 3000, 3, 4, 1.0, 2, False),
+    (FIG1_STYLE_LISTS, 2, 2, 3, 0.5, 5, False),       # lists longer than a block's entries
+    (_random_lists(64, 9), 700, 5, 6, 0.1, 17, False),
+    (_random_lists(40, 4), 20_000, 2, 3, 0.0, 3, True),
+])
+def test_pba_factions_match_oracle(lists, n_b, m, n0, f, seed, id64):
+    B = len(lists)
+    got = pg.gen_pba_factions(B * n_b, m, lists, n0=n0, inter_frac=f, seed=seed, id64=id64)
+    torch.cuda.synchronize()
+    ref, _, _ = o.pba_factions(B * n_b, m, B, n0, lists, f, seed)
+    assert_same(host(got, id64), ref)
+
+
+def test_pba_factions_aligned_lists_equal_gen_pba():
+    B, W, n_b = 16, 4, 5000
+    lists = [[(p // W) * W + t for t in range(W)] for p in range(B)]
+    a = pg.gen_pba_factions(B * n_b, 3, lists, n0=4, inter_frac=0.2, seed=8)
+    b = pg.gen_pba(B * n_b, 3, B, 4, W, 0.2, 8)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# Generation in parts: edge ranges and block ranges
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("id64", [False, True])
+def test_kronecker_ranges_concatenate_to_the_graph(id64):
+    Pm, k, M, seed = W.KRON_INITIATOR, 12, 100_003, 21
+    cuts = [0, 777, 50_000, 50_001, M]
+    spans = list(zip(cuts[:-1], cuts[1:]))
+    made = {sp: pg.gen_kronecker_range(Pm, k, M, sp[0], sp[1], seed=seed, id64=id64)
+            for sp in reversed(spans)}                          # made out of order
+    parts = [made[sp] for sp in spans]
+    torch.cuda.synchronize()
+    got = np.concatenate([host(t, id64) for t in parts])
+    assert_same(got, o.kron(Pm, k, M, seed))
+
+
+def test_deterministic_kronecker_ranges(golden):
+    G = np.array([[float(x) for x in r] for r in golden("pk_fig2_seed.txt")])
+    k = 4
+    full = pg.gen_kronecker(G, k, deterministic=True)
+    E = full.shape[0]
+    cuts = [0, 1, 4096, 4097, E]
+    parts = [pg.gen_kronecker_range(G, k, 0, a, b, deterministic=True)
+             for a, b in zip(cuts[:-1], cuts[1:])]
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat(parts), full)
+
+
+def test_pba_block_ranges_from_one_prepare():
+    n_b, m, B, n0, Wd, f, seed = 3000, 3, 16, 4, 2, 0.2, 12
+    n = B * n_b
+    ws = pg.pg_pba_prepare(n, m, B, n0, Wd, f, seed)
+    ranges = [(5, 9), (0, 5), (9, 16), (3, 4)]                 # any order, overlaps allowed
+    parts = {r: pg.gen_pba_blocks(ws, n, m, B, r[0], r[1], n0=n0, seed=seed) for r in ranges}
+    full = pg.gen_pba(n, m, B, n0, Wd, f, seed)
+    torch.cuda.synchronize()
+    per = full.shape[0] // B
+    for (a, b), t in parts.items():
+        assert torch.equal(t, full[a * per:b * per]), (a, b)
+    ref, _, _ = o.pba(n, m, B, n0, Wd, f, seed)
+    assert_same(host(parts[(5, 9)]), ref[5 * per:9 * per])
+
+
+def test_pba_block_ranges_with_faction_lists():
+    lists = FIG1_STYLE_LISTS
+    B, n_b, m, n0, f, seed = len(lists), 2000, 2, 3, 0.4, 6
+    ws = pg.pg_pba_prepare(B * n_b, m, B, n0, inter_frac=f, seed=seed, factions=lists)
+    part = pg.gen_pba_blocks(ws, B * n_b, m, B, 2, 5, n0=n0, seed=seed, id64=True)
+    torch.cuda.synchronize()
+    ref, _, _ = o.pba_factions(B * n_b, m, B, n0, lists, f, seed)
+    per = ref.shape[0] // B
+    assert_same(host(part, True), ref[2 * per:5 * per])
+
+
+# --------------------------------------------------------------------------
 # CSR
 # --------------------------------------------------------------------------
 
@@ -236,9 +339,29 @@ def csr_check(edges_np, N, id64=False):
     (50_000, 1, 0.0, False),         # a single row: nothing to sort on
     (0, 10, 0.0, False),
     (70_000, 2**33 + 5, 0.1, True),  # 34-bit ids
+    (200_003, 3_000, 0.5, True),     # 64-bit ids, a row beyond shared memory
+    (50_000, 2**26 + 3, 0.2, False), # mostly empty rows
 ])
 def test_csr_random(M, N, hub, id64):
     csr_check(W.random_edges(M + N, M, N, id64=id64, hub_fraction=hub), N, id64)
+
+
+@pytest.mark.parametrize("N,id64", [(3000, False), (3000, True), (2**26 + 3, False),
+                                     (2**26 + 3, True)])
+def test_csr_row_length_classes(N, id64):
+    """Unsorted list whose rows straddle every length class of the row sort:
+    thread-sorted rows (up to 32), CTA-sorted rows in shared memory, and rows
+    longer than shared memory holds (12288 ids of 32 bits, 6144 of 64), with
+    an odd (N = 3000: 3 digit passes) and odd-and-long (2^26+3: 7) pass count."""
+    rng = np.random.default_rng(11 + N % 7 + id64)
+    lens = list(range(0, 41)) + [63, 64, 65, 4095, 4096, 6144, 6145, 12288, 12289, 30001]
+    srcs = rng.choice(min(N, 10**6), size=len(lens), replace=False)
+    src = np.repeat(srcs, lens)
+    dst = rng.integers(0, N, size=src.size)
+    dst[::5] = dst[0]                                    # repeated destinations
+    perm = rng.permutation(src.size)
+    e = np.stack([src[perm], dst[perm]], 1).astype(np.uint64 if id64 else np.uint32)
+    csr_check(e, N, id64)
 
 
 def test_csr_of_kronecker_and_pba_graphs():
