@@ -67,9 +67,11 @@ def lib():
             L.or_kron.argtypes = [P, u32, u32, u64, u64, P]
             L.or_kron_det.argtypes = [P, u32, u32, P, u64, P, P]
             L.or_csr.argtypes = [P, u64, u64, P, P]
+            L.or_csr_opts.argtypes = [P, u64, u64, u32, P, P, P]
+            L.or_random_cells.argtypes = [u64, u64, u64, P]
             for name in ("or_ba", "or_pba_count", "or_pba_phase1_general", "or_pba_phase1", "or_pba_endpoints",
                          "or_pba_substitute", "or_pba", "or_pba_factions", "or_kron_thresholds", "or_kron",
-                         "or_kron_det", "or_csr"):
+                         "or_kron_det", "or_csr", "or_csr_opts", "or_random_cells"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -218,6 +220,28 @@ def kron_det(P_init, k: int, cap: int | None = None):
     _check(lib().or_kron_det(_ptr(Pm), Pm.shape[0], k, _ptr(out), cap, _ptr(n_out), _ptr(peak)),
            "kron_det")
     return out[:int(n_out[0])], int(peak[0])
+
+
+CSR_SYMMETRIZE, CSR_DEDUP, CSR_NO_LOOPS, CSR_ODD = 1, 2, 4, 8
+
+
+def csr_opts(edges, n_vertices: int, flags: int):
+    """CSR with options (symmetrise, dedup, drop loops, odd multiplicity)."""
+    e = np.ascontiguousarray(edges, dtype=np.uint64).reshape(-1, 2)
+    M = e.shape[0]
+    row_ptr = np.zeros(n_vertices + 1, dtype=np.uint64)
+    col = np.zeros(max(2 * M, 1), dtype=np.uint64)
+    m_out = np.zeros(1, dtype=np.uint64)
+    _check(lib().or_csr_opts(_ptr(e), M, n_vertices, flags, _ptr(row_ptr), _ptr(col),
+                             _ptr(m_out)), "csr_opts")
+    return row_ptr, col[:int(m_out[0])]
+
+
+def random_cells(n_vertices: int, n_edges: int, seed: int) -> np.ndarray:
+    """Random graph G(N, M) with replacement, as (M, 2) uint64 pairs."""
+    out = np.zeros((max(n_edges, 1), 2), dtype=np.uint64)
+    _check(lib().or_random_cells(n_vertices, n_edges, seed, _ptr(out)), "random_cells")
+    return out[:n_edges]
 
 
 def csr(edges, n_vertices: int):

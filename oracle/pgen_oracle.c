@@ -538,6 +538,68 @@ static int cmp_pair(const void* a, const void* b)
     return 0;
 }
 
+/* CSR with options (not in the paper; reading R11). The list is the M pairs,
+ * plus (dst, src) for each when OR_CSR_SYMMETRIZE; self-loops are dropped
+ * when OR_CSR_NO_LOOPS; after sorting, OR_CSR_DEDUP keeps one copy of each
+ * distinct pair and OR_CSR_ODD keeps one copy of each pair that occurs an
+ * odd number of times (the exclusive-or of adjacency matrices, Sec. 3 PK
+ * randomisation). *M_out receives the number of col entries.             */
+#define OR_CSR_SYMMETRIZE 1u
+#define OR_CSR_DEDUP 2u
+#define OR_CSR_NO_LOOPS 4u
+#define OR_CSR_ODD 8u
+
+int or_csr_opts(const uint64_t* pairs, uint64_t M, uint64_t N, uint32_t flags, uint64_t* row_ptr,
+                uint64_t* col, uint64_t* M_out)
+{
+    uint64_t cap = (flags & OR_CSR_SYMMETRIZE) ? 2 * M : M;
+    uint64_t* s = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (cap ? cap : 1));
+    if (!s) return 2;
+    uint64_t n = 0;
+    for (uint64_t e = 0; e < M; ++e) {
+        uint64_t a = pairs[2 * e], b = pairs[2 * e + 1];
+        if (a >= N || b >= N) { free(s); return 1; }
+        if ((flags & OR_CSR_NO_LOOPS) && a == b) continue;
+        s[2 * n] = a; s[2 * n + 1] = b; ++n;
+        if (flags & OR_CSR_SYMMETRIZE) { s[2 * n] = b; s[2 * n + 1] = a; ++n; }
+    }
+    qsort(s, n, 2 * sizeof(uint64_t), cmp_pair);
+    uint64_t k = 0;
+    for (uint64_t i = 0; i < n;) {
+        uint64_t j = i + 1;
+        while (j < n && s[2 * j] == s[2 * i] && s[2 * j + 1] == s[2 * i + 1]) ++j;
+        uint64_t copies = j - i;
+        if (flags & OR_CSR_ODD) copies = (j - i) & 1;
+        else if (flags & OR_CSR_DEDUP) copies = 1;
+        for (uint64_t c = 0; c < copies; ++c) {
+            s[2 * k] = s[2 * i]; s[2 * k + 1] = s[2 * i + 1]; ++k;
+        }
+        i = j;
+    }
+    for (uint64_t v = 0; v <= N; ++v) row_ptr[v] = 0;
+    for (uint64_t e = 0; e < k; ++e) row_ptr[s[2 * e] + 1]++;
+    for (uint64_t v = 0; v < N; ++v) row_ptr[v + 1] += row_ptr[v];
+    for (uint64_t e = 0; e < k; ++e) col[e] = s[2 * e + 1];
+    *M_out = k;
+    free(s);
+    return 0;
+}
+
+/* Random graph G(N, M) with replacement (reading R11): edge e is the cell */
+/* (uniform over N from (w1:w0), uniform over N from (w3:w2)) of the draw  */
+/* with counter (e_lo, e_hi, 0, 4).                                        */
+int or_random_cells(uint64_t N, uint64_t M, uint64_t seed, uint64_t* out)
+{
+    if (N == 0 && M > 0) return 1;
+    for (uint64_t e = 0; e < M; ++e) {
+        uint32_t w[4];
+        draw(seed, e, 0, 4, w);
+        out[2 * e] = or_uniform(w[0], w[1], N);
+        out[2 * e + 1] = or_uniform(w[2], w[3], N);
+    }
+    return 0;
+}
+
 int or_csr(const uint64_t* pairs, uint64_t M, uint64_t N, uint64_t* row_ptr, uint64_t* col)
 {
     uint64_t* s = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (M ? M : 1));

@@ -36,5 +36,8 @@ int or_kron_det(const double* P, uint32_t n0, uint32_t k, uint64_t* out, uint64_
                 uint64_t* n_out, uint64_t* max_depth_out);
 
 int or_csr(const uint64_t* pairs, uint64_t M, uint64_t N, uint64_t* row_ptr, uint64_t* col);
+int or_csr_opts(const uint64_t* pairs, uint64_t M, uint64_t N, uint32_t flags, uint64_t* row_ptr,
+                uint64_t* col, uint64_t* M_out);
+int or_random_cells(uint64_t N, uint64_t M, uint64_t seed, uint64_t* out);
 
 #endif

@@ -542,3 +542,84 @@ def test_csr_matches_lexsort(N, M):
 def test_csr_rejects_out_of_range_source():
     with pytest.raises(ValueError):
         o.csr(np.array([[3, 0]], np.uint64), 3)
+
+
+# --------------------------------------------------------------------------
+# CSR options and the random graph used to randomise PK (reading R11)
+# --------------------------------------------------------------------------
+
+def _multigraph(seed, M, N, loops=True):
+    rng = np.random.default_rng(seed)
+    e = rng.integers(0, N, size=(M, 2), dtype=np.uint64)
+    e[: M // 5] = e[M // 5: 2 * (M // 5)]            # many repeated pairs
+    if loops:
+        e[::11, 1] = e[::11, 0]                       # self-loops
+    return e
+
+
+def _rows(row_ptr, col):
+    return [tuple(col[row_ptr[v]:row_ptr[v + 1]].tolist()) for v in range(len(row_ptr) - 1)]
+
+
+def test_csr_dedup_equals_numpy_unique():
+    e = _multigraph(1, 5000, 300)
+    rp, col = o.csr_opts(e, 300, o.CSR_DEDUP)
+    u = np.unique(e, axis=0)
+    assert np.array_equal(col, u[:, 1])
+    assert np.array_equal(rp, np.concatenate([[0], np.cumsum(np.bincount(u[:, 0].astype(np.int64),
+                                                                         minlength=300))]))
+
+
+def test_csr_symmetrize_is_symmetric_with_multiplicity():
+    e = _multigraph(2, 3000, 100)
+    rp, col = o.csr_opts(e, 100, o.CSR_SYMMETRIZE)
+    assert col.size == 2 * e.shape[0]
+    src = np.repeat(np.arange(100, dtype=np.uint64), np.diff(rp).astype(np.int64))
+    fwd = Counter(zip(src.tolist(), col.tolist()))
+    assert fwd == Counter((b, a) for (a, b) in fwd.elements())
+
+
+def test_csr_odd_keeps_pairs_of_odd_multiplicity():
+    e = _multigraph(3, 4000, 60)
+    rp, col = o.csr_opts(e, 60, o.CSR_ODD)
+    counts = Counter(map(tuple, e.tolist()))
+    want = sorted(p for p, c in counts.items() if c % 2 == 1)
+    src = np.repeat(np.arange(60), np.diff(rp).astype(np.int64))
+    assert list(zip(src.tolist(), col.tolist())) == want
+    # XOR identities: a list with itself cancels; disjoint sets give their union
+    both = np.concatenate([e, e])
+    _, c2 = o.csr_opts(both, 60, o.CSR_ODD)
+    assert c2.size == 0
+    a = np.array([[0, 1], [2, 3]], np.uint64)
+    b = np.array([[1, 0], [3, 3]], np.uint64)
+    _, c3 = o.csr_opts(np.concatenate([a, b]), 4, o.CSR_ODD)
+    assert c3.tolist() == [1, 0, 3, 3]
+
+
+def test_csr_no_loops_drops_exactly_the_loops():
+    e = _multigraph(4, 2000, 50)
+    rp, col = o.csr_opts(e, 50, o.CSR_NO_LOOPS)
+    src = np.repeat(np.arange(50, dtype=np.uint64), np.diff(rp).astype(np.int64))
+    assert not (src == col).any()
+    assert col.size == int((e[:, 0] != e[:, 1]).sum())
+
+
+def test_random_cells_counter_layout():
+    """Edge e uses the draw with counter (e, 0, 0, 4); for N = 2^b the row is
+    the top b bits of (w1:w0) and the column the top b bits of (w3:w2)."""
+    seed, b = 0x1234_5678_9ABC, 10
+    cells = o.random_cells(2**b, 64, seed)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for e in range(64):
+        w = o.philox4x32_10([e, 0, 0, 4], key)
+        assert int(cells[e, 0]) == ((int(w[1]) << 32 | int(w[0])) >> (64 - b))
+        assert int(cells[e, 1]) == ((int(w[3]) << 32 | int(w[2])) >> (64 - b))
+
+
+def test_random_cells_uniform():
+    N, M = 37, 200_000
+    cells = o.random_cells(N, M, seed=9).astype(np.int64)
+    for axis in (0, 1):
+        obs = np.bincount(cells[:, axis], minlength=N)
+        assert stats.chisquare(obs).pvalue > 1e-4
+    assert stats.chisquare(np.bincount(cells[:, 0] * N + cells[:, 1], minlength=N * N)).pvalue > 1e-4
