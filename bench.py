@@ -180,6 +180,8 @@ def oracle_sample(name: str, cfg: dict, budget_s: float):
     same initiator and k, plus CSR of them. Returns (edges/s, description,
     seconds, samples).
     """
+    import numpy as np
+
     import oracle as o
     t_total, edges_total, samples = 0.0, 0, 0
     if cfg["kind"] == "batch":
@@ -205,6 +207,26 @@ def oracle_sample(name: str, cfg: dict, budget_s: float):
             t_total += time.perf_counter() - t0
             edges_total += e.shape[0]
             desc = "oracle on jobs of the batch (every 97th job)"
+        elif cfg["kind"] == "kron_xor":
+            M, Mr = 2**20, 2**20 * cfg["n_random"] // cfg["n_edges"]
+            t0 = time.perf_counter()
+            pk = o.kron(cfg["initiator"], cfg["k"], M, cfg["seed"] + samples)
+            rnd = o.random_cells(2 ** cfg["k"], Mr, cfg["seed"] + samples)
+            o.csr_opts(np.concatenate([pk, rnd]), 2 ** cfg["k"], o.CSR_ODD)
+            t_total += time.perf_counter() - t0
+            edges_total += M + Mr
+            desc = (f"or_kron k={cfg['k']} ({M} edges) + or_random_cells ({Mr}) + "
+                    "or_csr_opts (odd multiplicity) per sample")
+        elif cfg["kind"] == "pba" and cfg["blocks"] > 1 and cfg.get("factions"):
+            B = 2
+            n = B * (cfg["n"] // cfg["blocks"])
+            t0 = time.perf_counter()
+            e, _, _ = o.pba_factions(n, cfg["m"], B, cfg["n0"], W.ring_factions(B, 3),
+                                     cfg["inter_frac"], cfg["seed"] + samples)
+            t_total += time.perf_counter() - t0
+            edges_total += e.shape[0]
+            desc = (f"or_pba_factions, 2 blocks of n_b={cfg['n'] // cfg['blocks']} with ring "
+                    f"lists, m={cfg['m']}, f={cfg['inter_frac']}: {e.shape[0]} edges per sample")
         elif cfg["kind"] == "pba" and cfg["blocks"] > 1:
             B = 2
             n = B * (cfg["n"] // cfg["blocks"])
@@ -527,14 +549,33 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     if kind == "pba":
         n, m, B, n0 = cfg["n"], cfg["m"], cfg["blocks"], cfg["n0"]
         E = pg.pg_pba_edge_count(n, m, B, n0)
-        out = torch.empty((E, 2), dtype=torch.int32, device=dev)
+        parts = cfg.get("parts", 1)
+        out = torch.empty((E // parts if parts > 1 else E, 2), dtype=torch.int32, device=dev)
         ws_bytes = pg.pg_pba_workspace_size(n, m, B)
         ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+        factions = None
+        if cfg.get("factions") == "ring3":
+            factions = W.ring_factions(B, 3)
+            table = torch.from_numpy(pg.pba_faction_table(factions)).to(dev)
 
-        def step():
-            pg.gen_pba(n, m, B, n0, cfg["faction_width"], cfg["inter_frac"], seed, out=out,
-                       workspace=ws if B > 1 else None)
-        units = {"pba_phase1": B * (n // B) * m, "pba_emit": B * (n // B) * m,
+        if factions is not None:
+            def step():
+                pg.gen_pba_factions(n, m, factions, n0=n0, inter_frac=cfg["inter_frac"], seed=seed,
+                                    out=out, workspace=ws, table=table)
+        elif parts > 1:
+            per = B // parts
+
+            def step():
+                pg.pg_pba_prepare(n, m, B, n0, cfg["faction_width"], cfg["inter_frac"], seed,
+                                  workspace=ws)
+                for r in range(parts):
+                    pg.gen_pba_blocks(ws, n, m, B, r * per, (r + 1) * per, n0=n0, seed=seed,
+                                      out=out)
+        else:
+            def step():
+                pg.gen_pba(n, m, B, n0, cfg["faction_width"], cfg["inter_frac"], seed, out=out,
+                           workspace=ws if B > 1 else None)
+        units = {"pba_phase1": B * (n // B) * m, "pba_emit": B * (n // B) * m // parts,
                  "ba_chain": n * m}
         work = dict(KERNEL_WORK)
         out_bytes = E * 8
@@ -543,6 +584,33 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                         faction_width=cfg["faction_width"], inter_frac=cfg["inter_frac"],
                         seed=cfg["seed"], edges_per_step=E, id_width=32,
                         workspace_bytes=ws_bytes)
+        if factions is not None:
+            cfg_json["factions"] = "ring: block p lists p-1, p, p+1 (mod B)"
+        if parts > 1:
+            cfg_json["parts"] = (f"{parts} ranges of {B // parts} blocks through one buffer of "
+                                 f"{out.numel() * 4 / 1e9:.2f} GB")
+    elif kind == "kron_xor":
+        k, M, Mr = cfg["k"], cfg["n_edges"], cfg["n_random"]
+        N = 2**k
+        E = M + Mr
+        out = torch.empty((E, 2), dtype=torch.int32, device=dev)
+        row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(E, dtype=torch.int32, device=dev)
+        ws_bytes = pg._opts_lib().pg_csr_opts_workspace_size(E, N, pg.CSR_ODD)
+        ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+
+        def step():
+            pg.gen_kronecker(cfg["initiator"], k, M, seed, out=out[:M])
+            pg.gen_random_cells(N, Mr, seed, out=out[M:])
+            pg.edges_to_csr_opts(out, N, pg.CSR_ODD, row_ptr=row_ptr, col=col, workspace=ws)
+        units = {"kron_descent_n0_2": M}
+        work = {"kron_descent_n0_2": kron_work(k)}
+        units.update({kk: E for kk in CSR_WORK})
+        work.update(CSR_WORK)
+        out_bytes = E * 8 + (N + 1) * 8 + E * 4
+        cfg_json = dict(workload=args.workload, initiator=cfg["initiator"], k=k, n_edges=M,
+                        n_random=Mr, seed=cfg["seed"], csr="odd multiplicity (XOR)",
+                        edges_per_step=E, id_width=32)
     else:
         k, M = cfg["k"], cfg["n_edges"]
         N = 2**k
@@ -661,7 +729,9 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     # end to end through the public API with host buffers: the step plus the
     # device-to-host copy of everything it produced into pinned host memory
     if not args.no_e2e:
-        if kind == "pba":
+        if kind == "pba" and cfg.get("parts", 1) > 1:
+            line["e2e"] = measure_e2e_parts(args, cfg, seed, out, ws, E, dev, world)
+        elif kind == "pba" and not cfg.get("factions"):
             line["e2e"] = measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world)
         else:
             line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)
@@ -709,6 +779,59 @@ def measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world):
                 d2h_bytes_per_step=out_bytes, steps=steps,
                 host_buffer=f"pinned {out_bytes / 2**30:.1f} GiB; copy overlapped with "
                             "generation (gen_pba_to_host)")
+
+
+def measure_e2e_parts(args, cfg, seed, out, ws, E, dev, world):
+    """End to end for generation in parts: prepare, then each block range into
+    the device buffer and on to its place in one pinned host buffer of the
+    whole graph (range r+1 is generated while range r is copied)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1003_3684_gb300 as pg
+    B, parts = cfg["blocks"], cfg["parts"]
+    per = B // parts
+    rows = out.shape[0]
+    host = torch.empty((rows * parts, 2), dtype=out.dtype, pin_memory=True)
+    bufs = [out, torch.empty_like(out)]
+    copy = torch.cuda.Stream(device=dev)
+    main = torch.cuda.current_stream(dev)
+    done = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_step():
+        pg.pg_pba_prepare(cfg["n"], cfg["m"], B, cfg["n0"], cfg["faction_width"],
+                          cfg["inter_frac"], seed, workspace=ws)
+        for r in range(parts):
+            b = bufs[r % 2]
+            if r >= 2:
+                main.wait_event(done[r % 2])           # buffer free again
+            pg.gen_pba_blocks(ws, cfg["n"], cfg["m"], B, r * per, (r + 1) * per, n0=cfg["n0"],
+                              seed=seed, out=b)
+            ev = torch.cuda.Event()
+            ev.record(main)
+            copy.wait_event(ev)
+            with torch.cuda.stream(copy):
+                host[r * rows:(r + 1) * rows].copy_(b, non_blocking=True)
+            done[r % 2].record(copy)
+        copy.synchronize()
+        main.synchronize()
+
+    e2e_step()
+    steps = max(1, min(args.steps, 3))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dt = float(t.item())
+    return dict(value=E * steps * world / dt, unit="edges/s", h2d_bytes_per_step=0,
+                d2h_bytes_per_step=E * 8, steps=steps,
+                host_buffer=f"pinned {E * 8 / 2**30:.1f} GiB; two device buffers of "
+                            f"{rows * 8 / 2**30:.1f} GiB, each range copied while the next is made")
 
 
 def measure_e2e(args, step, out, cfg, E, dev, world, rank):

@@ -268,6 +268,40 @@ pg_status edges_to_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertice
                        pg_idwidth w, uint64_t* d_row_ptr, void* d_col, void* d_ws,
                        size_t ws_bytes, void* stream);
 
+/* CSR with options (not in the paper, except PG_CSR_ODD below). flags:
+ *   PG_CSR_SYMMETRIZE  the list plus (dst, src) of every pair (an undirected
+ *                      graph's both directions); col then holds up to
+ *                      2*n_edges entries.
+ *   PG_CSR_DEDUP       one entry per distinct (src, dst).
+ *   PG_CSR_NO_LOOPS    pairs with src == dst are dropped.
+ *   PG_CSR_ODD         one entry per pair that occurs an odd number of times:
+ *                      the exclusive-or of adjacency matrices. A PK list
+ *                      concatenated with gen_random_cells' list gives the
+ *                      randomisation of Sec. 3 (PK method) that combines the
+ *                      Kronecker adjacency with a random graph's by XOR.
+ * Rows are sorted ascending as in edges_to_csr. The number of col entries
+ * written is row_ptr[n_vertices], on the device (read it after the stream
+ * work is done). cap_col: capacity of d_col in entries; it must cover the
+ * list (n_edges, or 2*n_edges with PG_CSR_SYMMETRIZE). flags = 0 is
+ * edges_to_csr. Workspace: pg_csr_opts_workspace_size() bytes, 256-byte
+ * aligned. */
+#define PG_CSR_SYMMETRIZE 1u
+#define PG_CSR_DEDUP 2u
+#define PG_CSR_NO_LOOPS 4u
+#define PG_CSR_ODD 8u
+size_t pg_csr_opts_workspace_size(uint64_t n_edges, uint64_t n_vertices, uint32_t flags);
+pg_status edges_to_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_vertices,
+                            pg_idwidth w, uint32_t flags, uint64_t* d_row_ptr, void* d_col,
+                            uint64_t cap_col, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Random graph G(N, M) with replacement, for the exclusive-or randomisation
+ * of PK graphs (Sec. 3, PK method): edge e (e < n_edges) is the cell
+ * (row, col) = (floor((w1:w0) * N / 2^64), floor((w3:w2) * N / 2^64)) of the
+ * Philox draw with counter (e_lo, e_hi, 0, 4); N = n_vertices. Written as
+ * pairs of width w to d_edges (16-byte aligned, cap_edges >= n_edges). */
+pg_status gen_random_cells(uint64_t n_vertices, uint64_t n_edges, uint64_t seed, pg_idwidth w,
+                           void* d_edges, uint64_t cap_edges, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched generation: many independent graphs in one persistent launch.
  *

@@ -30,7 +30,8 @@ __all__ = [
     "pg_status_string", "pg_device_sm_count", "pg_version",
     "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba", "gen_pba_to_host",
     "pba_faction_table", "gen_pba_factions", "pg_pba_prepare", "gen_pba_blocks",
-    "gen_kronecker_range", "philox_rate",
+    "gen_kronecker_range", "philox_rate", "edges_to_csr_opts", "gen_random_cells",
+    "kronecker_xor_random", "CSR_SYMMETRIZE", "CSR_DEDUP", "CSR_NO_LOOPS", "CSR_ODD",
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
 ]
@@ -199,13 +200,16 @@ def pba_faction_table(lists) -> np.ndarray:
 
 def gen_pba_factions(n: int, m: int, factions, n0: int | None = None, inter_frac: float = 0.1,
                      seed: int = 0, id64: bool = False, out=None, workspace=None, stream=None,
-                     device="cuda"):
+                     device="cuda", table=None):
     """Two-phase PBA with general faction lists: ``factions[p]`` lists the
-    members of every faction block p belongs to (blocks = len(factions))."""
+    members of every faction block p belongs to (blocks = len(factions)).
+    ``table``: the device copy of pba_faction_table(factions), when the
+    caller keeps one across calls (built and copied here otherwise)."""
     import torch
     blocks = len(factions)
     n0 = m + 1 if n0 is None else n0
-    table = torch.from_numpy(pba_faction_table(factions)).to(device)
+    if table is None:
+        table = torch.from_numpy(pba_faction_table(factions)).to(device)
     E = pg_pba_edge_count(n, m, blocks, n0)
     dtype = torch.int64 if id64 else torch.int32
     if out is None:
@@ -405,6 +409,88 @@ def edges_to_csr(edges, n_vertices: int, row_ptr=None, col=None, workspace=None,
                             _stream(stream))
     _check("edges_to_csr", st)
     return row_ptr, col[:E]
+
+
+CSR_SYMMETRIZE, CSR_DEDUP, CSR_NO_LOOPS, CSR_ODD = 1, 2, 4, 8
+
+
+def _opts_lib():
+    L = lib()
+    if not getattr(L, "_opts_ready", False):
+        L.pg_csr_opts_workspace_size.argtypes = [u64, u64, u32]
+        L.pg_csr_opts_workspace_size.restype = sz
+        L.edges_to_csr_opts.argtypes = [vp, u64, u64, i32, u32, vp, vp, u64, vp, sz, vp]
+        L.edges_to_csr_opts.restype = i32
+        L.gen_random_cells.argtypes = [u64, u64, u64, i32, vp, u64, vp]
+        L.gen_random_cells.restype = i32
+        L._opts_ready = True
+    return L
+
+
+def edges_to_csr_opts(edges, n_vertices: int, flags: int, row_ptr=None, col=None, workspace=None,
+                      stream=None):
+    """CSR with options (CSR_SYMMETRIZE | CSR_DEDUP | CSR_NO_LOOPS | CSR_ODD).
+
+    Returns (row_ptr, col) with col holding capacity for the whole list; the
+    entries in use are col[:row_ptr[-1]] (known once the stream's work ends).
+    """
+    import torch
+    L = _opts_lib()
+    id64 = edges.dtype == torch.int64
+    E = edges.shape[0]
+    listed = 2 * E if flags & CSR_SYMMETRIZE else E
+    if row_ptr is None:
+        row_ptr = _empty(n_vertices + 1, torch.int64, edges.device)
+    if col is None:
+        col = _empty(max(listed, 1), edges.dtype, edges.device)
+    if workspace is None:
+        workspace = _empty(max(L.pg_csr_opts_workspace_size(E, n_vertices, flags), 1),
+                           torch.uint8, edges.device)
+    st = L.edges_to_csr_opts(_ptr(edges), E, n_vertices, PG_ID64 if id64 else PG_ID32, flags,
+                             _ptr(row_ptr), _ptr(col), col.numel(), _ptr(workspace),
+                             workspace.numel(), _stream(stream))
+    _check("edges_to_csr_opts", st)
+    return row_ptr, col
+
+
+def gen_random_cells(n_vertices: int, n_edges: int, seed: int = 0, id64: bool = False, out=None,
+                     stream=None, device="cuda"):
+    """Random graph G(N, M) with replacement (the XOR partner of a PK graph)."""
+    import torch
+    dtype = torch.int64 if id64 else torch.int32
+    if out is None:
+        out = _empty((max(n_edges, 1), 2), dtype, device)
+    st = _opts_lib().gen_random_cells(n_vertices, n_edges, seed, PG_ID64 if id64 else PG_ID32,
+                                      _ptr(out), out.shape[0], _stream(stream))
+    _check("gen_random_cells", st)
+    return out[:n_edges]
+
+
+def kronecker_xor_random(initiator, k: int, n_random: int, n_edges: int = 0, seed: int = 0,
+                         deterministic: bool = True, id64: bool = False, stream=None,
+                         device="cuda"):
+    """PK graph randomised by exclusive-or with a random graph (Sec. 3, PK
+    method): the Kronecker list and G(N, n_random) in one buffer, then CSR
+    keeping the cells of odd multiplicity. Returns (row_ptr, col) as
+    edges_to_csr_opts does."""
+    import torch
+    P = _initiator(initiator)
+    M1 = pg_kron_edge_count(P, k, n_edges, deterministic)
+    N = P.shape[0] ** k
+    dtype = torch.int64 if id64 else torch.int32
+    buf = _empty((max(M1 + n_random, 1), 2), dtype, device)
+    # the order of the two lists does not matter to the exclusive-or; the
+    # second list must start on a 16-byte boundary (an even edge index for
+    # 32-bit ids), so the list with an even length goes first
+    kron_first = id64 or M1 % 2 == 0
+    if not kron_first and n_random % 2:
+        raise ValueError("kronecker_xor_random: both lists have odd lengths with 32-bit ids")
+    a, b = (0, M1) if kron_first else (n_random, 0)
+    gen_kronecker(P, k, n_edges, seed, deterministic=deterministic, id64=id64,
+                  out=buf[a:a + max(M1, 1)], stream=stream)
+    if n_random > 0:
+        gen_random_cells(N, n_random, seed, id64=id64, out=buf[b:b + n_random], stream=stream)
+    return edges_to_csr_opts(buf[:M1 + n_random], N, CSR_ODD, stream=stream)
 
 
 def pg_trace_enable(on: bool = True) -> None:

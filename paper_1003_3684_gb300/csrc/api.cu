@@ -457,6 +457,18 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
                        cap_edges, n_edges_out, stream);
 }
 
+pg_status gen_random_cells(uint64_t n_vertices, uint64_t n_edges, uint64_t seed, pg_idwidth w,
+                           void* d_edges, uint64_t cap_edges, void* stream)
+{
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (n_edges > 0 && n_vertices == 0) return PG_EINVAL;
+    if (w == PG_ID32 && n_vertices > ((uint64_t)1 << 32)) return PG_EINVAL;
+    if (cap_edges < n_edges) return PG_ENOSPC;
+    if (n_edges > 0 && (!d_edges || !aligned(d_edges, 16))) return PG_EINVAL;
+    return from_cuda(launch_random_cells(make_key(seed), n_vertices, w == PG_ID64, d_edges, 0,
+                                         n_edges, (cudaStream_t)stream));
+}
+
 pg_status gen_kronecker_range(const double* h_initiator, uint32_t n0, uint32_t k,
                               uint64_t n_edges, uint64_t seed, pg_kron_mode mode, pg_idwidth w,
                               uint64_t e_begin, uint64_t e_end, void* d_edges,
@@ -465,6 +477,38 @@ pg_status gen_kronecker_range(const double* h_initiator, uint32_t n0, uint32_t k
     if (e_end == ~(uint64_t)0) return PG_EINVAL;
     return kron_common(h_initiator, n0, k, n_edges, seed, mode, w, e_begin, e_end, d_edges,
                        cap_edges, nullptr, stream);
+}
+
+size_t pg_csr_opts_workspace_size(uint64_t n_edges, uint64_t n_vertices, uint32_t flags)
+{
+    if (flags == 0) return csr_workspace_bytes(n_edges, n_vertices);
+    return csr_opts_workspace_bytes(n_edges, n_vertices, flags);
+}
+
+pg_status edges_to_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_vertices,
+                            pg_idwidth w, uint32_t flags, uint64_t* d_row_ptr, void* d_col,
+                            uint64_t cap_col, void* d_ws, size_t ws_bytes, void* stream)
+{
+    if (flags & ~(uint32_t)(PG_CSR_SYMMETRIZE | PG_CSR_DEDUP | PG_CSR_NO_LOOPS | PG_CSR_ODD))
+        return PG_EINVAL;
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (n_edges > 0 && n_vertices == 0) return PG_EINVAL;
+    if (!d_row_ptr || !aligned(d_row_ptr, 8)) return PG_EINVAL;
+    if (n_edges >> 62) return PG_EINVAL;
+    const uint64_t listed = (flags & PG_CSR_SYMMETRIZE) ? 2 * n_edges : n_edges;
+    if (cap_col < listed) return PG_ENOSPC;
+    if (n_edges > 0 && (!d_edges || !d_col || !aligned(d_edges, w == PG_ID64 ? 16 : 8)))
+        return PG_EINVAL;
+    if (w == PG_ID32 && n_vertices > ((uint64_t)1 << 32)) return PG_EINVAL;
+    const size_t need = pg_csr_opts_workspace_size(n_edges, n_vertices, flags);
+    if (ws_bytes < need || (need > 0 && !d_ws)) return PG_ENOMEM;
+    if (d_ws && !aligned(d_ws, 256)) return PG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags == 0)
+        return from_cuda(launch_csr(d_edges, n_edges, n_vertices, w == PG_ID64, d_row_ptr, d_col,
+                                    d_ws, ws_bytes, s));
+    return from_cuda(launch_csr_opts(d_edges, n_edges, n_vertices, w == PG_ID64, flags, d_row_ptr,
+                                     d_col, d_ws, s));
 }
 
 size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices)

@@ -457,6 +457,107 @@ __global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<I
     }
 }
 
+// ---- CSR options (symmetrise, dedup, drop loops, odd multiplicity) ---------
+// All options act on the list sorted by (src, dst): the sort always runs,
+// then a compaction keeps the wanted positions of the sorted pairs, writes
+// their destinations to col in order and marks row ends for the prefix max.
+constexpr uint32_t kOptSym = 1, kOptDedup = 2, kOptNoLoops = 4, kOptOdd = 8;
+
+template <typename Id>
+__global__ void __launch_bounds__(256) csr_sym_kernel(const typename PairOf<Id>::T* __restrict__ in,
+                                                      uint64_t M,
+                                                      typename PairOf<Id>::T* __restrict__ x)
+{
+    using P = typename PairOf<Id>::T;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const P e = in[i];
+        P r;
+        r.x = e.y;
+        r.y = e.x;
+        x[2 * i] = e;
+        x[2 * i + 1] = r;
+    }
+}
+
+template <typename P>
+__device__ __forceinline__ bool same_pair(const P& a, const P& b)
+{
+    return a.x == b.x && a.y == b.y;
+}
+
+// S[i] = i where a run of equal pairs starts, else 0 (a prefix max then
+// gives every position the start of its run).
+template <typename Id>
+__global__ void __launch_bounds__(256) csr_runstart_kernel(const typename PairOf<Id>::T* __restrict__ s,
+                                                           uint64_t M, uint64_t* __restrict__ S)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride)
+        S[i] = (i == 0 || !same_pair(s[i], s[i - 1])) ? i : 0;
+}
+
+// Whether sorted position i survives the options.
+template <typename P>
+__device__ __forceinline__ bool keep_at(const P* s, uint64_t M, uint64_t i, uint32_t flags,
+                                        const uint64_t* S)
+{
+    const P e = s[i];
+    if ((flags & kOptNoLoops) && e.x == e.y) return false;
+    if (flags & kOptOdd) {
+        const bool end = (i + 1 == M) || !same_pair(s[i + 1], e);
+        return end && (((i + 1 - S[i]) & 1) != 0);
+    }
+    if (flags & kOptDedup) return i == 0 || !same_pair(s[i - 1], e);
+    return true;
+}
+
+template <typename Id>
+__global__ void __launch_bounds__(256) csr_keep_count_kernel(const typename PairOf<Id>::T* __restrict__ s,
+                                                             uint64_t M, uint32_t flags,
+                                                             const uint64_t* __restrict__ S,
+                                                             uint64_t* __restrict__ part)
+{
+    __shared__ uint64_t s_warp[32];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    uint64_t cnt = 0;
+    for (uint32_t t = threadIdx.x; t < kScanTile; t += blockDim.x)
+        if (base + t < M) cnt += keep_at(s, M, base + t, flags, S) ? 1 : 0;
+    uint64_t total;
+    block_exclusive_scan(cnt, s_warp, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Each thread takes kScanTile/256 consecutive positions of its tile, so the
+// kept destinations are written in sorted order; the last position of every
+// row writes row_ptr[src + 1] = kept entries up to and including it.
+template <typename Id>
+__global__ void __launch_bounds__(256) csr_keep_apply_kernel(const typename PairOf<Id>::T* __restrict__ s,
+                                                             uint64_t M, uint64_t N, uint32_t flags,
+                                                             const uint64_t* __restrict__ S,
+                                                             const uint64_t* __restrict__ part,
+                                                             Id* __restrict__ col,
+                                                             uint64_t* __restrict__ row_ptr)
+{
+    __shared__ uint64_t s_warp[32];
+    constexpr int per = kScanTile / 256;
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * per;
+    uint32_t keep = 0;
+#pragma unroll
+    for (int t = 0; t < per; ++t)
+        if (base + t < M && keep_at(s, M, base + t, flags, S)) keep |= 1u << t;
+    uint64_t total;
+    uint64_t e = part[blockIdx.x] + block_exclusive_scan((uint64_t)__popc(keep), s_warp, total);
+#pragma unroll
+    for (int t = 0; t < per; ++t) {
+        const uint64_t i = base + t;
+        if (i >= M) break;
+        const uint64_t v = s[i].x;
+        if (keep & (1u << t)) col[e++] = (Id)s[i].y;
+        if (v < N && (i + 1 == M || (uint64_t)s[i + 1].x != v)) row_ptr[v + 1] = e;
+    }
+}
+
 int bit_length(uint64_t x)
 {
     int b = 0;
@@ -507,42 +608,33 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
 }
 
 template <typename Id>
-cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_row_ptr, void* d_col,
-                     void* d_ws, cudaStream_t s)
+void set_csr_attributes()
 {
-    using P = typename PairOf<Id>::T;
-    const CsrLayout L = csr_layout(M, N, sizeof(P));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(radix_scatter_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scatter_smem_bytes<Id>());
         attr = true;
     }
-    unsigned char* ws = (unsigned char*)d_ws;
+}
+
+// LSD radix passes over M pairs starting at `in` (dst digits, then src
+// digits). *sorted receives the sorted list (in itself when there is no
+// digit to sort), *spare a ping-pong buffer the result does not occupy.
+template <typename Id>
+cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t N, const CsrLayout& L,
+                         unsigned char* ws, const uint32_t* sort_needed, cudaStream_t s,
+                         const typename PairOf<Id>::T** sorted, typename PairOf<Id>::T** spare)
+{
+    using P = typename PairOf<Id>::T;
     P* buf[2] = {(P*)(ws + L.off_a), (P*)(ws + L.off_b)};
     uint32_t* H = (uint32_t*)(ws + L.off_h);
     uint64_t* Hs = (uint64_t*)(ws + L.off_hs);
     uint64_t* part = (uint64_t*)(ws + L.off_part);
-    uint32_t* sort_needed = (uint32_t*)(ws + L.off_flag);
     cudaError_t err;
-    const uint64_t work = M + 1;
-    int grid = (int)((work + 255) / 256);
-    const int cap = device_sm_count() * 8;
-    if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    if (cudaMemsetAsync(sort_needed, 0, 4, s) != cudaSuccess) return cudaErrorUnknown;
-    if (cudaMemsetAsync(d_row_ptr, 0, (N + 1) * 8, s) != cudaSuccess) return cudaErrorUnknown;
-    {
-        TraceScope trace("csr_check", s);
-        csr_check_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, sort_needed);
-        csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, N, (Id*)d_col, d_row_ptr,
-                                                   sort_needed);
-    }
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-
     const int bits = bit_length(N > 0 ? N - 1 : 0);
     const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
-    const P* cur = (const P*)d_edges;
+    const P* cur = in;
     int which = 0;
     if (M > 0) {
         for (int field = 0; field < 2; ++field) {      // dst digits, then src digits
@@ -578,13 +670,126 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
             }
         }
     }
+    *sorted = cur;
+    *spare = buf[which];
+    return cudaSuccess;
+}
+
+// In-place prefix maximum over n uint64 (three kernels).
+cudaError_t prefix_max(uint64_t* data, uint64_t n, uint64_t* parts, cudaStream_t s)
+{
+    const uint64_t n_parts = (n + kScanTile - 1) / kScanTile;
+    if (n_parts == 0) return cudaSuccess;
+    max_reduce_kernel<<<(unsigned)n_parts, 256, 0, s>>>(data, n, parts);
+    max_parts_kernel<<<1, 1024, 0, s>>>(parts, n_parts);
+    max_apply_kernel<<<(unsigned)n_parts, 256, 0, s>>>(data, n, parts);
+    return cudaGetLastError();
+}
+
+int sort_grid(uint64_t work)
+{
+    int grid = (int)((work + 255) / 256);
+    const int cap = device_sm_count() * 8;
+    if (grid > cap) grid = cap;
+    return grid < 1 ? 1 : grid;
+}
+
+template <typename Id>
+cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_row_ptr, void* d_col,
+                     void* d_ws, cudaStream_t s)
+{
+    using P = typename PairOf<Id>::T;
+    const CsrLayout L = csr_layout(M, N, sizeof(P));
+    set_csr_attributes<Id>();
+    unsigned char* ws = (unsigned char*)d_ws;
+    uint32_t* sort_needed = (uint32_t*)(ws + L.off_flag);
+    cudaError_t err;
+    const int grid = sort_grid(M + 1);
+    if (cudaMemsetAsync(sort_needed, 0, 4, s) != cudaSuccess) return cudaErrorUnknown;
+    if (cudaMemsetAsync(d_row_ptr, 0, (N + 1) * 8, s) != cudaSuccess) return cudaErrorUnknown;
+    {
+        TraceScope trace("csr_check", s);
+        csr_check_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, sort_needed);
+        csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, N, (Id*)d_col, d_row_ptr,
+                                                   sort_needed);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const P* cur;
+    P* spare;
+    if ((err = radix_passes<Id>((const P*)d_edges, M, N, L, ws, sort_needed, s, &cur, &spare)) !=
+        cudaSuccess)
+        return err;
     TraceScope trace("csr_finish", s);
     csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed);
-    uint64_t* rpart = (uint64_t*)(ws + L.off_rpart);
-    max_reduce_kernel<<<(unsigned)L.n_rparts, 256, 0, s>>>(d_row_ptr, N + 1, rpart);
-    max_parts_kernel<<<1, 1024, 0, s>>>(rpart, L.n_rparts);
-    max_apply_kernel<<<(unsigned)L.n_rparts, 256, 0, s>>>(d_row_ptr, N + 1, rpart);
-    return cudaGetLastError();
+    return prefix_max(d_row_ptr, N + 1, (uint64_t*)(ws + L.off_rpart), s);
+}
+
+// Workspace of the options path: the sort's layout for the (possibly
+// doubled) list, then the doubled list, and the parts of two scans.
+struct OptsLayout {
+    CsrLayout L;
+    size_t off_x, off_cpart, off_spart, total;
+    uint64_t M2, n_cparts;
+};
+
+OptsLayout opts_layout(uint64_t M, uint64_t N, uint32_t flags, size_t pair_bytes)
+{
+    OptsLayout O;
+    O.M2 = (flags & kOptSym) ? 2 * M : M;
+    O.L = csr_layout(O.M2, N, pair_bytes);
+    size_t o = a256(O.L.total);
+    O.off_x = o;
+    if (flags & kOptSym) o += a256(O.M2 * pair_bytes);
+    O.n_cparts = (O.M2 + kScanTile - 1) / kScanTile;
+    O.off_cpart = o;
+    o += a256((O.n_cparts + 1) * 8);
+    O.off_spart = o;
+    o += a256((O.n_cparts + 1) * 8);
+    O.total = o;
+    return O;
+}
+
+template <typename Id>
+cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t flags,
+                          uint64_t* d_row_ptr, void* d_col, void* d_ws, cudaStream_t s)
+{
+    using P = typename PairOf<Id>::T;
+    const OptsLayout O = opts_layout(M, N, flags, sizeof(P));
+    set_csr_attributes<Id>();
+    unsigned char* ws = (unsigned char*)d_ws;
+    uint32_t* sort_needed = (uint32_t*)(ws + O.L.off_flag);
+    cudaError_t err;
+    const uint64_t M2 = O.M2;
+    // every option needs the sorted list: the sort kernels run unconditionally
+    if (cudaMemsetAsync(sort_needed, 1, 4, s) != cudaSuccess) return cudaErrorUnknown;
+    if (cudaMemsetAsync(d_row_ptr, 0, (N + 1) * 8, s) != cudaSuccess) return cudaErrorUnknown;
+    const P* in = (const P*)d_edges;
+    if ((flags & kOptSym) && M > 0) {
+        P* x = (P*)(ws + O.off_x);
+        csr_sym_kernel<Id><<<sort_grid(M), 256, 0, s>>>(in, M, x);
+        in = x;
+    }
+    const P* cur;
+    P* spare;
+    if ((err = radix_passes<Id>(in, M2, N, O.L, ws, sort_needed, s, &cur, &spare)) != cudaSuccess)
+        return err;
+    TraceScope trace("csr_compact", s);
+    if (M2 > 0) {
+        uint64_t* S = nullptr;
+        if (flags & kOptOdd) {
+            S = reinterpret_cast<uint64_t*>(spare);    // M2 words fit: a pair is >= 8 bytes
+            csr_runstart_kernel<Id><<<sort_grid(M2), 256, 0, s>>>(cur, M2, S);
+            if ((err = prefix_max(S, M2, (uint64_t*)(ws + O.off_spart), s)) != cudaSuccess)
+                return err;
+        }
+        uint64_t* cpart = (uint64_t*)(ws + O.off_cpart);
+        csr_keep_count_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, flags, S, cpart);
+        scan_parts_kernel<<<1, 1024, 0, s>>>(cpart, O.n_cparts, sort_needed);
+        csr_keep_apply_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, N, flags, S, cpart,
+                                                                        (Id*)d_col, d_row_ptr);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    return prefix_max(d_row_ptr, N + 1, (uint64_t*)(ws + O.L.off_rpart), s);
 }
 
 }  // namespace
@@ -595,6 +800,23 @@ size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices)
     const size_t a = csr_layout(n_edges, n_vertices, 16).total;
     const size_t b = csr_layout(n_edges, n_vertices, 8).total;
     return a > b ? a : b;
+}
+
+size_t csr_opts_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint32_t flags)
+{
+    const size_t a = opts_layout(n_edges, n_vertices, flags, 16).total;
+    const size_t b = opts_layout(n_edges, n_vertices, flags, 8).total;
+    return a > b ? a : b;
+}
+
+cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
+                            uint32_t flags, uint64_t* d_row_ptr, void* d_col, void* d_ws,
+                            cudaStream_t s)
+{
+    return id64 ? csr_opts_impl<uint64_t>(d_edges, n_edges, n_vertices, flags, d_row_ptr, d_col,
+                                          d_ws, s)
+                : csr_opts_impl<uint32_t>(d_edges, n_edges, n_vertices, flags, d_row_ptr, d_col,
+                                          d_ws, s);
 }
 
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,

@@ -196,6 +196,29 @@ __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ K
     }
 }
 
+// ---- random graph G(N, M) with replacement (the exclusive-or randomisation
+// of Sec. 3's PK method): edge e is the cell (uniform over N from (w1:w0),
+// uniform over N from (w3:w2)) of the draw with counter (e_lo, e_hi, 0, 4).
+template <typename Id>
+__global__ void __launch_bounds__(256) random_cells_kernel(const Key key, uint64_t N,
+                                                           Id* __restrict__ out, uint64_t e_begin,
+                                                           uint64_t n_edges)
+{
+    const uint64_t n_pairs = (n_edges + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
+        const uint64_t e = 2 * t;
+        const uint4 a = draw(e_begin + e, 0, 4, key);
+        if (e + 1 < n_edges) {
+            const uint4 b = draw(e_begin + e + 1, 0, 4, key);
+            Pair2<Id>::store(out, e, uniform64(a.x, a.y, N), uniform64(a.z, a.w, N),
+                             uniform64(b.x, b.y, N), uniform64(b.z, b.w, N));
+        } else {
+            Pair2<Id>::store1(out, e, uniform64(a.x, a.y, N), uniform64(a.z, a.w, N));
+        }
+    }
+}
+
 template <typename K>
 int grid_for(K kernel, uint64_t work_items, int threads)
 {
@@ -249,6 +272,22 @@ cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint6
     } else {
         auto k = kron_det_kernel<uint32_t>;
         k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_random_cells(const Key& key, uint64_t n_vertices, int id64, void* d_out,
+                                uint64_t e_begin, uint64_t n_edges, cudaStream_t s)
+{
+    if (n_edges == 0) return cudaSuccess;
+    const uint64_t pairs = (n_edges + 1) / 2;
+    TraceScope trace("random_cells", s);
+    if (id64) {
+        auto k = random_cells_kernel<uint64_t>;
+        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(key, n_vertices, (uint64_t*)d_out, e_begin, n_edges);
+    } else {
+        auto k = random_cells_kernel<uint32_t>;
+        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(key, n_vertices, (uint32_t*)d_out, e_begin, n_edges);
     }
     return cudaGetLastError();
 }

@@ -37,6 +37,8 @@ cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, u
                                    uint64_t n_edges, cudaStream_t s);
 cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint64_t e_begin,
                             uint64_t n_edges, cudaStream_t s);
+cudaError_t launch_random_cells(const Key& key, uint64_t n_vertices, int id64, void* d_out,
+                                uint64_t e_begin, uint64_t n_edges, cudaStream_t s);
 
 // PBA (two-phase preferential attachment) geometry.
 struct PbaGeom {
@@ -93,6 +95,10 @@ cudaError_t launch_pba(const PbaGeom& g, int id64, void* d_out, void* d_ws, cuda
                        const HostCopy* hc = nullptr);
 
 // CSR assembly.
+size_t csr_opts_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint32_t flags);
+cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
+                            uint32_t flags, uint64_t* d_row_ptr, void* d_col, void* d_ws,
+                            cudaStream_t s);
 size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices);
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                        uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,

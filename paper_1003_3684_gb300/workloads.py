@@ -26,6 +26,20 @@ CONFIGS = {
     # blocks of 2^20, 5 edges each, inter-block fraction 0.1
     "pba_n2p30_b1024_m5": dict(kind="pba", n=2**30, m=5, blocks=1024, n0=6, faction_width=1,
                                inter_frac=0.1, seed=3),
+    # the headline PBA with overlapping factions: block p's list names its
+    # neighbours p-1, p, p+1 (mod 1024), so every block shares its faction
+    # with two others, as F0..F2 of Fig. 1 overlap
+    "pba_n2p30_b1024_m5_factions": dict(kind="pba", n=2**30, m=5, blocks=1024, n0=6,
+                                        faction_width=1, factions="ring3", inter_frac=0.1,
+                                        seed=3),
+    # the headline PBA made in 8 ranges of 128 blocks through an output buffer
+    # one eighth of the graph (prepare once, then each range on demand)
+    "pba_n2p30_b1024_m5_parts8": dict(kind="pba", n=2**30, m=5, blocks=1024, n0=6,
+                                      faction_width=1, inter_frac=0.1, seed=3, parts=8),
+    # Kronecker k = 20 made irregular by exclusive-or with a random graph of
+    # 2^20 cells, then CSR keeping the cells of odd multiplicity
+    "kron_k20_m16x_xor": dict(kind="kron_xor", initiator=KRON_INITIATOR, k=20,
+                              n_edges=16 * 2**20, n_random=2**20, seed=7),
     # 4096 independent graphs of uneven sizes in one persistent launch
     "batch_4096_mixed": dict(kind="batch", n_jobs=4096, seed=0),
     # served requests: Poisson arrivals at 2000/s, half BA / half Kronecker,
@@ -34,6 +48,12 @@ CONFIGS = {
     "serve_poisson_2000": dict(kind="serve", rate=2000.0, duration=20.0, budget=64 << 30,
                                seed=0),
 }
+
+
+def ring_factions(B: int, width: int = 3):
+    """Faction lists of a ring: block p's list is p - width//2 .. p + width//2 (mod B)."""
+    h = width // 2
+    return [[(p + d) % B for d in range(-h, width - h)] for p in range(B)]
 
 
 def random_edges(seed: int, n_edges: int, n_vertices: int, id64: bool = False,

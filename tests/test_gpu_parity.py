@@ -364,6 +364,58 @@ def test_csr_row_length_classes(N, id64):
     csr_check(e, N, id64)
 
 
+def _multigraph(seed, M, N, id64):
+    rng = np.random.default_rng(seed)
+    e = rng.integers(0, N, size=(M, 2), dtype=np.uint64)
+    if M > 5:
+        e[: M // 5] = e[M // 5: 2 * (M // 5)]        # repeated pairs
+        e[::11, 1] = e[::11, 0]                       # self-loops
+        e[3::97] = e[5]                               # one pair many times
+    return e.astype(np.uint64 if id64 else np.uint32)
+
+
+@pytest.mark.parametrize("flags", [1, 2, 4, 8, 1 | 2, 2 | 4, 1 | 2 | 4, 8 | 4, 1 | 8])
+@pytest.mark.parametrize("M,N,id64", [(50_001, 3000, False), (20_000, 2**22 + 5, True),
+                                      (9_999, 1, False), (0, 7, False)])
+def test_csr_options_match_oracle(flags, M, N, id64):
+    e = _multigraph(M + flags, M, N, id64)
+    t = torch.from_numpy(e.view(np.int64 if id64 else np.int32)).cuda()
+    rp, col = pg.edges_to_csr_opts(t, N, flags)
+    torch.cuda.synchronize()
+    ref_rp, ref_col = o.csr_opts(e.astype(np.uint64), N, flags)
+    got_rp = rp.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got_rp, ref_rp)
+    k = int(got_rp[-1])
+    assert_same(host(col, id64)[:k], ref_col)
+
+
+@pytest.mark.parametrize("N,M,id64", [(1000, 100_001, False), (2**40 + 7, 50_000, True), (1, 33, False)])
+def test_random_cells_match_oracle(N, M, id64):
+    got = pg.gen_random_cells(N, M, seed=2**33 + 9, id64=id64)
+    torch.cuda.synchronize()
+    assert_same(host(got, id64), o.random_cells(N, M, 2**33 + 9))
+
+
+@pytest.mark.parametrize("deterministic", [True, False])
+def test_kronecker_xor_random_matches_oracle(golden, deterministic):
+    if deterministic:
+        G = np.array([[float(x) for x in r] for r in golden("pk_fig2_seed.txt")])
+        k, n_edges = 4, 0
+        pk = o.kron_det(G, k)[0]
+    else:
+        G, k, n_edges = W.KRON_INITIATOR, 12, 40_000
+        pk = o.kron(G, k, n_edges, 5)
+    N = len(G) ** k
+    rnd = o.random_cells(N, 3000, 5)
+    rp, col = pg.kronecker_xor_random(G, k, 3000, n_edges=n_edges, seed=5,
+                                      deterministic=deterministic)
+    torch.cuda.synchronize()
+    ref_rp, ref_col = o.csr_opts(np.concatenate([pk, rnd]), N, o.CSR_ODD)
+    got_rp = rp.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got_rp, ref_rp)
+    assert_same(host(col)[:int(got_rp[-1])], ref_col)
+
+
 def test_csr_of_kronecker_and_pba_graphs():
     ek = o.kron(W.KRON_INITIATOR, 16, 2**20, 7).astype(np.uint32)
     csr_check(ek, 2**16)
