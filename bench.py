@@ -189,8 +189,22 @@ def oracle_sample(name: str, cfg: dict, budget_s: float):
     if cfg["kind"] == "serve":
         from paper_1003_3684_gb300 import serve
         trace = serve.poisson_workload(cfg["rate"], 2.0, seed=cfg["seed"])
+    if cfg["kind"] == "bfs":
+        # the oracle BFS over the undirected CSR of a 2-block graph of the same
+        # block size (built once, not timed), from a new source each sample
+        nb = cfg["n"] // cfg["blocks"]
+        e, _, _ = o.pba(2 * nb, cfg["m"], 2, cfg["n0"], 1, cfg["inter_frac"], cfg["seed"])
+        Ns = 2 * (cfg["n0"] + nb)
+        rp, col = o.csr_opts(e, Ns, o.CSR_SYMMETRIZE)
     while samples == 0 or t_total < budget_s:
-        if cfg["kind"] == "serve":
+        if cfg["kind"] == "bfs":
+            t0 = time.perf_counter()
+            _, _, sc = o.bfs(rp, col, (samples * 2654435761) % Ns)
+            t_total += time.perf_counter() - t0
+            edges_total += sc
+            desc = (f"or_bfs over the undirected CSR of a 2-block PBA graph (n_b={nb}, "
+                    f"m={cfg['m']}); adjacency entries scanned per sample")
+        elif cfg["kind"] == "serve":
             _, j = trace[(samples * 97) % len(trace)]
             t0 = time.perf_counter()
             e = (o.ba(j["n"], j["m"], j["n0"], j["seed"]) if j["kind"] == "pba"
@@ -270,14 +284,16 @@ def run_reference(args, rank: int, world: int):
         times.append(t)
         eps.append(v)
     value = sum(v * t for v, t in zip(eps, times)) / sum(times)
-    line = dict(impl="reference", metric="edges/sec", value=value, unit="edges/s",
+    metric, unit = (("scanned_entries/sec", "entries/s") if cfg["kind"] == "bfs"
+                    else ("edges/sec", "edges/s"))
+    line = dict(impl="reference", metric=metric, value=value, unit=unit,
                 n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1000 * statistics.mean(times), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
                 config=dict(workload=args.workload, sample=desc),
-                cpu_baseline=dict(kind="oracle", value=value, unit="edges/s", cores=1,
+                cpu_baseline=dict(kind="oracle", value=value, unit=unit, cores=1,
                                   sample=desc),
-                e2e=dict(value=value, unit="edges/s", h2d_bytes_per_step=0,
+                e2e=dict(value=value, unit=unit, h2d_bytes_per_step=0,
                          d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -412,7 +428,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                          unit="GB/s", frac=total * 8 / waves / per_launch / (peaks["hbm_gbs"] * 1e9)),
                 ms_per_launch=per_launch * 1000.0,
                 peak_source=f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz")
-    line = dict(metric="edges/sec", value=value, unit="edges/s", n_gpus=world, steps=args.steps,
+    metric, unit = ("scanned_entries/sec", "entries/s") if kind == "bfs" else ("edges/sec", "edges/s")
+    line = dict(metric=metric, value=value, unit=unit, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
                 config=dict(workload=args.workload, n_jobs=len(jobs), edges_per_step=total,
@@ -589,6 +606,36 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
         if parts > 1:
             cfg_json["parts"] = (f"{parts} ranges of {B // parts} blocks through one buffer of "
                                  f"{out.numel() * 4 / 1e9:.2f} GB")
+    elif kind == "bfs":
+        n, m, B, n0 = cfg["n"], cfg["m"], cfg["blocks"], cfg["n0"]
+        Ep = pg.pg_pba_edge_count(n, m, B, n0)
+        N = B * (n0 + n // B)
+        edges = pg.gen_pba(n, m, B, n0, cfg["faction_width"], cfg["inter_frac"], seed)
+        row_ptr, col = pg.edges_to_csr_opts(edges, N, pg.CSR_SYMMETRIZE)
+        del edges
+        torch.cuda.synchronize()
+        dist = torch.empty(N, dtype=torch.int32, device=dev)
+        bws = torch.empty(pg._analysis_lib().pg_bfs_workspace_size(N), dtype=torch.uint8,
+                          device=dev)
+        sources = [(i * 2654435761) % N for i in range(cfg["sources"])]
+        scanned_per_step = [0]
+
+        def step():
+            tot = 0
+            for src in sources:
+                _, _, sc = pg.bfs(row_ptr, col, src, dist=dist, workspace=bws)
+                tot += sc
+            scanned_per_step[0] = tot
+        step()
+        E = scanned_per_step[0]
+        units = {"bfs": E}
+        work = {"bfs": dict(ops=0, bytes=8)}     # col entry + the distance it tests
+        out = dist
+        out_bytes = N * 4
+        cfg_json = dict(workload=args.workload, n=n, m=m, blocks=B, n0=n0, vertices=N,
+                        csr_entries=2 * Ep, sources=len(sources),
+                        metric_note="adjacency entries scanned per second over BFS from "
+                                    "each source (undirected CSR)", id_width=32)
     elif kind == "kron_xor":
         k, M, Mr = cfg["k"], cfg["n_edges"], cfg["n_random"]
         N = 2**k
@@ -728,7 +775,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
 
     # end to end through the public API with host buffers: the step plus the
     # device-to-host copy of everything it produced into pinned host memory
-    if not args.no_e2e:
+    if not args.no_e2e and kind != "bfs":
         if kind == "pba" and cfg.get("parts", 1) > 1:
             line["e2e"] = measure_e2e_parts(args, cfg, seed, out, ws, E, dev, world)
         elif kind == "pba" and not cfg.get("factions"):
@@ -737,7 +784,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, tsec, ns = oracle_sample(args.workload, cfg, args.cpu_budget)
-        line["cpu_baseline"] = dict(value=v, unit="edges/s", cores=1, kind="oracle",
+        line["cpu_baseline"] = dict(value=v, unit=unit, cores=1, kind="oracle",
                                     sample=f"{desc}; {ns} samples, {tsec:.1f} s")
     if rank == 0:
         print(json.dumps(line), flush=True)

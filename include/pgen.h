@@ -303,6 +303,39 @@ pg_status gen_random_cells(uint64_t n_vertices, uint64_t n_edges, uint64_t seed,
                            void* d_edges, uint64_t cap_edges, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Graph-property checks (Sec. 4 studies the degree distribution and the path
+ * lengths of the generated graphs). Exact integer results.
+ *
+ * pg_degrees: d_deg[v] (n_vertices uint64, cleared by the call) = number of
+ *   edges with src == v (PG_DEG_OUT), dst == v (PG_DEG_IN), or both counted
+ *   (PG_DEG_TOTAL; a self-loop counts twice). Ids >= n_vertices are skipped.
+ * pg_degree_histogram: d_hist (max_degree + 2 uint64, cleared by the call)
+ *   [d] = number of vertices of degree d for d <= max_degree, and
+ *   [max_degree + 1] = the number of vertices of larger degree.
+ * pg_bfs: breadth-first search over a CSR graph (row_ptr, col as
+ *   edges_to_csr writes them; for undirected distances pass the CSR of
+ *   edges_to_csr_opts with PG_CSR_SYMMETRIZE) from `source`:
+ *   d_dist[v] (n_vertices uint32) = hops from source, 0xFFFFFFFF where
+ *   unreached. n_vertices < 2^32 - 1. Workspace: pg_bfs_workspace_size()
+ *   bytes, 256-byte aligned. Unlike the generators, this call waits for the
+ *   stream once per BFS level (to read the next frontier's size);
+ *   *levels_out (host) = number of levels run (the source's eccentricity + 1
+ *   within its component), *scanned_out (host) = adjacency entries examined
+ *   (the sum of the reached vertices' row lengths).
+ * ---------------------------------------------------------------------- */
+#define PG_DEG_OUT 0
+#define PG_DEG_IN 1
+#define PG_DEG_TOTAL 2
+pg_status pg_degrees(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                     int which, uint64_t* d_deg, void* stream);
+pg_status pg_degree_histogram(const uint64_t* d_deg, uint64_t n_vertices, uint32_t max_degree,
+                              uint64_t* d_hist, void* stream);
+size_t pg_bfs_workspace_size(uint64_t n_vertices);
+pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertices, pg_idwidth w,
+                 uint64_t source, uint32_t* d_dist, void* d_ws, size_t ws_bytes,
+                 uint32_t* levels_out, uint64_t* scanned_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * Batched generation: many independent graphs in one persistent launch.
  *
  * A job is a serial BA graph (gen_pba with blocks = 1: n new vertices, m

@@ -69,9 +69,13 @@ def lib():
             L.or_csr.argtypes = [P, u64, u64, P, P]
             L.or_csr_opts.argtypes = [P, u64, u64, u32, P, P, P]
             L.or_random_cells.argtypes = [u64, u64, u64, P]
+            L.or_degrees.argtypes = [P, u64, u64, C.c_int, P]
+            L.or_degree_histogram.argtypes = [P, u64, u64, P]
+            L.or_bfs.argtypes = [P, P, u64, u64, P, P, P]
             for name in ("or_ba", "or_pba_count", "or_pba_phase1_general", "or_pba_phase1", "or_pba_endpoints",
                          "or_pba_substitute", "or_pba", "or_pba_factions", "or_kron_thresholds", "or_kron",
-                         "or_kron_det", "or_csr", "or_csr_opts", "or_random_cells"):
+                         "or_kron_det", "or_csr", "or_csr_opts", "or_random_cells", "or_degrees",
+                         "or_degree_histogram", "or_bfs"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -242,6 +246,36 @@ def random_cells(n_vertices: int, n_edges: int, seed: int) -> np.ndarray:
     out = np.zeros((max(n_edges, 1), 2), dtype=np.uint64)
     _check(lib().or_random_cells(n_vertices, n_edges, seed, _ptr(out)), "random_cells")
     return out[:n_edges]
+
+
+DEG_OUT, DEG_IN, DEG_TOTAL = 0, 1, 2
+
+
+def degrees(edges, n_vertices: int, which: int) -> np.ndarray:
+    e = np.ascontiguousarray(edges, dtype=np.uint64).reshape(-1, 2)
+    deg = np.zeros(max(n_vertices, 1), dtype=np.uint64)
+    _check(lib().or_degrees(_ptr(e), e.shape[0], n_vertices, which, _ptr(deg)), "degrees")
+    return deg[:n_vertices]
+
+
+def degree_histogram(deg, max_degree: int) -> np.ndarray:
+    d = np.ascontiguousarray(deg, dtype=np.uint64)
+    hist = np.zeros(max_degree + 2, dtype=np.uint64)
+    _check(lib().or_degree_histogram(_ptr(d), d.size, max_degree, _ptr(hist)), "degree_histogram")
+    return hist
+
+
+def bfs(row_ptr, col, source: int):
+    """BFS distances (uint32, 0xFFFFFFFF unreached), levels, scanned entries."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+    c = np.ascontiguousarray(col, dtype=np.uint64)
+    N = rp.size - 1
+    dist = np.zeros(max(N, 1), dtype=np.uint32)
+    lv = np.zeros(1, dtype=np.uint32)
+    sc = np.zeros(1, dtype=np.uint64)
+    _check(lib().or_bfs(_ptr(rp), _ptr(c if c.size else np.zeros(1, np.uint64)), N, source,
+                        _ptr(dist), _ptr(lv), _ptr(sc)), "bfs")
+    return dist[:N], int(lv[0]), int(sc[0])
 
 
 def csr(edges, n_vertices: int):

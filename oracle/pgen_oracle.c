@@ -615,3 +615,58 @@ int or_csr(const uint64_t* pairs, uint64_t M, uint64_t N, uint64_t* row_ptr, uin
     free(s);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Graph properties (Sec. 4 examines degree distributions and path lengths). */
+/* which: 0 = out (src), 1 = in (dst), 2 = both ends counted.               */
+/* ------------------------------------------------------------------------ */
+int or_degrees(const uint64_t* pairs, uint64_t M, uint64_t N, int which, uint64_t* deg)
+{
+    if (which < 0 || which > 2) return 1;
+    for (uint64_t v = 0; v < N; ++v) deg[v] = 0;
+    for (uint64_t e = 0; e < M; ++e) {
+        uint64_t a = pairs[2 * e], b = pairs[2 * e + 1];
+        if (which != 1 && a < N) deg[a]++;
+        if (which != 0 && b < N) deg[b]++;
+    }
+    return 0;
+}
+
+int or_degree_histogram(const uint64_t* deg, uint64_t N, uint64_t max_deg, uint64_t* hist)
+{
+    for (uint64_t d = 0; d < max_deg + 2; ++d) hist[d] = 0;
+    for (uint64_t v = 0; v < N; ++v) hist[deg[v] <= max_deg ? deg[v] : max_deg + 1]++;
+    return 0;
+}
+
+/* Breadth-first search with an explicit FIFO queue; dist = UINT32_MAX where */
+/* unreached. *levels = 1 + the largest distance; *scanned = the sum of the  */
+/* row lengths of the reached vertices.                                      */
+int or_bfs(const uint64_t* row_ptr, const uint64_t* col, uint64_t N, uint64_t source,
+           uint32_t* dist, uint32_t* levels, uint64_t* scanned)
+{
+    if (source >= N) return 1;
+    uint64_t* queue = (uint64_t*)malloc(sizeof(uint64_t) * (N ? N : 1));
+    if (!queue) return 2;
+    for (uint64_t v = 0; v < N; ++v) dist[v] = 0xFFFFFFFFu;
+    uint64_t head = 0, tail = 0, sc = 0;
+    uint32_t deepest = 0;
+    dist[source] = 0;
+    queue[tail++] = source;
+    while (head < tail) {
+        uint64_t v = queue[head++];
+        sc += row_ptr[v + 1] - row_ptr[v];
+        if (dist[v] > deepest) deepest = dist[v];
+        for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            uint64_t u = col[e];
+            if (u < N && dist[u] == 0xFFFFFFFFu) {
+                dist[u] = dist[v] + 1;
+                queue[tail++] = u;
+            }
+        }
+    }
+    *levels = deepest + 1;
+    *scanned = sc;
+    free(queue);
+    return 0;
+}

@@ -40,4 +40,9 @@ int or_csr_opts(const uint64_t* pairs, uint64_t M, uint64_t N, uint32_t flags, u
                 uint64_t* col, uint64_t* M_out);
 int or_random_cells(uint64_t N, uint64_t M, uint64_t seed, uint64_t* out);
 
+int or_degrees(const uint64_t* pairs, uint64_t M, uint64_t N, int which, uint64_t* deg);
+int or_degree_histogram(const uint64_t* deg, uint64_t N, uint64_t max_deg, uint64_t* hist);
+int or_bfs(const uint64_t* row_ptr, const uint64_t* col, uint64_t N, uint64_t source,
+           uint32_t* dist, uint32_t* levels, uint64_t* scanned);
+
 #endif

@@ -32,6 +32,8 @@ __all__ = [
     "pba_faction_table", "gen_pba_factions", "pg_pba_prepare", "gen_pba_blocks",
     "gen_kronecker_range", "philox_rate", "edges_to_csr_opts", "gen_random_cells",
     "kronecker_xor_random", "CSR_SYMMETRIZE", "CSR_DEDUP", "CSR_NO_LOOPS", "CSR_ODD",
+    "DEG_OUT", "DEG_IN", "DEG_TOTAL", "degrees", "degree_histogram", "bfs", "powerlaw_exponent",
+    "path_length_stats",
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
 ]
@@ -386,6 +388,90 @@ def philox_rate(calls_per_thread: int = 2048, reps: int = 3, device="cuda") -> f
         if i > 0 and (best is None or ms < best):      # the first launch is a warm-up
             best = ms
     return n * calls_per_thread / (best / 1000.0)
+
+
+DEG_OUT, DEG_IN, DEG_TOTAL = 0, 1, 2
+
+
+def _analysis_lib():
+    L = lib()
+    if not getattr(L, "_analysis_ready", False):
+        L.pg_degrees.argtypes = [vp, u64, u64, i32, C.c_int, vp, vp]
+        L.pg_degrees.restype = i32
+        L.pg_degree_histogram.argtypes = [vp, u64, u32, vp, vp]
+        L.pg_degree_histogram.restype = i32
+        L.pg_bfs_workspace_size.argtypes = [u64]
+        L.pg_bfs_workspace_size.restype = sz
+        L.pg_bfs.argtypes = [vp, vp, u64, i32, u64, vp, vp, sz, C.POINTER(u32),
+                             C.POINTER(u64), vp]
+        L.pg_bfs.restype = i32
+        L._analysis_ready = True
+    return L
+
+
+def degrees(edges, n_vertices: int, which: int = DEG_TOTAL, out=None, stream=None):
+    """Vertex degrees of an (E, 2) edge tensor as int64[n_vertices] (counts)."""
+    import torch
+    if out is None:
+        out = _empty(max(n_vertices, 1), torch.int64, edges.device)
+    st = _analysis_lib().pg_degrees(_ptr(edges), edges.shape[0], n_vertices,
+                                    PG_ID64 if edges.dtype == torch.int64 else PG_ID32, which,
+                                    _ptr(out), _stream(stream))
+    _check("pg_degrees", st)
+    return out[:n_vertices]
+
+
+def degree_histogram(deg, max_degree: int, out=None, stream=None):
+    """int64[max_degree + 2]: vertices per degree, the last bucket all larger."""
+    import torch
+    if out is None:
+        out = _empty(max_degree + 2, torch.int64, deg.device)
+    st = _analysis_lib().pg_degree_histogram(_ptr(deg), deg.numel(), max_degree, _ptr(out),
+                                             _stream(stream))
+    _check("pg_degree_histogram", st)
+    return out
+
+
+def bfs(row_ptr, col, source: int, dist=None, workspace=None, stream=None):
+    """BFS hop distances from source (int32 view of uint32; -1 = unreached).
+
+    Returns (dist, levels, scanned). Waits for the stream once per level."""
+    import torch
+    L = _analysis_lib()
+    N = row_ptr.numel() - 1
+    if dist is None:
+        dist = _empty(max(N, 1), torch.int32, row_ptr.device)
+    if workspace is None:
+        workspace = _empty(L.pg_bfs_workspace_size(N), torch.uint8, row_ptr.device)
+    levels, scanned = u32(0), u64(0)
+    st = L.pg_bfs(_ptr(row_ptr), _ptr(col), N, PG_ID64 if col.dtype == torch.int64 else PG_ID32,
+                  source, _ptr(dist), _ptr(workspace), workspace.numel(), C.byref(levels),
+                  C.byref(scanned), _stream(stream))
+    _check("pg_bfs", st)
+    return dist[:N], int(levels.value), int(scanned.value)
+
+
+def powerlaw_exponent(hist, d_min: int) -> float:
+    """Discrete power-law exponent of a degree histogram over degrees >= d_min
+    (Clauset, Shalizi & Newman 2009, the approximate discrete MLE
+    1 + n / sum(ln(d / (d_min - 1/2)))). Host arithmetic on the counts;
+    the overflow bucket of degree_histogram is left out."""
+    h = np.asarray(hist, dtype=np.float64)[:-1]
+    d = np.arange(h.size, dtype=np.float64)
+    sel = d >= d_min
+    n = h[sel].sum()
+    if n == 0:
+        raise ValueError("no vertex of degree >= d_min")
+    return 1.0 + n / float((h[sel] * np.log(d[sel] / (d_min - 0.5))).sum())
+
+
+def path_length_stats(dist) -> dict:
+    """Mean and largest hop distance over the vertices a BFS reached (source excluded)."""
+    d = np.asarray(dist).view(np.uint32).astype(np.int64)
+    reached = d[(d != 0xFFFFFFFF) & (d > 0)]
+    return dict(reached=int(reached.size) + 1,
+                mean=float(reached.mean()) if reached.size else 0.0,
+                max=int(reached.max()) if reached.size else 0)
 
 
 def pg_csr_workspace_size(n_edges: int, n_vertices: int) -> int:

@@ -1,0 +1,213 @@
+// Graph-property checks on generated graphs (Sec. 4 examines the degree
+// distribution and path lengths of the generated graphs): vertex degrees,
+// their histogram, and breadth-first search distances from a source.
+//
+// Every result is exact integer work. Degrees and histogram counts are sums
+// (atomic order does not change them); BFS distances are unique even though
+// the order in which a level's vertices are found depends on the schedule.
+#include <cstring>
+
+#include "../../include/pgen.h"
+#include "pg_internal.h"
+#include "pg_trace.h"
+
+namespace pgen {
+namespace {
+
+constexpr uint32_t kUnreached = 0xFFFFFFFFu;
+constexpr uint32_t kHistSmem = 8192;   // histograms up to this many buckets count in smem
+
+template <typename Id>
+__global__ void __launch_bounds__(256) degree_kernel(const Id* __restrict__ e, uint64_t M,
+                                                     uint64_t N, int which,
+                                                     unsigned long long* __restrict__ deg)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const uint64_t s = e[2 * i], d = e[2 * i + 1];
+        if (which != PG_DEG_IN && s < N) atomicAdd(&deg[s], 1ull);
+        if (which != PG_DEG_OUT && d < N) atomicAdd(&deg[d], 1ull);
+    }
+}
+
+// hist[d] = #{v : deg[v] = d} for d <= max_deg, hist[max_deg + 1] = the rest.
+__global__ void __launch_bounds__(256) histogram_kernel(const uint64_t* __restrict__ deg, uint64_t N,
+                                                        uint32_t max_deg,
+                                                        unsigned long long* __restrict__ hist)
+{
+    __shared__ uint32_t h[kHistSmem];
+    const uint32_t nb = max_deg + 2;
+    const bool in_smem = nb <= kHistSmem;
+    if (in_smem) {
+        for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) h[t] = 0;
+        __syncthreads();
+    }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += stride) {
+        const uint64_t d = deg[v];
+        const uint32_t b = d <= max_deg ? (uint32_t)d : max_deg + 1;
+        if (in_smem) atomicAdd(&h[b], 1u);
+        else atomicAdd(&hist[b], 1ull);
+    }
+    if (in_smem) {
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x)
+            if (h[t]) atomicAdd(&hist[t], (unsigned long long)h[t]);
+    }
+}
+
+// One BFS level: each warp takes frontier vertices in turn and its lanes
+// walk the vertex's row; a neighbour still unreached is claimed with one
+// compare-and-swap and appended to the next frontier (one atomic per warp
+// iteration for the appends). scanned += the degrees of the frontier.
+template <typename Id>
+__global__ void __launch_bounds__(256) bfs_level_kernel(const uint64_t* __restrict__ row_ptr,
+                                                        const Id* __restrict__ col,
+                                                        const uint32_t* __restrict__ frontier,
+                                                        uint32_t fsize, uint32_t* __restrict__ next,
+                                                        uint32_t* __restrict__ nsize,
+                                                        uint32_t* __restrict__ dist, uint32_t level,
+                                                        uint64_t N,
+                                                        unsigned long long* __restrict__ scanned)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long seen = 0;
+    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < fsize; i += warps) {
+        const uint32_t v = frontier[i];
+        const uint64_t a = row_ptr[v], b = row_ptr[v + 1];
+        seen += b - a;
+        for (uint64_t base = a; base < b; base += 32) {
+            const uint64_t e = base + lane;
+            bool claim = false;
+            uint32_t u = 0;
+            if (e < b) {
+                const uint64_t u64 = col[e];
+                if (u64 < N) {
+                    u = (uint32_t)u64;
+                    claim = dist[u] == kUnreached && atomicCAS(&dist[u], kUnreached, level + 1) == kUnreached;
+                }
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, claim);
+            if (m) {
+                uint32_t at = 0;
+                if (lane == 0) at = atomicAdd(nsize, (uint32_t)__popc(m));
+                at = __shfl_sync(0xFFFFFFFFu, at, 0);
+                if (claim) next[at + __popc(m & lt)] = u;
+            }
+        }
+    }
+    if (lane == 0 && seen) atomicAdd(scanned, seen);
+}
+
+__global__ void bfs_seed_kernel(uint32_t* dist, uint32_t* frontier, uint32_t source)
+{
+    dist[source] = 0;
+    frontier[0] = source;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+int grid_cap(uint64_t items)
+{
+    const uint64_t full = (uint64_t)device_sm_count() * 8;
+    const uint64_t need = (items + 255) / 256;
+    return (int)(need < 1 ? 1 : (need < full ? need : full));
+}
+
+}  // namespace
+}  // namespace pgen
+
+using namespace pgen;
+
+extern "C" {
+
+pg_status pg_degrees(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                     int which, uint64_t* d_deg, void* stream)
+{
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (which != PG_DEG_OUT && which != PG_DEG_IN && which != PG_DEG_TOTAL) return PG_EINVAL;
+    if (n_vertices > 0 && !d_deg) return PG_EINVAL;
+    if (n_edges > 0 && !d_edges) return PG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_vertices > 0 && cudaMemsetAsync(d_deg, 0, n_vertices * 8, s) != cudaSuccess) return PG_ECUDA;
+    if (n_edges == 0) return PG_OK;
+    TraceScope trace("degrees", s);
+    const int grid = grid_cap(n_edges);
+    if (w == PG_ID64)
+        degree_kernel<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)d_edges, n_edges, n_vertices,
+                                                    which, (unsigned long long*)d_deg);
+    else
+        degree_kernel<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)d_edges, n_edges, n_vertices,
+                                                    which, (unsigned long long*)d_deg);
+    return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
+}
+
+pg_status pg_degree_histogram(const uint64_t* d_deg, uint64_t n_vertices, uint32_t max_degree,
+                              uint64_t* d_hist, void* stream)
+{
+    if (!d_hist || (n_vertices > 0 && !d_deg) || max_degree > 0xFFFFFFF0u) return PG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_hist, 0, ((size_t)max_degree + 2) * 8, s) != cudaSuccess) return PG_ECUDA;
+    if (n_vertices == 0) return PG_OK;
+    TraceScope trace("degree_histogram", s);
+    histogram_kernel<<<grid_cap(n_vertices), 256, 0, s>>>(d_deg, n_vertices, max_degree,
+                                                         (unsigned long long*)d_hist);
+    return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
+}
+
+size_t pg_bfs_workspace_size(uint64_t n_vertices)
+{
+    // two frontiers of n_vertices uint32, then the counters
+    return 2 * (((size_t)n_vertices * 4 + 255) & ~(size_t)255) + 256;
+}
+
+pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertices, pg_idwidth w,
+                 uint64_t source, uint32_t* d_dist, void* d_ws, size_t ws_bytes,
+                 uint32_t* levels_out, uint64_t* scanned_out, void* stream)
+{
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (n_vertices == 0 || n_vertices >= 0xFFFFFFFFull || source >= n_vertices) return PG_EINVAL;
+    if (!d_row_ptr || !d_col || !d_dist || !d_ws || !aligned(d_ws, 256)) return PG_EINVAL;
+    if (ws_bytes < pg_bfs_workspace_size(n_vertices)) return PG_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t fbytes = ((size_t)n_vertices * 4 + 255) & ~(size_t)255;
+    unsigned char* ws = (unsigned char*)d_ws;
+    uint32_t* fr[2] = {(uint32_t*)ws, (uint32_t*)(ws + fbytes)};
+    uint32_t* nsize = (uint32_t*)(ws + 2 * fbytes);
+    unsigned long long* scanned = (unsigned long long*)(ws + 2 * fbytes + 8);
+    if (cudaMemsetAsync(d_dist, 0xFF, n_vertices * 4, s) != cudaSuccess) return PG_ECUDA;
+    if (cudaMemsetAsync(ws + 2 * fbytes, 0, 256, s) != cudaSuccess) return PG_ECUDA;
+    bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, fr[0], (uint32_t)source);
+    uint32_t fsize = 1, level = 0, cur = 0;
+    TraceScope trace("bfs", s);
+    while (fsize > 0) {
+        if (cudaMemsetAsync(nsize, 0, 4, s) != cudaSuccess) return PG_ECUDA;
+        const int grid = grid_cap((uint64_t)fsize * 32);
+        if (w == PG_ID64)
+            bfs_level_kernel<uint64_t><<<grid, 256, 0, s>>>(d_row_ptr, (const uint64_t*)d_col,
+                                                            fr[cur], fsize, fr[cur ^ 1], nsize,
+                                                            d_dist, level, n_vertices, scanned);
+        else
+            bfs_level_kernel<uint32_t><<<grid, 256, 0, s>>>(d_row_ptr, (const uint32_t*)d_col,
+                                                            fr[cur], fsize, fr[cur ^ 1], nsize,
+                                                            d_dist, level, n_vertices, scanned);
+        if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
+        // the next frontier's size decides whether another level runs
+        if (cudaMemcpyAsync(&fsize, nsize, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return PG_ECUDA;
+        cur ^= 1;
+        ++level;
+    }
+    uint64_t sc = 0;
+    if (cudaMemcpyAsync(&sc, scanned, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PG_ECUDA;
+    if (levels_out) *levels_out = level;
+    if (scanned_out) *scanned_out = sc;
+    return PG_OK;
+}
+
+}  // extern "C"

@@ -40,6 +40,10 @@ CONFIGS = {
     # 2^20 cells, then CSR keeping the cells of odd multiplicity
     "kron_k20_m16x_xor": dict(kind="kron_xor", initiator=KRON_INITIATOR, k=20,
                               n_edges=16 * 2**20, n_random=2**20, seed=7),
+    # graph check: breadth-first search over the undirected CSR of a PBA graph
+    # (2^24 new vertices in 64 blocks, m = 5) from 8 fixed sources
+    "bfs_pba_n2p24_b64": dict(kind="bfs", n=2**24, m=5, blocks=64, n0=6, faction_width=1,
+                              inter_frac=0.1, seed=3, sources=8),
     # 4096 independent graphs of uneven sizes in one persistent launch
     "batch_4096_mixed": dict(kind="batch", n_jobs=4096, seed=0),
     # served requests: Poisson arrivals at 2000/s, half BA / half Kronecker,

@@ -465,3 +465,57 @@ def test_csr_of_gpu_ba_output_is_canonical():
     ref_rp, ref_col = o.csr(o.ba(n, m, n0, seed), n0 + n)
     assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp)
     assert_same(host(col), ref_col)
+
+
+# --------------------------------------------------------------------------
+# Graph properties on the GPU: degrees, histogram, BFS
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+@pytest.mark.parametrize("id64", [False, True])
+def test_degrees_and_histogram_match_oracle(which, id64):
+    e, _, _ = o.pba(16 * 3000, 4, 16, 5, 2, 0.2, 4)
+    N = 16 * (5 + 3000)
+    e = e.astype(np.uint64 if id64 else np.uint32)
+    t = torch.from_numpy(e.view(np.int64 if id64 else np.int32)).cuda()
+    deg = pg.degrees(t, N, which)
+    h_small = pg.degree_histogram(deg, 50)          # shared-memory buckets
+    h_big = pg.degree_histogram(deg, 20_000)        # global buckets
+    torch.cuda.synchronize()
+    ref = o.degrees(e.astype(np.uint64), N, which)
+    assert np.array_equal(deg.cpu().numpy().view(np.uint64), ref)
+    assert np.array_equal(h_small.cpu().numpy().view(np.uint64), o.degree_histogram(ref, 50))
+    assert np.array_equal(h_big.cpu().numpy().view(np.uint64), o.degree_histogram(ref, 20_000))
+
+
+def _bfs_case(name):
+    if name == "pba_undirected":
+        e, _, _ = o.pba(8 * 4000, 3, 8, 4, 1, 0.1, 9)
+        return e, 8 * 4004, o.CSR_SYMMETRIZE, [0, 5, 8 * 4004 - 1]
+    if name == "kron_directed":
+        return o.kron(W.KRON_INITIATOR, 14, 60_000, 3), 2**14, 0, [0, 1, 12345]
+    if name == "path":
+        n = 3000                                  # 3000 levels
+        e = np.stack([np.arange(n - 1), np.arange(1, n)], 1).astype(np.uint64)
+        return e, n, o.CSR_SYMMETRIZE, [0, 1500]
+    if name == "single":
+        return np.zeros((0, 2), np.uint64), 1, 0, [0]
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["pba_undirected", "kron_directed", "path", "single"])
+@pytest.mark.parametrize("id64", [False, True])
+def test_bfs_matches_oracle(name, id64):
+    e, N, flags, sources = _bfs_case(name)
+    ref_rp, ref_col = o.csr_opts(e, N, flags)
+    rp = torch.from_numpy(ref_rp.view(np.int64)).cuda()
+    col = torch.from_numpy(ref_col.astype(np.uint64 if id64 else np.uint32)
+                           .view(np.int64 if id64 else np.int32)).cuda()
+    if col.numel() == 0:
+        col = torch.zeros(1, dtype=col.dtype, device="cuda")
+    for s in sources:
+        dist, levels, scanned = pg.bfs(rp, col, s)
+        torch.cuda.synchronize()
+        rd, rl, rs = o.bfs(ref_rp, ref_col, s)
+        assert np.array_equal(dist.cpu().numpy().view(np.uint32), rd), (name, s)
+        assert (levels, scanned) == (rl, rs), (name, s)

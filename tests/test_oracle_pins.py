@@ -623,3 +623,54 @@ def test_random_cells_uniform():
         obs = np.bincount(cells[:, axis], minlength=N)
         assert stats.chisquare(obs).pvalue > 1e-4
     assert stats.chisquare(np.bincount(cells[:, 0] * N + cells[:, 1], minlength=N * N)).pvalue > 1e-4
+
+
+# --------------------------------------------------------------------------
+# Graph properties: degrees, histogram, BFS distances (Sec. 4's checks)
+# --------------------------------------------------------------------------
+
+def test_degrees_and_histogram_equal_bincount():
+    rng = np.random.default_rng(12)
+    N = 400
+    e = rng.integers(0, N, size=(5000, 2), dtype=np.uint64)
+    e[::7, 1] = e[::7, 0]
+    for which, cols in ((o.DEG_OUT, [0]), (o.DEG_IN, [1]), (o.DEG_TOTAL, [0, 1])):
+        deg = o.degrees(e, N, which)
+        want = sum(np.bincount(e[:, c].astype(np.int64), minlength=N) for c in cols)
+        assert np.array_equal(deg, want.astype(np.uint64))
+        for max_deg in (5, 40, 10**4):
+            h = o.degree_histogram(deg, max_deg)
+            clamped = np.minimum(deg, max_deg + 1).astype(np.int64)
+            assert np.array_equal(h, np.bincount(clamped, minlength=max_deg + 2).astype(np.uint64))
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_bfs_equals_networkx_shortest_paths(symmetric):
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(5 + symmetric)
+    N = 300
+    e = rng.integers(0, N, size=(700, 2), dtype=np.uint64)
+    flags = o.CSR_SYMMETRIZE if symmetric else 0
+    rp, col = o.csr_opts(e, N, flags)
+    G = nx.DiGraph()
+    G.add_nodes_from(range(N))
+    src = np.repeat(np.arange(N), np.diff(rp).astype(np.int64))
+    G.add_edges_from(zip(src.tolist(), col.tolist()))
+    for s in (0, 17, 299):
+        dist, levels, scanned = o.bfs(rp, col, s)
+        want = nx.single_source_shortest_path_length(G, s)
+        got = {v: int(d) for v, d in enumerate(dist) if d != 0xFFFFFFFF}
+        assert got == want
+        assert levels == max(want.values()) + 1
+        assert scanned == int(sum(rp[v + 1] - rp[v] for v in want))
+
+
+def test_powerlaw_exponent_of_ba_is_three():
+    """The BA model's degree law P(k) ~ k^-3 (Bollobas-Riordan): the discrete
+    estimator on a 10^6-vertex oracle graph must recover an exponent near 3."""
+    import paper_1003_3684_gb300 as pg
+    e = o.ba(10**6, 4, 5, seed=3)
+    deg = o.degrees(e, 10**6 + 5, o.DEG_TOTAL)
+    h = o.degree_histogram(deg, 5000)
+    gamma = pg.powerlaw_exponent(h, 12)
+    assert 2.8 < gamma < 3.2, gamma
