@@ -104,6 +104,29 @@ def load_peaks():
 
 
 # --------------------------------------------------------------------------
+# several GPUs: independent replicas (no collective on the data path)
+# --------------------------------------------------------------------------
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Rank r generates its own instance of the workload, seeded base + r."""
+    return base_seed + rank
+
+
+def max_over_ranks(value: float, device, world: int) -> float:
+    """The largest value over the ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Units of the whole job per second: every rank's units over the slowest time."""
+    return units_per_rank_step * steps * world / (ms_max / 1000.0)
+
+
+# --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
@@ -559,7 +582,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
         # a smaller case of the same workload: fewer blocks of the same size
         cfg["n"] = cfg["n"] // cfg["blocks"] * args.blocks
         cfg["blocks"] = args.blocks
-    seed = cfg["seed"] + rank
+    seed = replica_seed(cfg["seed"], rank)
     stream = torch.cuda.current_stream()
     kind = cfg["kind"]
 
@@ -710,11 +733,8 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     pg.pg_trace_enable(False)
     kernels = pg.pg_trace_dump()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = E * args.steps * world / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, dev, world)
+    value = job_throughput(E, args.steps, world, ms_max)
     launches = sum(v[0] for v in kernels.values())
 
     # roofline of the dominant kernel
