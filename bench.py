@@ -451,8 +451,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                          unit="GB/s", frac=total * 8 / waves / per_launch / (peaks["hbm_gbs"] * 1e9)),
                 ms_per_launch=per_launch * 1000.0,
                 peak_source=f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz")
-    metric, unit = ("scanned_entries/sec", "entries/s") if kind == "bfs" else ("edges/sec", "edges/s")
-    line = dict(metric=metric, value=value, unit=unit, n_gpus=world, steps=args.steps,
+    line = dict(metric="edges/sec", value=value, unit="edges/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
                 config=dict(workload=args.workload, n_jobs=len(jobs), edges_per_step=total,
@@ -783,7 +782,9 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
         roof["step_bound_ms"] = 1000.0 * max(step_alu, step_hbm)
         roof["step_frac"] = roof["step_bound_ms"] / (ms_max / args.steps)
 
-    line = dict(metric="edges/sec", value=value, unit="edges/s", n_gpus=world,
+    metric, unit = (("scanned_entries/sec", "entries/s") if kind == "bfs"
+                    else ("edges/sec", "edges/s"))
+    line = dict(metric=metric, value=value, unit=unit, n_gpus=world,
                 steps=args.steps, warmup=args.warmup, ms_per_step=ms_max / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u32",
                 data="synthetic", config=cfg_json, roofline=roof, gpu_launches=launches,
