@@ -64,32 +64,44 @@ struct SortShape {
     static constexpr uint32_t tile = kSortThreads * items;
 };
 
+// Per-tile digit counts. Each warp counts into its own shared-memory
+// histogram with plain atomic increments (no cross-warp contention; a skewed
+// digit only meets the other lanes of its warp), then the warps' counts are
+// summed per digit. Dynamic shared memory: kSortWarps << bits counters.
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(
     const typename PairOf<Id>::T* __restrict__ in, uint64_t M, int field, int shift, int bits,
     uint32_t* __restrict__ H, uint32_t n_tiles, const uint32_t* __restrict__ sort_needed)
 {
-    __shared__ uint32_t h[kMaxBuckets];
+    extern __shared__ uint32_t wh[];
     if (*sort_needed == 0) return;
     const uint32_t nb = 1u << bits, mask = nb - 1;
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) h[d] = 0;
+    const uint32_t wid = threadIdx.x >> 5;
+    for (uint32_t t = threadIdx.x; t < kSortWarps * nb; t += blockDim.x) wh[t] = 0;
     __syncthreads();
     constexpr uint32_t kTile = SortShape<Id>::tile;
     const uint64_t base = (uint64_t)blockIdx.x * kTile;
     const uint64_t end = (base + kTile < M) ? base + kTile : M;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (uint64_t i0 = base + (threadIdx.x & ~31u); i0 < end; i0 += blockDim.x) {
-        const uint64_t i = i0 + lane;
-        const uint32_t d = (i < end) ? digit_of(in[i], field, shift, mask) : 0xFFFFFFFFu;
-        // one shared-memory atomic per distinct digit of the warp (skewed
-        // digits -- hubs -- would otherwise serialise on one counter)
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        if (d != 0xFFFFFFFFu && (peers & lt) == 0) atomicAdd(&h[d], __popc(peers));
+    uint32_t* mine = wh + wid * nb;
+    constexpr int kUnroll = 4;
+    for (uint64_t i0 = base + threadIdx.x; i0 < end; i0 += (uint64_t)kUnroll * blockDim.x) {
+        uint32_t d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+            d[u] = (i < end) ? digit_of(in[i], field, shift, mask) : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (d[u] != 0xFFFFFFFFu) atomicAdd(&mine[d[u]], 1u);
     }
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x)
-        H[(uint64_t)d * n_tiles + blockIdx.x] = h[d];
+    for (uint32_t dd = threadIdx.x; dd < nb; dd += blockDim.x) {
+        uint32_t sum = 0;
+#pragma unroll 4
+        for (int w = 0; w < kSortWarps; ++w) sum += wh[w * nb + dd];
+        H[(uint64_t)dd * n_tiles + blockIdx.x] = sum;
+    }
 }
 
 // One LSD pass over a tile: load once, rank stably (per warp by match, then
@@ -614,6 +626,8 @@ void set_csr_attributes()
     if (!attr) {
         cudaFuncSetAttribute(radix_scatter_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scatter_smem_bytes<Id>());
+        cudaFuncSetAttribute(radix_hist_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSortWarps * 4 * kMaxBuckets));
         attr = true;
     }
 }
@@ -647,7 +661,8 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
                 const uint64_t nh = ((uint64_t)1 << b) * L.n_tiles;
                 {
                     TraceScope trace("csr_radix_hist", s);
-                    radix_hist_kernel<Id><<<L.n_tiles, kSortThreads, 0, s>>>(
+                    radix_hist_kernel<Id><<<L.n_tiles, kSortThreads,
+                                            (size_t)kSortWarps * 4 << b, s>>>(
                         cur, M, field, shift, b, H, L.n_tiles, sort_needed);
                 }
                 const uint64_t n_parts = (nh + kScanTile - 1) / kScanTile;

@@ -53,16 +53,56 @@ struct Pair2<uint64_t> {
 };
 
 // ---- stochastic descent, initiator order 2 (branch-free 3-threshold pick) --
+// T is uint32_t when k <= 32 (ids fit 32 bits), else uint64_t.
+template <typename T>
 __device__ __forceinline__ void descend2(uint32_t w, uint32_t u0, uint32_t u1, uint32_t u2,
-                                         uint32_t base, uint64_t& row, uint64_t& col)
+                                         uint32_t base, T& row, T& col)
 {
     const uint32_t cell = base + (w > u0) + (w > u1) + (w > u2);
-    row = (row << 1) | (cell >> 1);
-    col = (col << 1) | (cell & 1);
+    row = (row << 1) | (T)(cell >> 1);
+    col = (col << 1) | (T)(cell & 1);
 }
 
+// The same pick when cell 0 has positive weight and all three thresholds
+// are real (n_zero = 0, n_u = 3): with u0 <= u1 <= u2 the row bit of the
+// cell is (w > u1) and the column bit the parity of the three compares;
+// row = 2*row + a runs on the multiply-add pipe rather than the ALU pipe.
+template <typename T>
+__device__ __forceinline__ void descend2_full(uint32_t w, uint32_t u0, uint32_t u1, uint32_t u2,
+                                              T& row, T& col)
+{
+    const uint32_t a = w > u1 ? 1u : 0u;
+    const uint32_t b = (w > u0 ? 1u : 0u) ^ a ^ (w > u2 ? 1u : 0u);
+    row = row * 2 + (T)a;
+    col = col * 2 + (T)b;
+}
+
+template <typename T>
+__device__ __forceinline__ void kron2_edge_full(const KronParams& p, uint64_t e, uint32_t u0,
+                                                uint32_t u1, uint32_t u2, T& row, T& col)
+{
+    row = 0;
+    col = 0;
+    const uint32_t k = p.k;
+    uint32_t l = 0;
+    for (uint32_t g = 0; l + 4 <= k; ++g, l += 4) {
+        const uint4 w = draw(e, g, 3, p.key);
+        descend2_full(w.x, u0, u1, u2, row, col);
+        descend2_full(w.y, u0, u1, u2, row, col);
+        descend2_full(w.z, u0, u1, u2, row, col);
+        descend2_full(w.w, u0, u1, u2, row, col);
+    }
+    if (l < k) {
+        const uint4 w = draw(e, l >> 2, 3, p.key);
+        descend2_full(w.x, u0, u1, u2, row, col);
+        if (l + 1 < k) descend2_full(w.y, u0, u1, u2, row, col);
+        if (l + 2 < k) descend2_full(w.z, u0, u1, u2, row, col);
+    }
+}
+
+template <typename T>
 __device__ __forceinline__ void kron2_edge(const KronParams& p, uint64_t e, uint32_t u0,
-                                           uint32_t u1, uint32_t u2, uint64_t& row, uint64_t& col)
+                                           uint32_t u1, uint32_t u2, T& row, T& col)
 {
     row = 0;
     col = 0;
@@ -83,7 +123,7 @@ __device__ __forceinline__ void kron2_edge(const KronParams& p, uint64_t e, uint
     }
 }
 
-template <typename Id>
+template <typename Id, typename T, bool kFull>
 __global__ void __launch_bounds__(256) kron2_kernel(const __grid_constant__ KronParams p,
                                                     Id* __restrict__ out, uint64_t e_begin,
                                                     uint64_t n_edges)
@@ -91,13 +131,17 @@ __global__ void __launch_bounds__(256) kron2_kernel(const __grid_constant__ Kron
     const uint32_t u0 = p.u[0], u1 = p.u[1], u2 = p.u[2];   // padded to three
     const uint64_t n_pairs = (n_edges + 1) >> 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    auto edge = [&](uint64_t ee, T& r, T& c) {
+        if constexpr (kFull) kron2_edge_full(p, ee, u0, u1, u2, r, c);
+        else kron2_edge(p, ee, u0, u1, u2, r, c);
+    };
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
         const uint64_t e = 2 * t;
-        uint64_t r0, c0;
-        kron2_edge(p, e_begin + e, u0, u1, u2, r0, c0);
+        T r0, c0;
+        edge(e_begin + e, r0, c0);
         if (e + 1 < n_edges) {
-            uint64_t r1, c1;
-            kron2_edge(p, e_begin + e + 1, u0, u1, u2, r1, c1);
+            T r1, c1;
+            edge(e_begin + e + 1, r1, c1);
             Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
             Pair2<Id>::store1(out, e, r0, c0);
@@ -241,11 +285,16 @@ cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, u
     const uint64_t pairs = (n_edges + 1) / 2;
     TraceScope trace(p.n0 == 2 ? "kron_descent_n0_2" : "kron_descent", s);
     if (p.n0 == 2) {
-        if (id64) {
-            auto k = kron2_kernel<uint64_t>;
+        // 32-bit descent state when every id fits (k <= 32)
+        const bool full = p.n_zero == 0 && p.n_u == 3;
+        if (id64 && p.k > 32) {
+            auto k = full ? kron2_kernel<uint64_t, uint64_t, true> : kron2_kernel<uint64_t, uint64_t, false>;
+            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+        } else if (id64) {
+            auto k = full ? kron2_kernel<uint64_t, uint32_t, true> : kron2_kernel<uint64_t, uint32_t, false>;
             k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
         } else {
-            auto k = kron2_kernel<uint32_t>;
+            auto k = full ? kron2_kernel<uint32_t, uint32_t, true> : kron2_kernel<uint32_t, uint32_t, false>;
             k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
         }
     } else {
