@@ -110,12 +110,35 @@ __device__ __forceinline__ void kron_level(uint32_t w, uint32_t base, uint32_t u
     col = (col << 1) | (cell & 1);
 }
 
+// The same pick for a 2x2 initiator whose four cells are all positive
+// (n_zero = 0, three real thresholds u0 <= u1 <= u2): the row bit is
+// (w > u1), the column bit the parity of the three compares.
+__device__ __forceinline__ void kron_level_full(uint32_t w, uint32_t u0, uint32_t u1, uint32_t u2,
+                                                uint64_t& row, uint64_t& col)
+{
+    const uint32_t a = w > u1 ? 1u : 0u;
+    const uint32_t b = (w > u0 ? 1u : 0u) ^ a ^ (w > u2 ? 1u : 0u);
+    row = row * 2 + a;
+    col = col * 2 + b;
+}
+
 __device__ __forceinline__ void kron_edge(const BatchJob& J, const Key& key,
                                           const uint32_t* pool, uint64_t e, uint64_t& row,
                                           uint64_t& col)
 {
     row = 0;
     col = 0;
+    if (J.n0 == 2 && J.n_zero == 0 && J.n_u == 3) {
+        uint32_t l = 0;
+        for (uint32_t g = 0; l < J.k; ++g, l += 4) {
+            const uint4 w = philox(make_uint4((uint32_t)e, (uint32_t)(e >> 32), g, 3u), key);
+            kron_level_full(w.x, J.u0, J.u1, J.u2, row, col);
+            if (l + 1 < J.k) kron_level_full(w.y, J.u0, J.u1, J.u2, row, col);
+            if (l + 2 < J.k) kron_level_full(w.z, J.u0, J.u1, J.u2, row, col);
+            if (l + 3 < J.k) kron_level_full(w.w, J.u0, J.u1, J.u2, row, col);
+        }
+        return;
+    }
     if (J.n0 == 2) {
         uint32_t l = 0;
         for (uint32_t g = 0; l < J.k; ++g, l += 4) {
