@@ -6,14 +6,20 @@
  * Graphs" (arXiv 1003.3684): the parallel Barabasi-Albert method with
  * two-phase preferential attachment (Sec. 3, PBA method, Fig. 1) and the
  * Kronecker method (Sec. 3, PK method, Fig. 2; stochastic initiator of the
- * Kronecker model cited in Sec. 2), plus CSR assembly and batched launch.
+ * Kronecker model cited in Sec. 2, and its randomisation by exclusive-or with
+ * a random graph), with general faction lists and generation in parts; plus
+ * CSR assembly, batched launch and the graph checks of Sec. 4 (degrees,
+ * degree histogram, breadth-first distances).
  *
  * Conventions shared by every entry point:
  *  - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
  *    are host pointers. The caller owns every buffer; the library allocates
- *    no device memory (scratch comes from the caller's workspace d_ws).
+ *    no device memory (scratch comes from the caller's workspace d_ws; the
+ *    one exception, gen_pba_noalloc, uses a fixed array compiled into the
+ *    library).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream). Calls only enqueue work; none synchronises the stream. Outputs
+ *    stream). Calls only enqueue work and do not synchronise the stream,
+ *    except pg_bfs, which waits once per search level (see there). Outputs
  *    written through h_* pointers are computed from the arguments on the
  *    host before any launch and are valid on return.
  *  - Arguments are validated on the host before anything is launched; an

@@ -208,13 +208,9 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     uint32_t own = 0;   // entries equal to p (the most frequent value) counted here
     while (__any_sync(0xFFFFFFFFu, active || pend)) {
         // every lane draws (an idle lane's draw is discarded), so the trip is
-        // straight-line code apart from the deferred store and count
+        // straight-line code apart from the deferred store
         const uint4 w = philox(make_uint4(cur, 0u, p, 1u), g.key);
-        if (pend) {   // the value loaded one trip ago
-            my[pend_k] = (uint16_t)pend_v;
-            if (pend_v != p) atomicAdd(&hist[pend_v], 1u);
-        }
-        own += (pend && pend_v == p) ? 1u : 0u;
+        if (pend) my[pend_k] = (uint16_t)pend_v;   // the value loaded one trip ago
         const bool coin = coin_on && w.z < g.coin_thr;
         const uint32_t r = uniform32(w.x, w.y, cur);
         const bool hit = !coin && r < L;
@@ -241,6 +237,12 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
         next += __popc(dm);
     }
     __syncwarp();
+    // counts of the finished run, outside the pooled loop (converged lanes)
+    for (uint32_t t = lane; t < n_items; t += 32) {
+        const uint32_t v = my[t];
+        if (v == p) ++own;
+        else atomicAdd(&hist[v], 1u);
+    }
     // the run back to A: 16-byte stores when the run is whole (run is a
     // multiple of 8 entries and rows are 16-byte aligned)
     if (n_items == kPassRun) {
