@@ -117,6 +117,9 @@ PBA_CASES = [
     (3, 1, 1, 1, 0.2, 2, 1),           # one vertex per block
     (7, 0, 3, 7, 0.1, 4, 1),           # no new vertices: seed cliques only
     (2, 50_000, 1, 1, 0.9, 2, 12345),
+    (16, 2**14, 5, 1, 0.1, 6, 5),      # n_b a power of two: shift instead of division
+    (4, 5_000, 3, 1, 0.2, 40, 8),      # 780 seed edges: long seed-endpoint walks
+    (8, 3_000, 48, 2, 0.25, 49, 21),   # many edges per vertex
 ]
 
 
