@@ -795,6 +795,10 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             roof["alu_measured"] = dict(philox_per_s=rate, peak=meas / 1e12,
                                         unit="Tops/s (int32 lane ops)", frac=ops_rate / meas,
                                         source="pg_philox_probe: Philox4x32-10 calls/s x 60 ops")
+            # per-SM-per-clock rates of the operations Philox is made of
+            clk = peaks["sm_max_mhz"] * 1e6
+            roof["int_pipes_per_sm_clk"] = {
+                k: round(v / sms / clk, 1) for k, v in pg.int_pipe_rates().items()}
         roof["ms_per_launch"] = per_launch_s * 1000.0
         roof["units_per_launch"] = u
         roof["ops_per_unit"] = work[dom]["ops"]

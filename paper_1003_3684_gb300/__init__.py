@@ -30,7 +30,7 @@ __all__ = [
     "pg_status_string", "pg_device_sm_count", "pg_version",
     "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba", "gen_pba_to_host",
     "pba_faction_table", "gen_pba_factions", "pg_pba_prepare", "gen_pba_blocks",
-    "gen_kronecker_range", "philox_rate", "edges_to_csr_opts", "gen_random_cells",
+    "gen_kronecker_range", "philox_rate", "int_pipe_rates", "edges_to_csr_opts", "gen_random_cells",
     "kronecker_xor_random", "CSR_SYMMETRIZE", "CSR_DEDUP", "CSR_NO_LOOPS", "CSR_ODD",
     "DEG_OUT", "DEG_IN", "DEG_TOTAL", "degrees", "degree_histogram", "bfs", "powerlaw_exponent",
     "path_length_stats",
@@ -472,6 +472,36 @@ def path_length_stats(dist) -> dict:
     return dict(reached=int(reached.size) + 1,
                 mean=float(reached.mean()) if reached.size else 0.0,
                 max=int(reached.max()) if reached.size else 0)
+
+
+def int_pipe_rates(iters: int = 1024, device="cuda") -> dict:
+    """Measured operations per second of the device for a 32x32->64 multiply,
+    a 32-bit multiply-add, a three-input XOR and a three-input add (the
+    operations of Philox and the index arithmetic), from the library's probe."""
+    import torch
+    L = lib()
+    if not getattr(L, "_intprobe_ready", False):
+        L.pg_philox_probe_threads.restype = sz
+        L.pg_int_probe.argtypes = [C.c_int, u32, vp, sz, vp]
+        L.pg_int_probe.restype = i32
+        L._intprobe_ready = True
+    n = int(L.pg_philox_probe_threads())
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream(out.device)
+    rates = {}
+    for op, name in enumerate(("mul_wide", "mad32", "xor3", "add3")):
+        best = None
+        for i in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _check("pg_int_probe", L.pg_int_probe(op, iters, _ptr(out), n, vp(stream.cuda_stream)))
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            if i > 0 and (best is None or ms < best):
+                best = ms
+        rates[name] = n * 8 * iters / (best / 1000.0)
+    return rates
 
 
 def pg_csr_workspace_size(n_edges: int, n_vertices: int) -> int:

@@ -539,3 +539,11 @@ def test_bfs_matches_oracle(name, id64):
         rd, rl, rs = o.bfs(ref_rp, ref_col, s)
         assert np.array_equal(dist.cpu().numpy().view(np.uint32), rd), (name, s)
         assert (levels, scanned) == (rl, rs), (name, s)
+
+
+def test_throughput_probes_run():
+    """The probes behind the bench's measured integer ceilings launch and give rates."""
+    r = pg.philox_rate(calls_per_thread=256, reps=1)
+    pipes = pg.int_pipe_rates(iters=256)
+    assert r > 1e10
+    assert set(pipes) == {"mul_wide", "mad32", "xor3", "add3"} and min(pipes.values()) > 1e11
