@@ -827,7 +827,10 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     if not args.no_e2e and kind != "bfs":
         if kind == "pba" and cfg.get("parts", 1) > 1:
             line["e2e"] = measure_e2e_parts(args, cfg, seed, out, ws, E, dev, world)
-        elif kind == "pba" and not cfg.get("factions"):
+        elif kind == "pba" and not cfg.get("factions") and world == 1:
+            # one rank: a pinned host buffer of the whole graph, copies
+            # overlapped with generation; with several ranks on one host the
+            # copies go through a 4 GB pinned buffer per rank instead
             line["e2e"] = measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world)
         else:
             line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)

@@ -74,7 +74,7 @@ pg_status pg_philox_probe(uint32_t calls_per_thread, uint32_t* d_out, size_t out
                           void* stream);
 /* Integer pipe probe: same launch shape; each thread runs 8 independent
  * chains of `iters` operations of one kind (op 0: 32x32->64 multiply, 1:
- * 32-bit multiply-add, 2: three-input XOR, 3: three-input add), so
+ * 32-bit multiply-add, 2: three-input logic x ^ (y & z), 3: three-input add), so
  * threads * 8 * iters / seconds is the device's rate for that operation. */
 pg_status pg_int_probe(int op, uint32_t iters, uint32_t* d_out, size_t out_words, void* stream);
 

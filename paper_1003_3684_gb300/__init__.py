@@ -476,7 +476,7 @@ def path_length_stats(dist) -> dict:
 
 def int_pipe_rates(iters: int = 1024, device="cuda") -> dict:
     """Measured operations per second of the device for a 32x32->64 multiply,
-    a 32-bit multiply-add, a three-input XOR and a three-input add (the
+    a 32-bit multiply-add, a three-input logic operation and a three-input add (the
     operations of Philox and the index arithmetic), from the library's probe."""
     import torch
     L = lib()
@@ -489,7 +489,7 @@ def int_pipe_rates(iters: int = 1024, device="cuda") -> dict:
     out = torch.empty(n, dtype=torch.int32, device=device)
     stream = torch.cuda.current_stream(out.device)
     rates = {}
-    for op, name in enumerate(("mul_wide", "mad32", "xor3", "add3")):
+    for op, name in enumerate(("mul_wide", "mad32", "lop3", "add3")):
         best = None
         for i in range(3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -51,7 +51,6 @@ constexpr int kEmitWarps = 8;
 constexpr int kEmitThreads = kEmitWarps * 32;
 constexpr int kEmitItems = 16;
 constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 512 entries per warp run
-constexpr bool kEmitDual = false;   // two chains per lane in the emit loop
 constexpr uint32_t kMaxBlocks = 1024;
 constexpr int kBaThreads = 256;
 template <typename Id>
@@ -374,75 +373,11 @@ __device__ __forceinline__ bool t_step(uint64_t& cur, uint32_t q, const QDiv& qd
     return false;
 }
 
-// The draw of one 32-bit link: e = r >> 1 and side = r & 1 for the slot
-// drawn by entry `cur` of T_q (no branches, so two of these interleave).
-__device__ __forceinline__ void t_draw32(uint32_t cur, uint32_t q, const QRecip& c,
-                                         const PbaGeom& g, uint32_t& e, uint32_t& side)
-{
-    const uint32_t nb = (uint32_t)g.n_b;
-    const uint32_t sig = sigma32(cur, c);
-    uint32_t before;
-    if (g.nb_shift != 0xFFFFFFFFu)
-        before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
-    else
-        before = (uint32_t)fdiv((uint64_t)sig * c.R + (nb - 1), g.div_nb);
-    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
-    const uint32_t X = (uint32_t)g.e0 + before;
-    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
-    e = (uint32_t)(s >> 32);
-    side = ((uint32_t)s) >> 31;
-}
-
-// Resolution of a drawn link: true with v when the chain ends here.
-__device__ __forceinline__ bool t_resolve32(uint32_t e, uint32_t side, uint32_t& cur,
-                                            const QRecip& c, const PbaGeom& g, uint32_t& v)
-{
-    if (e < (uint32_t)g.e0) {
-        v = seed_endpoint(e, side, g.n0);
-        return true;
-    }
-    const uint32_t e2 = e - (uint32_t)g.e0;
-    if (side == 0) {
-        v = g.n0 + sigma32(e2, c);
-        return true;
-    }
-    cur = e2;
-    return false;
-}
-
-// 32-bit link (R_q + e0 < 2^32): the same values as t_step.
-__device__ __forceinline__ bool t_step32(uint32_t& cur, uint32_t q, const QRecip& c,
-                                         const PbaGeom& g, uint32_t& v)
-{
-    const uint32_t nb = (uint32_t)g.n_b;
-    const uint32_t sig = sigma32(cur, c);
-    uint32_t before;
-    if (g.nb_shift != 0xFFFFFFFFu)
-        before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
-    else
-        before = (uint32_t)fdiv((uint64_t)sig * c.R + (nb - 1), g.div_nb);
-    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
-    // r = floor(W * 2X / 2^64) with W = (w1:w0), X = e0 + before < 2^32:
-    // e = r >> 1 is the high word of s = w1*X + (w0*X >> 32), side = bit 31
-    const uint32_t X = (uint32_t)g.e0 + before;
-    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
-    const uint32_t e = (uint32_t)(s >> 32);
-    const uint32_t side = ((uint32_t)s) >> 31;
-    if (e < (uint32_t)g.e0) {
-        v = seed_endpoint(e, side, g.n0);
-        return true;
-    }
-    const uint32_t e2 = e - (uint32_t)g.e0;
-    if (side == 0) {
-        v = g.n0 + sigma32(e2, c);
-        return true;
-    }
-    cur = e2;
-    return false;
-}
-
-// The same link with one rarely taken branch (a seed slot): the side-0 value
-// is computed on every link and selected, so lanes of a warp that stop and
+// 32-bit link (R_q + e0 < 2^32), the same values as t_step: with W = (w1:w0)
+// and X = e0 + before < 2^32, the slot r = floor(W * 2X / 2^64) has
+// e = r >> 1 = the high word of s = w1*X + (w0*X >> 32) and side = bit 31 of
+// s's low word. One rarely taken branch (a seed slot): the side-0 value is
+// computed on every link and selected, so lanes of a warp that stop and
 // lanes that continue run the same instructions.
 __device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip& c,
                                          const PbaGeom& g, uint32_t& v)
@@ -610,58 +545,6 @@ struct EmitWarpSmem {
     uint16_t qs[kEmitRun];     // target block of each entry of the run
 };
 
-// Two chains per lane (slots a and b: 64 virtual lanes per warp). Both
-// links of a trip are drawn before either is resolved, so their Philox
-// rounds interleave; claims go to slot a's finishers first, then slot b's.
-template <typename CurT>
-__device__ __forceinline__ void emit_chains_dual(EmitWarpSmem<CurT>& ws, const PbaGeom& g,
-                                                 const QRecip* __restrict__ recip, uint32_t lane)
-{
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t ka = lane, kb = 32 + lane, next = 64;
-    bool acta = true, actb = true, fra = true, frb = true;
-    uint32_t qa = 0xFFFFu, qb = 0xFFFFu, cura = 0, curb = 0;
-    QRecip ca{0, 0, 0, 0}, cb{0, 0, 0, 0};
-    while (__any_sync(0xFFFFFFFFu, acta || actb)) {
-        if (acta && fra) {
-            qa = ws.qs[ka];
-            cura = (uint32_t)ws.item[ka];
-            if (qa != 0xFFFFu) ca = recip[qa];
-            fra = false;
-        }
-        if (actb && frb) {
-            qb = ws.qs[kb];
-            curb = (uint32_t)ws.item[kb];
-            if (qb != 0xFFFFu) cb = recip[qb];
-            frb = false;
-        }
-        __syncwarp();
-        const bool la = acta && qa != 0xFFFFu, lb = actb && qb != 0xFFFFu;
-        uint32_t ea, sa, eb, sb;
-        t_draw32(cura, qa, ca, g, ea, sa);
-        t_draw32(curb, qb, cb, g, eb, sb);
-        uint32_t va = 0, vb = 0;
-        const bool fa = la && t_resolve32(ea, sa, cura, ca, g, va);
-        const bool fb = lb && t_resolve32(eb, sb, curb, cb, g, vb);
-        if (fa) ws.item[ka] = va;
-        if (fb) ws.item[kb] = vb;
-        const bool da = acta && (fa || !la), db = actb && (fb || !lb);
-        const uint32_t ma = __ballot_sync(0xFFFFFFFFu, da);
-        const uint32_t mb = __ballot_sync(0xFFFFFFFFu, db);
-        if (da) {
-            ka = next + __popc(ma & lt);
-            acta = ka < kEmitRun;
-            fra = true;
-        }
-        if (db) {
-            kb = next + __popc(ma) + __popc(mb & lt);
-            actb = kb < kEmitRun;
-            frb = true;
-        }
-        next += __popc(ma) + __popc(mb);
-    }
-}
-
 template <typename Id, bool kFast>
 __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const __grid_constant__ PbaGeom g, const uint16_t* __restrict__ A,
@@ -729,9 +612,7 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
         // The loop body is kept straight-line -- load the new entry, reconverge,
         // then ONE link for every lane -- so a warp whose lanes are at
         // different depths still runs the link code once per trip.
-        if constexpr (kFast && kEmitDual) {
-            emit_chains_dual(ws, g, recip, lane);
-        } else if constexpr (kFast) {
+        if constexpr (kFast) {
             // items [0, n); a lane that finishes an entry stores its value and
             // claims the next unclaimed item (claims are in lane order)
             uint32_t k = lane, next = 32, q = 0, cur = 0;
@@ -762,7 +643,6 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             uint32_t k = lane, next = 32, q = 0xFFFFu;
             bool active = true, fresh = true;
             CurT cur = 0;
-            QRecip c{0, 0, 0, 0};
             QDiv qd;
             qd.R = 0;
             qd.d = FastDiv{0, 0, 0};
@@ -771,12 +651,8 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                     q = ws.qs[k];
                     cur = ws.item[k];
                     if (q != 0xFFFFu) {
-                        if (kFast) {
-                            c = recip[q];
-                        } else {
-                            qd.R = R[q];
-                            qd.d = divR[q];
-                        }
+                        qd.R = R[q];
+                        qd.d = divR[q];
                     }
                     fresh = false;
                 }
@@ -784,15 +660,9 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                 const bool live = active && q != 0xFFFFu;   // 0xFFFF: past the segment end
                 uint32_t v = 0;
                 bool fin = false;
-                if constexpr (kFast) {
-                    uint32_t c32 = cur;
-                    if (live) fin = t_step32(c32, q, c, g, v);
-                    cur = c32;
-                } else {
-                    uint64_t c64 = cur;
-                    if (live) fin = t_step(c64, q, qd, g, v);
-                    cur = c64;
-                }
+                uint64_t c64 = cur;
+                if (live) fin = t_step(c64, q, qd, g, v);
+                cur = c64;
                 if (fin) ws.item[k] = v;
                 const bool done = active && (fin || !live);
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);

@@ -31,9 +31,10 @@ __global__ void __launch_bounds__(kProbeThreads) philox_probe_kernel(uint32_t* _
 
 // Integer pipe rates: 8 dependency chains per thread, each applying one kind
 // of operation `iters` times (8 independent operations per step); the
-// results are folded into one word so no chain is dead code. op 0: 32x32->64 multiply (the Philox
-// round's product), 1: 32-bit multiply-add, 2: three-input XOR, 3: three-input
-// add.
+// results are folded into one word so no chain is dead code. op 0: 32x32->64
+// multiply (the Philox round's product), 1: 32-bit multiply-add, 2: a
+// three-input logic operation (x ^ (y & z): not linear, so no XOR terms can
+// cancel across steps), 3: three-input add.
 __global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(uint32_t* __restrict__ out,
                                                                   uint32_t iters, int op,
                                                                   uint32_t k0, uint32_t k1)
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(uint32_t* __re
         for (uint32_t i = 0; i < iters; ++i) {
             uint32_t b[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) b[c] = a[c] ^ a[(c + 3) & 7] ^ k0;
+            for (int c = 0; c < 8; ++c) b[c] = a[c] ^ (a[(c + 3) & 7] & a[(c + 5) & 7]);
 #pragma unroll
             for (int c = 0; c < 8; ++c) a[c] = b[c];
         }

@@ -546,4 +546,4 @@ def test_throughput_probes_run():
     r = pg.philox_rate(calls_per_thread=256, reps=1)
     pipes = pg.int_pipe_rates(iters=256)
     assert r > 1e10
-    assert set(pipes) == {"mul_wide", "mad32", "xor3", "add3"} and min(pipes.values()) > 1e11
+    assert set(pipes) == {"mul_wide", "mad32", "lop3", "add3"} and min(pipes.values()) > 1e11
