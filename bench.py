@@ -32,20 +32,17 @@ DEFAULT_WORKLOAD = "pba_n2p30_b1024_m5"
 
 # Algorithmic work per unit (32-bit lane operations and bytes), per kernel.
 # A Philox4x32-10 call is 60 lane ops (10 rounds of two 32x32->64 multiplies,
-# counted as two ops each, and two three-input XORs); a Philox2x32-10 call,
-# the copy draw of phase 2, is 30 (one multiply and one three-input XOR per
-# round); a 64-bit uniform draw adds 4. Chain links recomputed beyond the
-# first draw of a unit are NOT counted: they are the implementation's
-# overhead, not the method's work.
+# counted as two ops each, and two three-input XORs); a 64-bit uniform draw
+# adds 4. Chain links recomputed beyond the first draw of a unit are NOT
+# counted: they are the implementation's overhead, not the method's work.
 PHILOX_OPS = 60
-PHILOX2_OPS = 30
 KERNEL_WORK = {
     # unit = one phase-1 entry: its own draw (coin + uniform index) + select
     "pba_phase1": dict(ops=PHILOX_OPS + 4 + 6, bytes=2),
     # unit = one edge: its endpoint draw + uniform + sigma/E index arithmetic
     # and the rank bookkeeping; bytes = the (src, dst) pair written
-    "pba_emit": dict(ops=PHILOX2_OPS + 4 + 16, bytes=8),
-    "ba_chain": dict(ops=PHILOX2_OPS + 4 + 16, bytes=8),
+    "pba_emit": dict(ops=PHILOX_OPS + 4 + 16, bytes=8),
+    "ba_chain": dict(ops=PHILOX_OPS + 4 + 16, bytes=8),
 }
 
 

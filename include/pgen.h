@@ -31,10 +31,7 @@
  *    16-byte aligned (inputs to edges_to_csr: aligned to one pair).
  *  - Every random draw is Philox4x32-10 (Salmon et al., SC'11) with key
  *    (seed & 0xffffffff, seed >> 32) and a counter that names the draw, so
- *    the output is a pure function of the arguments. The copy draws of the
- *    BA methods (phase 2, and the serial method) take their 64 bits from
- *    Philox2x32-10 of the same paper, keyed by word 0 of the seed's
- *    Philox4x32-10 block at counter (0, 0, 0, 5).
+ *    the output is a pure function of the arguments.
  */
 #ifndef PGEN_H
 #define PGEN_H

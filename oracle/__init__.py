@@ -49,10 +49,6 @@ def lib():
             L = C.CDLL(_LIB)
             L.or_philox4x32_10.argtypes = [P, P, P]
             L.or_philox4x32_10.restype = None
-            L.or_philox2x32_10.argtypes = [P, u32, P]
-            L.or_philox2x32_10.restype = None
-            L.or_link_key.argtypes = [u64]
-            L.or_link_key.restype = u32
             L.or_uniform.argtypes = [u32, u32, u64]
             L.or_uniform.restype = u64
             L.or_coin_threshold.argtypes = [dbl]
@@ -100,18 +96,6 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
-
-
-def philox2x32_10(ctr, key: int) -> np.ndarray:
-    c = np.asarray(ctr, dtype=np.uint32).copy()
-    out = np.zeros(2, dtype=np.uint32)
-    lib().or_philox2x32_10(_ptr(c), int(key) & 0xFFFFFFFF, _ptr(out))
-    return out
-
-
-def link_key(seed: int) -> int:
-    """Key of the copy-draw generator for a seed."""
-    return int(lib().or_link_key(int(seed) & (2**64 - 1)))
 
 
 def uniform(w0: int, w1: int, R: int) -> int:

@@ -34,13 +34,9 @@
  *      faction, with probability f per entry j >= s.
  *  R6  random draws: Philox4x32-10 (Salmon et al., SC'11) with key
  *      (seed_lo, seed_hi) and counter (idx_lo, idx_hi, stream, tag);
- *      tag 1 = phase-1 entry, tag 3 = Kronecker level group, tag 4 =
- *      random cell. The copy draws of phase 2 (local edge i of block q;
- *      the serial method's edge i, q = 0) take 64 bits from Philox2x32-10
- *      (same paper) with counter (i_lo, i_hi + 2^16 * q) and key k2 =
- *      word 0 of the tag-5 draw at index 0, stream 0; this needs
- *      i < 2^48 and q < 2^16. A uniform integer in [0, R) is the high 64
- *      bits of ((w1 << 32) | w0) * R; the coin is w2 < T_f with
+ *      tag 1 = phase-1 entry, tag 2 = phase-2 local edge, tag 3 = Kronecker
+ *      level group. A uniform integer in [0, R) is the high 64 bits of
+ *      ((w1 << 32) | w0) * R; the coin is w2 < T_f with
  *      T_f = min(2^32 - 1, round_half_even(f * 2^32)).
  *  R7  Kronecker: thresholds T_c = round_half_even(2^32 * cum_c / S) where
  *      cum_c is the left-to-right double sum of the initiator's first c+1
@@ -90,44 +86,6 @@ static void draw(uint64_t seed, uint64_t idx, uint32_t stream, uint32_t tag, uin
     or_philox4x32_10(c, k, w);
 }
 
-/* ------------------------------------------------------------------------ */
-/* Philox2x32-10: the same paper's Philox with two words: per round one     */
-/* 32x32->64 multiply of word 0; the high half XORed with word 1 and the    */
-/* round key becomes word 0, the low half becomes word 1; the key is bumped */
-/* by the golden-ratio Weyl constant each round. The tests pin these rounds */
-/* by running them backwards; agreement with the published known answers   */
-/* of the two-word variant is unpinned (none is available offline).        */
-/* ------------------------------------------------------------------------ */
-void or_philox2x32_10(const uint32_t ctr[2], uint32_t key, uint32_t out[2])
-{
-    const uint64_t mult = 0xD256D345u;
-    const uint32_t weyl = 0x9E3779B9u;
-    uint32_t x0 = ctr[0], x1 = ctr[1], k = key;
-    for (int round = 0; round < 10; ++round) {
-        if (round > 0) k += weyl;
-        uint64_t p = mult * (uint64_t)x0;
-        uint32_t y0 = (uint32_t)(p >> 32) ^ x1 ^ k;
-        uint32_t y1 = (uint32_t)p;
-        x0 = y0; x1 = y1;
-    }
-    out[0] = x0; out[1] = x1;
-}
-
-/* Key of the copy-draw generator (R6): word 0 of the tag-5 draw. */
-uint32_t or_link_key(uint64_t seed)
-{
-    uint32_t w[4];
-    draw(seed, 0, 0, 5, w);
-    return w[0];
-}
-
-/* Copy draw for index idx of stream q (R6), under k2 = or_link_key(seed). */
-static void draw_link(uint32_t k2, uint64_t idx, uint32_t q, uint32_t w[2])
-{
-    uint32_t c[2] = {(uint32_t)idx, (uint32_t)(idx >> 32) + (q << 16)};
-    or_philox2x32_10(c, k2, w);
-}
-
 /* Uniform integer in [0, R): high half of the 128-bit product (R6). */
 uint64_t or_uniform(uint32_t w0, uint32_t w1, uint64_t R)
 {
@@ -163,16 +121,14 @@ static void seed_clique(uint32_t n0, uint32_t* ea, uint32_t* eb)
 /* degree-proportional choice done in O(1) by taking a uniform existing     */
 /* edge and then a uniform end of it). An explicit endpoint array M         */
 /* holds both endpoints of every edge made so far; a new edge copies M[r].  */
-/* Copy draws use stream `stream` (R6), so blocks = 1 of the two-phase      */
+/* Draws use stream `stream` of tag 2, so blocks = 1 of the two-phase       */
 /* method (whose only endpoint list is T_0) reproduces it exactly.          */
 /* ------------------------------------------------------------------------ */
 int or_ba(uint64_t n, uint32_t m, uint32_t n0, uint64_t seed, uint32_t stream, uint64_t* out)
 {
-    if (m < 1 || n0 < 2 || stream >= (1u << 16)) return 1;
-    if (n >= ((uint64_t)1 << 48) / m) return 1;   /* copy-draw index < 2^48 (R6) */
+    if (m < 1 || n0 < 2) return 1;
     uint64_t e0 = seed_edge_count(n0);
     uint64_t n_edges = e0 + n * m;
-    uint32_t k2 = or_link_key(seed);
     uint64_t* M = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (n_edges ? n_edges : 1));
     uint32_t* ea = (uint32_t*)malloc(sizeof(uint32_t) * e0);
     uint32_t* eb = (uint32_t*)malloc(sizeof(uint32_t) * e0);
@@ -187,8 +143,8 @@ int or_ba(uint64_t n, uint32_t m, uint32_t n0, uint64_t seed, uint32_t stream, u
         uint64_t slots = 2 * (e0 + i * m);
         for (uint32_t t = 0; t < m; ++t) {
             uint64_t j = i * m + t;
-            uint32_t w[2];
-            draw_link(k2, j, stream, w);
+            uint32_t w[4];
+            draw(seed, j, stream, 2, w);
             uint64_t r = or_uniform(w[0], w[1], slots);
             M[2 * (e0 + j)] = n0 + i;
             M[2 * (e0 + j) + 1] = M[r];
@@ -284,8 +240,6 @@ int or_pba_endpoints(uint32_t q, uint64_t R_q, uint64_t n_b, uint32_t n0, uint64
                      uint64_t len, uint32_t* T)
 {
     if (n0 < 2 || len > R_q || (R_q > 0 && n_b == 0)) return 1;
-    if (q >= (1u << 16) || len > ((uint64_t)1 << 48)) return 1;   /* R6 */
-    uint32_t k2 = or_link_key(seed);
     uint64_t e0 = seed_edge_count(n0);
     uint64_t* M = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (e0 + len + 1));
     uint32_t* ea = (uint32_t*)malloc(sizeof(uint32_t) * e0);
@@ -301,8 +255,8 @@ int or_pba_endpoints(uint32_t q, uint64_t R_q, uint64_t n_b, uint32_t n0, uint64
         /* number of local edges whose source time is before sigma */
         unsigned __int128 num = (unsigned __int128)sigma * R_q;
         uint64_t before = (uint64_t)((num + n_b - 1) / n_b);
-        uint32_t w[2];
-        draw_link(k2, i, q, w);
+        uint32_t w[4];
+        draw(seed, i, q, 2, w);
         uint64_t r = or_uniform(w[0], w[1], 2 * (e0 + before));
         M[2 * (e0 + i)] = n0 + sigma;
         M[2 * (e0 + i) + 1] = M[r];

@@ -8,8 +8,6 @@
 #include <stdint.h>
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
-void or_philox2x32_10(const uint32_t ctr[2], uint32_t key, uint32_t out[2]);
-uint32_t or_link_key(uint64_t seed);
 uint64_t or_uniform(uint32_t w0, uint32_t w1, uint64_t R);
 uint64_t or_coin_threshold(double f);
 

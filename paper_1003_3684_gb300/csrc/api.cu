@@ -65,7 +65,6 @@ PbaCheck check_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, 
     if (w == PG_ID32 && ids > ((u128)1 << 32)) return c;
     if ((u128)n0 + n_b >= ((u128)1 << 32)) return c;       // local ids are 32-bit
     if (N_e >= ((u128)1 << 32)) return c;                  // entries per block are 32-bit
-    // so every copy-draw index (< B * N_e < 2^42) and stream (< 2^10) fits its counter
     // phase-2 index arithmetic: (total entries) * n_b must stay below 2^63
     if ((u128)B * N_e * (n_b ? n_b : 1) >= ((u128)1 << 63)) return c;
     c.st = PG_OK;

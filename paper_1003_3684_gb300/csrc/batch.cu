@@ -38,8 +38,8 @@ struct BatchJob {              // 256 bytes, one per job
     uint32_t u0, u1, u2, pad;  // KRON n0 = 2 thresholds
     FastDiv32 div_m;
     uint32_t pad2;
-    Key key;                   // 120 bytes
-    uint8_t reserved[256 - 120 - 88];
+    Key key;                   // 80 bytes
+    uint8_t reserved[256 - 80 - 88];
 };
 static_assert(sizeof(BatchJob) == 256, "job record is 256 bytes");
 
@@ -84,7 +84,7 @@ __device__ __forceinline__ bool ba_link(uint32_t& cur, const BatchJob& J, const 
                                         uint32_t& v)
 {
     const uint32_t sig = fdiv32(cur, J.div_m);
-    const uint2 w = philox2(cur, 0u, key);
+    const uint4 w = philox(make_uint4(cur, 0u, 0u, 2u), key);
     const uint32_t X = (uint32_t)J.e0 + sig * J.m;
     const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
     const uint32_t e = (uint32_t)(s >> 32);

@@ -343,8 +343,8 @@ __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restri
 // local preferential attachment: local edge i stands at source time
 // sigma(i) = floor(i*n_b/R_q) and copies a uniform slot among the seed clique
 // and the E(sigma(i)) = ceil(sigma(i)*R_q/n_b) edges of earlier source times.
-// One Philox2x32-10 copy draw per link; a link ends the chain when it lands
-// on a seed slot or on the source end of an earlier edge.
+// One Philox per link; a link ends the chain when it lands on a seed slot or
+// on the source end of an earlier edge.
 // ---------------------------------------------------------------------------
 struct QDiv {
     uint64_t R;
@@ -357,7 +357,7 @@ __device__ __forceinline__ bool t_step(uint64_t& cur, uint32_t q, const QDiv& qd
 {
     const uint64_t sig = fdiv(cur * g.n_b, qd.d);
     const uint64_t before = fdiv(sig * qd.R + (g.n_b - 1), g.div_nb);
-    const uint2 w = draw_copy(cur, q, g.key);
+    const uint4 w = draw(cur, q, 2, g.key);
     const uint64_t r = uniform64(w.x, w.y, 2 * (g.e0 + before));
     uint64_t e = r >> 1;
     if (e < g.e0) {
@@ -389,7 +389,7 @@ __device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip
         before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
     else
         before = (uint32_t)fdiv((uint64_t)sig * c.R + (nb - 1), g.div_nb);
-    const uint2 w = philox2(cur, q << 16, g.key);
+    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
     const uint32_t e0 = (uint32_t)g.e0;
     const uint32_t X = e0 + before;
     const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
@@ -409,7 +409,7 @@ __device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip
 __device__ __forceinline__ bool ba_step(uint64_t& cur, const PbaGeom& g, uint64_t& v)
 {
     const uint64_t sig = fdiv(cur, g.div_m);
-    const uint2 w = draw_copy(cur, 0, g.key);
+    const uint4 w = draw(cur, 0, 2, g.key);
     const uint64_t r = uniform64(w.x, w.y, 2 * (g.e0 + sig * g.m));
     uint64_t e = r >> 1;
     if (e < g.e0) {
@@ -429,7 +429,7 @@ __device__ __forceinline__ bool ba_step(uint64_t& cur, const PbaGeom& g, uint64_
 __device__ __forceinline__ bool ba_step32(uint32_t& cur, const PbaGeom& g, uint32_t& v)
 {
     const uint32_t sig = fdiv32(cur, g.div_m32);
-    const uint2 w = philox2(cur, 0u, g.key);
+    const uint4 w = philox(make_uint4(cur, 0u, 0u, 2u), g.key);
     const uint32_t X = (uint32_t)g.e0 + sig * g.m;
     const uint64_t hi = (uint64_t)w.y * X, lo = (uint64_t)w.x * X;
     const uint64_t r = (hi + (lo >> 32)) >> 31;

@@ -15,28 +15,9 @@ namespace pgen {
 // The round keys (the seed key advanced by the Weyl constants once per
 // round) are computed on the host, so inside a kernel they are plain
 // constant-bank operands of the XORs.
-//
-// The copy draws of phase 2 need 64 bits each and use the two-word member
-// of the same family, Philox2x32-10: one 32x32 -> 64 multiply of word 0 per
-// round, its high half XORed with word 1 and the round key. Its 32-bit key
-// is word 0 of the seed's Philox4x32-10 block at counter (0, 0, 0, 5); its
-// counter is (i_lo, i_hi + 2^16 q) for index i < 2^48 of stream q < 2^16.
 struct Key {
     uint32_t k0[10], k1[10];
-    uint32_t k2[10];   // Philox2x32-10 round keys of the copy draws
 };
-
-__host__ __device__ __forceinline__ uint4 philox(uint4 c, const Key& key)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ key.k0[r], (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ key.k1[r], (uint32_t)p0);
-    }
-    return c;
-}
 
 __host__ __device__ inline Key make_key(uint64_t seed)
 {
@@ -48,30 +29,19 @@ __host__ __device__ inline Key make_key(uint64_t seed)
         a += 0x9E3779B9u;
         b += 0xBB67AE85u;
     }
-    uint32_t c = philox(make_uint4(0u, 0u, 0u, 5u), k).x;
-    for (int r = 0; r < 10; ++r) {
-        k.k2[r] = c;
-        c += 0x9E3779B9u;
-    }
     return k;
 }
 
-// Philox2x32-10 of counter (c0, c1) under the copy-draw round keys.
-__device__ __forceinline__ uint2 philox2(uint32_t c0, uint32_t c1, const Key& key)
+__device__ __forceinline__ uint4 philox(uint4 c, const Key& key)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t p = (uint64_t)0xD256D345u * c0;
-        c0 = (uint32_t)(p >> 32) ^ c1 ^ key.k2[r];
-        c1 = (uint32_t)p;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ key.k0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ key.k1[r], (uint32_t)p0);
     }
-    return make_uint2(c0, c1);
-}
-
-// Copy draw for index i (< 2^48) of stream q (< 2^16).
-__device__ __forceinline__ uint2 draw_copy(uint64_t i, uint32_t q, const Key& key)
-{
-    return philox2((uint32_t)i, (uint32_t)(i >> 32) + (q << 16), key);
+    return c;
 }
 
 __device__ __forceinline__ uint4 draw(uint64_t idx, uint32_t stream, uint32_t tag, const Key& key)
