@@ -12,8 +12,10 @@
 // first the digits of dst, then those of src, up to 10 bits per pass. Each
 // pass is three kernels:
 //   radix_hist     per-tile digit counts, stored digit-major H[d][tile];
-//   scan_*         one exclusive scan over H gives, for every (digit, tile),
-//                  where that tile's run of the digit starts in the output;
+//   scan_rows      per digit, the exclusive scan of its counts over tiles,
+//                  and (by the last CTA to finish) the scan of the digit
+//                  totals: together, where each tile's run of each digit
+//                  starts in the output;
 //   radix_scatter  stable rank of each element within its tile among equal
 //                  digits (warp match + per-warp counters + cross-warp scan)
 //                  and a scattered write of the (src, dst) pair.
@@ -111,8 +113,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const typename PairOf<Id>::T* __restrict__ in, typename PairOf<Id>::T* __restrict__ out,
-    uint64_t M, int field, int shift, int bits, const uint64_t* __restrict__ Hs, uint32_t n_tiles,
-    const uint32_t* __restrict__ sort_needed)
+    uint64_t M, int field, int shift, int bits, const uint64_t* __restrict__ Hs,
+    const uint64_t* __restrict__ dstart, uint32_t n_tiles, const uint32_t* __restrict__ sort_needed)
 {
     using P = typename PairOf<Id>::T;
     constexpr int kItems = SortShape<Id>::items;
@@ -129,13 +131,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const uint32_t tile = blockIdx.x;
     for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) {
         for (int w = 0; w < kSortWarps; ++w) wcnt[w][d] = 0;
-        tbase[d] = Hs[(uint64_t)d * n_tiles + tile];
+        tbase[d] = dstart[d] + Hs[(uint64_t)d * n_tiles + tile];
     }
     const uint64_t tile0 = (uint64_t)tile * kTile;
     const uint32_t n = (uint32_t)((M - tile0 < kTile) ? M - tile0 : kTile);
     const uint32_t wbase = wid * (32 * kItems);
     P e[kItems];
-    uint32_t dig[kItems], rnk[kItems];
+    // ranks within the warp (< 32 * kItems <= 512), two per register; the
+    // digits are recomputed from e[] where needed, so no array holds them
+    uint32_t rk[kItems / 2];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const uint32_t t = wbase + r * 32 + lane;
@@ -143,18 +147,26 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
+    // item r of every lane, in lane order: the lowest lane of each group of
+    // equal digits reads and advances the warp's counter, the group gets the
+    // old value by shuffle; the counter is touched by one thread per group
+    // and the syncwarp orders it before the next item's read
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const uint32_t t = wbase + r * 32 + lane;
         const uint32_t d = (t < n) ? digit_of(e[r], field, shift, mask) : 0xFFFFFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t leader = __ffs(peers) - 1;
         uint32_t prev = 0;
-        if (d != 0xFFFFFFFFu) prev = wcnt[wid][d];
+        if (lane == leader && d != 0xFFFFFFFFu) {
+            prev = wcnt[wid][d];
+            wcnt[wid][d] = (uint16_t)(prev + __popc(peers));
+        }
+        prev = __shfl_sync(0xFFFFFFFFu, prev, leader);
         __syncwarp();
-        if (d != 0xFFFFFFFFu && (peers & lt) == 0) wcnt[wid][d] = (uint16_t)(prev + __popc(peers));
-        __syncwarp();
-        dig[r] = d;
-        rnk[r] = prev + __popc(peers & lt);
+        const uint32_t rank = prev + __popc(peers & lt);
+        if (r & 1) rk[r >> 1] |= rank << 16;
+        else rk[r >> 1] = rank;
     }
     __syncthreads();
     // per digit: prefix over warps (in wcnt) and the tile total (in loff)
@@ -203,8 +215,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     __syncthreads();
     // reorder the tile by digit in shared memory
 #pragma unroll
-    for (int r = 0; r < kItems; ++r)
-        if (dig[r] != 0xFFFFFFFFu) buf[loff[dig[r]] + wcnt[wid][dig[r]] + rnk[r]] = e[r];
+    for (int r = 0; r < kItems; ++r) {
+        const uint32_t t = wbase + r * 32 + lane;
+        if (t < n) {
+            const uint32_t d = digit_of(e[r], field, shift, mask);
+            const uint32_t rank = (rk[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
+            buf[loff[d] + wcnt[wid][d] + rank] = e[r];
+        }
+    }
     __syncthreads();
     // write runs: sorted position p goes to tbase[d] + (p - loff[d])
     for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
@@ -251,23 +269,76 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* s
     return before + x - v;
 }
 
-// per-tile sums (tile = kScanTile counts, 256 threads x 16)
-__global__ void __launch_bounds__(256) scan_reduce_kernel(const uint32_t* __restrict__ in,
-                                                          uint64_t n, uint64_t* __restrict__ part,
-                                                          const uint32_t* __restrict__ sort_needed)
+// Offsets of one LSD pass in one launch. H is digit-major: n_tiles counts
+// per digit. CTA d scans its row into Hs[d][t] = sum of H[d][t'] over t' < t
+// and writes the row total to tot[d]. The CTA that finishes last (it draws the
+// last ticket; no CTA waits on another) scans the totals into dstart[d], the
+// first output position of digit d, and puts the ticket back to zero. The
+// scatter adds dstart[d] and Hs[d][t].
+constexpr uint32_t kRowPer = 4;
+__global__ void __launch_bounds__(1024) scan_rows_kernel(const uint32_t* __restrict__ H,
+                                                         uint32_t n_tiles, uint32_t nb,
+                                                         uint64_t* __restrict__ Hs,
+                                                         uint64_t* __restrict__ tot,
+                                                         uint64_t* __restrict__ dstart,
+                                                         uint32_t* __restrict__ ticket,
+                                                         const uint32_t* __restrict__ sort_needed)
 {
     __shared__ uint64_t s_warp[32];
+    __shared__ uint32_t s_last;
     if (*sort_needed == 0) return;
-    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-    uint64_t sum = 0;
-    for (uint32_t t = threadIdx.x; t < kScanTile; t += blockDim.x)
-        if (base + t < n) sum += in[base + t];
-    uint64_t total;
-    block_exclusive_scan(sum, s_warp, total);
-    if (threadIdx.x == 0) part[blockIdx.x] = total;
+    const uint32_t d = blockIdx.x;
+    const uint32_t* row = H + (uint64_t)d * n_tiles;
+    uint64_t* out = Hs + (uint64_t)d * n_tiles;
+    uint64_t carry = 0;
+    for (uint32_t t0 = 0; t0 < n_tiles; t0 += blockDim.x * kRowPer) {
+        const uint32_t tb = t0 + threadIdx.x * kRowPer;
+        uint32_t v[kRowPer];
+        uint64_t sum = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kRowPer; ++k) {
+            v[k] = (tb + k < n_tiles) ? row[tb + k] : 0;
+            sum += v[k];
+        }
+        uint64_t total;
+        uint64_t run = carry + block_exclusive_scan(sum, s_warp, total);
+#pragma unroll
+        for (uint32_t k = 0; k < kRowPer; ++k) {
+            if (tb + k < n_tiles) out[tb + k] = run;
+            run += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        tot[d] = carry;
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == nb - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last == 0) return;
+    __threadfence();
+    const unsigned long long* tot_l2 = reinterpret_cast<const unsigned long long*>(tot);
+    uint64_t start = 0;
+    for (uint32_t d0 = 0; d0 < nb; d0 += blockDim.x) {
+        const uint32_t i = d0 + threadIdx.x;
+        const uint64_t c = i < nb ? (uint64_t)__ldcg(tot_l2 + i) : 0;   // not from L1
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan(c, s_warp, total);
+        if (i < nb) dstart[i] = start + ex;
+        start += total;
+    }
+    if (threadIdx.x == 0) *ticket = 0;
 }
 
-// exclusive scan of the tile sums, one CTA looping over chunks
+// Threads per CTA of scan_rows: enough for one trip over a row, 32 to 1024.
+uint32_t scan_rows_threads(uint32_t n_tiles)
+{
+    const uint32_t want = (n_tiles + kRowPer - 1) / kRowPer;
+    const uint32_t t = (want + 31) & ~31u;
+    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
+// exclusive scan of n_parts sums in place, one CTA looping over chunks
 __global__ void __launch_bounds__(1024) scan_parts_kernel(uint64_t* __restrict__ part,
                                                           uint64_t n_parts,
                                                           const uint32_t* __restrict__ sort_needed)
@@ -285,32 +356,6 @@ __global__ void __launch_bounds__(1024) scan_parts_kernel(uint64_t* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) scan_apply_kernel(const uint32_t* __restrict__ in,
-                                                         uint64_t n,
-                                                         const uint64_t* __restrict__ part,
-                                                         uint64_t* __restrict__ out,
-                                                         const uint32_t* __restrict__ sort_needed)
-{
-    __shared__ uint64_t s_warp[32];
-    if (*sort_needed == 0) return;
-    constexpr int per = kScanTile / 256;
-    const uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * per;
-    uint32_t v[per];
-    uint64_t sum = 0;
-#pragma unroll
-    for (int t = 0; t < per; ++t) {
-        v[t] = (base + t < n) ? in[base + t] : 0;
-        sum += v[t];
-    }
-    uint64_t total;
-    uint64_t run = part[blockIdx.x] + block_exclusive_scan(sum, s_warp, total);
-#pragma unroll
-    for (int t = 0; t < per; ++t) {
-        if (base + t < n) out[base + t] = run;
-        run += v[t];
-    }
-}
-
 // ---- final pass: col and row_ptr from the sorted pairs ---------------------
 // Flags (sort_needed = 1) a list that is not grouped by source, or that has
 // a row longer than kGroupedMaxRow.
@@ -319,14 +364,29 @@ __global__ void __launch_bounds__(256) csr_check_kernel(const typename PairOf<Id
                                                         uint64_t M, uint32_t* __restrict__ sort_needed)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool bad = false;                 // one atomic per warp, not one per pair
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        const uint64_t src = s[i].x;
-        const bool starts = (i == 0) || s[i - 1].x != src;
-        bad |= i > 0 && (uint64_t)s[i - 1].x > src;
-        bad |= starts && i + kGroupedMaxRow < M && (uint64_t)s[i + kGroupedMaxRow].x == src;
+    // A warp that finds a violation sets the flag (one atomic per warp) and
+    // stops; every few rounds the warps also read the flag and stop once any
+    // warp has set it, so an unsorted list costs about one round, not a full
+    // read. The trip count is uniform across the warp (i0 steps by the grid).
+    const volatile uint32_t* flag = sort_needed;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t round = 0;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < M;
+         i0 += stride, ++round) {
+        const uint64_t i = i0 + lane;
+        bool bad = false;
+        if (i < M) {
+            const uint64_t src = s[i].x;
+            const bool starts = (i == 0) || s[i - 1].x != src;
+            bad = i > 0 && (uint64_t)s[i - 1].x > src;
+            bad |= starts && i + kGroupedMaxRow < M && (uint64_t)s[i + kGroupedMaxRow].x == src;
+        }
+        if (__any_sync(0xFFFFFFFFu, bad)) {
+            if (lane == 0) atomicOr(sort_needed, 1u);
+            return;
+        }
+        if ((round & 7) == 7 && *flag != 0) return;
     }
-    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(sort_needed, 1u);
 }
 
 // Row ends of a list sorted (or grouped) by source: the last edge i of row v
@@ -462,10 +522,30 @@ __global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<I
                                                          const uint32_t* __restrict__ sort_needed)
 {
     if (*sort_needed == 0) return;
+    // four grid strides per trip, so each thread has four independent loads
+    // in flight
+    constexpr int kU = 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        col[i] = (Id)s[i].y;
-        mark_row_end(s, M, N, i, row_ptr);
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += kU * stride) {
+        typename PairOf<Id>::T e[kU];
+        uint64_t nx[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint64_t i = i0 + u * stride;
+            if (i < M) {
+                e[u] = s[i];
+                nx[u] = (i + 1 < M) ? (uint64_t)s[i + 1].x : ~(uint64_t)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint64_t i = i0 + u * stride;
+            if (i < M) {
+                col[i] = (Id)e[u].y;
+                const uint64_t v = e[u].x;
+                if (v < N && nx[u] != v) row_ptr[v + 1] = i + 1;
+            }
+        }
     }
 }
 
@@ -581,9 +661,9 @@ int bit_length(uint64_t x)
 }
 
 struct CsrLayout {
-    size_t off_a, off_b, off_h, off_hs, off_part, off_flag, off_rpart, total;
+    size_t off_a, off_b, off_h, off_hs, off_flag, off_dig, off_rpart, total;
     uint32_t n_tiles, max_nb;
-    uint64_t n_h, n_parts, n_rparts;
+    uint64_t n_h, n_rparts;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -598,7 +678,6 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
     L.max_nb = 1u << dbits;
     L.n_tiles = (uint32_t)((M + tile - 1) / tile);
     L.n_h = (uint64_t)L.max_nb * L.n_tiles;
-    L.n_parts = (L.n_h + kScanTile - 1) / kScanTile;
     size_t o = 0;
     L.off_a = o;
     o += a256(M * pair_bytes);
@@ -608,10 +687,10 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
     o += a256(L.n_h * 4);
     L.off_hs = o;
     o += a256(L.n_h * 8);
-    L.off_part = o;
-    o += a256((L.n_parts + 1) * 8);
-    L.off_flag = o;
+    L.off_flag = o;   // +0: sort-needed flag, +64: the row scan's ticket
     o += 256;
+    L.off_dig = o;    // digit totals, then digit starts (kMaxBuckets each)
+    o += a256(2 * (size_t)kMaxBuckets * 8);
     L.n_rparts = (N + 1 + kScanTile - 1) / kScanTile;
     L.off_rpart = o;
     o += a256((L.n_rparts + 1) * 8);
@@ -644,8 +723,11 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
     P* buf[2] = {(P*)(ws + L.off_a), (P*)(ws + L.off_b)};
     uint32_t* H = (uint32_t*)(ws + L.off_h);
     uint64_t* Hs = (uint64_t*)(ws + L.off_hs);
-    uint64_t* part = (uint64_t*)(ws + L.off_part);
+    uint64_t* tot = (uint64_t*)(ws + L.off_dig);
+    uint64_t* dstart = tot + kMaxBuckets;
+    uint32_t* ticket = (uint32_t*)(ws + L.off_flag + 64);
     cudaError_t err;
+    if (cudaMemsetAsync(ticket, 0, 4, s) != cudaSuccess) return cudaErrorUnknown;
     const int bits = bit_length(N > 0 ? N - 1 : 0);
     const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
     const P* cur = in;
@@ -658,25 +740,22 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
                                   ? bits - shift
                                   : (bits + passes - 1) / passes;
                 if (b <= 0) break;
-                const uint64_t nh = ((uint64_t)1 << b) * L.n_tiles;
                 {
                     TraceScope trace("csr_radix_hist", s);
                     radix_hist_kernel<Id><<<L.n_tiles, kSortThreads,
                                             (size_t)kSortWarps * 4 << b, s>>>(
                         cur, M, field, shift, b, H, L.n_tiles, sort_needed);
                 }
-                const uint64_t n_parts = (nh + kScanTile - 1) / kScanTile;
                 {
                     TraceScope trace("csr_scan", s);
-                    scan_reduce_kernel<<<(unsigned)n_parts, 256, 0, s>>>(H, nh, part, sort_needed);
-                    scan_parts_kernel<<<1, 1024, 0, s>>>(part, n_parts, sort_needed);
-                    scan_apply_kernel<<<(unsigned)n_parts, 256, 0, s>>>(H, nh, part, Hs,
-                                                                        sort_needed);
+                    scan_rows_kernel<<<1u << b, scan_rows_threads(L.n_tiles), 0, s>>>(
+                        H, L.n_tiles, 1u << b, Hs, tot, dstart, ticket, sort_needed);
                 }
                 {
                     TraceScope trace("csr_radix_scatter", s);
                     radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
-                        cur, buf[which], M, field, shift, b, Hs, L.n_tiles, sort_needed);
+                        cur, buf[which], M, field, shift, b, Hs, dstart, L.n_tiles,
+                        sort_needed);
                 }
                 if ((err = cudaGetLastError()) != cudaSuccess) return err;
                 cur = buf[which];

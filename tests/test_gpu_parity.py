@@ -476,6 +476,22 @@ def test_csr_grouped_lists(max_row, id64):
     csr_check(_grouped(max_row, N, max_row, 1500, id64), N, id64)
 
 
+@pytest.mark.parametrize("flaw", ["none", "last_pair_out_of_order", "long_last_row"])
+def test_csr_grouped_check_reads_to_the_end(flaw):
+    """A list of 3.2M pairs, grouped except (maybe) at its very end: the
+    sortedness check must see a flaw that only the last rounds of its grid
+    stride reach, and must not flag a list that has none."""
+    N = 2**22
+    e = _grouped(11, N, 8, 800_000)
+    if flaw == "last_pair_out_of_order":
+        assert e[-2, 0] > 0
+        e[-1, 0] = e[-2, 0] - 1
+    elif flaw == "long_last_row":
+        tail = np.stack([np.full(40, N - 1), np.arange(40)[::-1]], 1).astype(e.dtype)
+        e = np.concatenate([e[e[:, 0] < N - 1], tail])
+    csr_check(e, N)
+
+
 def test_csr_of_gpu_ba_output_is_canonical():
     """Serial BA output is grouped by source: the CSR must equal the oracle's."""
     n, m, n0, seed = 20_000, 6, 7, 4
