@@ -14,7 +14,7 @@
 namespace pgen {
 namespace {
 
-constexpr uint32_t kUnreached = 0xFFFFFFFFu;
+constexpr uint32_t kBfsWarps = 8;          // warps per CTA of the BFS level kernel
 constexpr uint32_t kHistSmem = 8192;   // histograms up to this many buckets count in smem
 
 template <typename Id>
@@ -56,23 +56,39 @@ __global__ void __launch_bounds__(256) histogram_kernel(const uint64_t* __restri
     }
 }
 
+// Adjacency entries are read once per search: streaming loads, so that they
+// do not push the visited bitmap out of L2.
+__device__ __forceinline__ uint64_t load_streaming(const uint32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ uint64_t load_streaming(const uint64_t* p)
+{
+    return __ldcs(reinterpret_cast<const unsigned long long*>(p));
+}
+
 // One BFS level: each warp takes frontier vertices in turn and its lanes
-// walk the vertex's row; a neighbour still unreached is claimed with one
-// compare-and-swap and appended to the next frontier (one atomic per warp
-// iteration for the appends). scanned += the degrees of the frontier.
+// walk the vertex's row. A neighbour whose bit in the visited bitmap (N bits,
+// small enough to stay in L2) is clear is claimed by an atomic OR of that bit;
+// the claimer writes its distance and appends it to the next frontier.
+// scanned += the degrees of the frontier.
 template <typename Id>
-__global__ void __launch_bounds__(256) bfs_level_kernel(const uint64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_t* __restrict__ row_ptr,
                                                         const Id* __restrict__ col,
                                                         const uint32_t* __restrict__ frontier,
                                                         uint32_t fsize, uint32_t* __restrict__ next,
                                                         uint32_t* __restrict__ nsize,
-                                                        uint32_t* __restrict__ dist, uint32_t level,
+                                                        uint32_t* __restrict__ dist,
+                                                        uint32_t* __restrict__ vis, uint32_t level,
                                                         uint64_t N,
                                                         unsigned long long* __restrict__ scanned)
 {
-    const uint32_t lane = threadIdx.x & 31;
+    // claimed vertices collect in a per-warp buffer and leave 32 at a time,
+    // so the shared counter of the next frontier takes one atomic per 32
+    // claims (the frontier's order is not part of the result)
+    __shared__ uint32_t wbuf[kBfsWarps][64];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t* buf = wbuf[wid];
+    uint32_t held = 0;   // warp-uniform, < 32 between chunks
     unsigned long long seen = 0;
     for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < fsize; i += warps) {
         const uint32_t v = frontier[i];
@@ -83,27 +99,49 @@ __global__ void __launch_bounds__(256) bfs_level_kernel(const uint64_t* __restri
             bool claim = false;
             uint32_t u = 0;
             if (e < b) {
-                const uint64_t u64 = col[e];
+                const uint64_t u64 = load_streaming(col + e);
                 if (u64 < N) {
                     u = (uint32_t)u64;
-                    claim = dist[u] == kUnreached && atomicCAS(&dist[u], kUnreached, level + 1) == kUnreached;
+                    const uint32_t bit = 1u << (u & 31);
+                    // a stale cached word only costs an atomic that finds the bit set
+                    if ((vis[u >> 5] & bit) == 0) claim = (atomicOr(&vis[u >> 5], bit) & bit) == 0;
                 }
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, claim);
-            if (m) {
+            if (claim) {
+                dist[u] = level + 1;
+                buf[held + __popc(m & lt)] = u;
+            }
+            held += __popc(m);
+            if (held >= 32) {
+                __syncwarp();
                 uint32_t at = 0;
-                if (lane == 0) at = atomicAdd(nsize, (uint32_t)__popc(m));
+                if (lane == 0) at = atomicAdd(nsize, 32u);
                 at = __shfl_sync(0xFFFFFFFFu, at, 0);
-                if (claim) next[at + __popc(m & lt)] = u;
+                next[at + lane] = buf[lane];
+                const uint32_t rest = held - 32;
+                const uint32_t x = lane < rest ? buf[32 + lane] : 0;
+                __syncwarp();
+                if (lane < rest) buf[lane] = x;
+                __syncwarp();
+                held = rest;
             }
         }
+    }
+    __syncwarp();
+    if (held) {
+        uint32_t at = 0;
+        if (lane == 0) at = atomicAdd(nsize, held);
+        at = __shfl_sync(0xFFFFFFFFu, at, 0);
+        if (lane < held) next[at + lane] = buf[lane];
     }
     if (lane == 0 && seen) atomicAdd(scanned, seen);
 }
 
-__global__ void bfs_seed_kernel(uint32_t* dist, uint32_t* frontier, uint32_t source)
+__global__ void bfs_seed_kernel(uint32_t* dist, uint32_t* vis, uint32_t* frontier, uint32_t source)
 {
     dist[source] = 0;
+    vis[source >> 5] = 1u << (source & 31);
     frontier[0] = source;
 }
 
@@ -159,8 +197,9 @@ pg_status pg_degree_histogram(const uint64_t* d_deg, uint64_t n_vertices, uint32
 
 size_t pg_bfs_workspace_size(uint64_t n_vertices)
 {
-    // two frontiers of n_vertices uint32, then the counters
-    return 2 * (((size_t)n_vertices * 4 + 255) & ~(size_t)255) + 256;
+    // two frontiers of n_vertices uint32, the counters, the visited bitmap
+    return 2 * (((size_t)n_vertices * 4 + 255) & ~(size_t)255) + 256 +
+           ((((size_t)n_vertices + 31) / 32 * 4 + 255) & ~(size_t)255);
 }
 
 pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertices, pg_idwidth w,
@@ -177,22 +216,25 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
     uint32_t* fr[2] = {(uint32_t*)ws, (uint32_t*)(ws + fbytes)};
     uint32_t* nsize = (uint32_t*)(ws + 2 * fbytes);
     unsigned long long* scanned = (unsigned long long*)(ws + 2 * fbytes + 8);
+    uint32_t* vis = (uint32_t*)(ws + 2 * fbytes + 256);
+    const size_t vbytes = ((size_t)n_vertices + 31) / 32 * 4;
     if (cudaMemsetAsync(d_dist, 0xFF, n_vertices * 4, s) != cudaSuccess) return PG_ECUDA;
     if (cudaMemsetAsync(ws + 2 * fbytes, 0, 256, s) != cudaSuccess) return PG_ECUDA;
-    bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, fr[0], (uint32_t)source);
+    if (cudaMemsetAsync(vis, 0, vbytes, s) != cudaSuccess) return PG_ECUDA;
+    bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, vis, fr[0], (uint32_t)source);
     uint32_t fsize = 1, level = 0, cur = 0;
     TraceScope trace("bfs", s);
     while (fsize > 0) {
         if (cudaMemsetAsync(nsize, 0, 4, s) != cudaSuccess) return PG_ECUDA;
         const int grid = grid_cap((uint64_t)fsize * 32);
         if (w == PG_ID64)
-            bfs_level_kernel<uint64_t><<<grid, 256, 0, s>>>(d_row_ptr, (const uint64_t*)d_col,
+            bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(d_row_ptr, (const uint64_t*)d_col,
                                                             fr[cur], fsize, fr[cur ^ 1], nsize,
-                                                            d_dist, level, n_vertices, scanned);
+                                                            d_dist, vis, level, n_vertices, scanned);
         else
-            bfs_level_kernel<uint32_t><<<grid, 256, 0, s>>>(d_row_ptr, (const uint32_t*)d_col,
+            bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(d_row_ptr, (const uint32_t*)d_col,
                                                             fr[cur], fsize, fr[cur ^ 1], nsize,
-                                                            d_dist, level, n_vertices, scanned);
+                                                            d_dist, vis, level, n_vertices, scanned);
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
         // the next frontier's size decides whether another level runs
         if (cudaMemcpyAsync(&fsize, nsize, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
