@@ -194,6 +194,13 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the workload
 # --------------------------------------------------------------------------
+def all_cores_estimate(value: float) -> dict:
+    """The one-core oracle rate scaled by the host's core count: a labelled
+    estimate (the blocks of the workload are independent), not a measurement."""
+    n = os.cpu_count() or 1
+    return dict(value=value * n, host_cores=n, note="estimate: one-core rate x host cores")
+
+
 def oracle_sample(name: str, cfg: dict, budget_s: float):
     """Time the oracle, as it stands, on samples of the workload.
 
@@ -315,7 +322,7 @@ def run_reference(args, rank: int, world: int):
                 scaling="weak", vs_baseline=None, dtype="u32", data="synthetic",
                 config=dict(workload=args.workload, sample=desc),
                 cpu_baseline=dict(kind="oracle", value=value, unit=unit, cores=1,
-                                  sample=desc),
+                                  sample=desc, all_cores_estimate=all_cores_estimate(value)),
                 e2e=dict(value=value, unit=unit, h2d_bytes_per_step=0,
                          d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -494,7 +501,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
             t_cpu += time.perf_counter() - t0
             i += 1
         line["cpu_baseline"] = dict(value=e_cpu / t_cpu, unit="edges/s", cores=1, kind="oracle",
-                                    sample=f"{i} jobs of the batch (every 97th), {t_cpu:.1f} s")
+                                    sample=f"{i} jobs of the batch (every 97th), {t_cpu:.1f} s",
+                                    all_cores_estimate=all_cores_estimate(e_cpu / t_cpu))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -732,13 +740,15 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
         sampler.start()
         time.sleep(0.3)
     if flush is None:
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
+        # one event between consecutive steps: the region's time and each step's
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
+        ms = evs[0].elapsed_time(evs[-1])
+        per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     else:
         # each step timed alone, after a write of a buffer twice the L2 size
         evs = []
@@ -750,7 +760,8 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
+        per_step = [a.elapsed_time(b) for a, b in evs]
+        ms = sum(per_step)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
@@ -817,7 +828,10 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u32",
                 data="synthetic", config=cfg_json, roofline=roof, gpu_launches=launches,
                 kernels={kk: [v[0], round(v[1], 4)] for kk, v in kernels.items()},
-                clocks=clocks)
+                clocks=clocks,
+                step_ms=dict(best=round(min(per_step), 4),
+                             median=round(statistics.median(per_step), 4),
+                             mean=round(ms / args.steps, 4), rank=0))
     if kind == "pba" and cfg["blocks"] > 1:
         line["paper_context"] = ("PBA 1e9 vertices / 5e9 edges in 12.39 s on 1,000 CPUs "
                                  "(~4.0e8 edges/s): context, other hardware")
@@ -837,7 +851,8 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, tsec, ns = oracle_sample(args.workload, cfg, args.cpu_budget)
         line["cpu_baseline"] = dict(value=v, unit=unit, cores=1, kind="oracle",
-                                    sample=f"{desc}; {ns} samples, {tsec:.1f} s")
+                                    sample=f"{desc}; {ns} samples, {tsec:.1f} s",
+                                    all_cores_estimate=all_cores_estimate(v))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
