@@ -63,6 +63,18 @@ const char* pg_status_string(pg_status s);
 int pg_device_sm_count(void);
 const char* pg_version(void);
 
+/* Test hook (not part of the method): with on != 0, gen_pba, gen_pba_factions,
+ * pg_pba_prepare / gen_pba_blocks, gen_pba_to_host and gen_pba_noalloc use the
+ * 64-bit-index variants of their kernels for every input. Those variants
+ * otherwise run only when a block's phase-2 list plus its seed edges reach
+ * 2^32 entries (or, for blocks = 1, n*m + e0 >= 2^32). The output is the same
+ * either way; the switch lets parity tests check the 64-bit arithmetic on
+ * graphs small enough for the oracle. Process-wide and read at each launch;
+ * a prepared workspace keeps the choice made when it was prepared (after the
+ * switch has once been on, emits also launch the 64-bit variant, which exits
+ * at once for workspaces prepared without it). Default off; cannot fail. */
+void pg_force_wide_path(int on);
+
 /* Throughput probe (not part of the method): launches one kernel in which
  * each of pg_philox_probe_threads() threads (8 CTAs of 256 per SM) makes
  * calls_per_thread Philox4x32-10 calls and writes one folded word to

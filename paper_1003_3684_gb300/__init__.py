@@ -28,7 +28,7 @@ __all__ = [
     "PG_OK", "PG_EINVAL", "PG_ENOSPC", "PG_ECUDA", "PG_ETIMEOUT", "PG_ENOMEM",
     "PgenError", "lib", "library_path",
     "pg_status_string", "pg_device_sm_count", "pg_version",
-    "pg_pba_edge_count", "pg_pba_workspace_size", "gen_pba", "gen_pba_to_host",
+    "pg_pba_edge_count", "pg_force_wide_path", "pg_pba_workspace_size", "gen_pba", "gen_pba_to_host",
     "pba_faction_table", "gen_pba_factions", "pg_pba_prepare", "gen_pba_blocks",
     "gen_kronecker_range", "philox_rate", "int_pipe_rates", "edges_to_csr_opts", "gen_random_cells",
     "kronecker_xor_random", "CSR_SYMMETRIZE", "CSR_DEDUP", "CSR_NO_LOOPS", "CSR_ODD",
@@ -137,6 +137,15 @@ def pg_device_sm_count() -> int:
 
 def pg_version() -> str:
     return lib().pg_version().decode()
+
+
+def pg_force_wide_path(on: bool) -> None:
+    """Test hook: the PBA kernels take their 64-bit-index variants for every
+    input (the output is the same), so that parity tests reach them."""
+    L = lib()
+    L.pg_force_wide_path.argtypes = [C.c_int]
+    L.pg_force_wide_path.restype = None
+    L.pg_force_wide_path(1 if on else 0)
 
 
 def pg_pba_edge_count(n: int, m: int, blocks: int, n0: int) -> int:

@@ -155,6 +155,8 @@ int pg_device_sm_count(void) { return device_sm_count(); }
 
 const char* pg_version(void) { return "pgen 0.1 (sm_103a)"; }
 
+void pg_force_wide_path(int on) { set_wide_path_forced(on != 0); }
+
 uint64_t pg_pba_edge_count(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0)
 {
     const PbaCheck c = check_pba(n, m, blocks, n0, blocks ? blocks : 1, 0.0, PG_ID64);

@@ -33,6 +33,7 @@
 // entries; each lane follows one chain, one Philox per loop trip, and a lane
 // whose entry is finished takes the next unclaimed entry of the run (ballot),
 // so lanes stay busy until the run is exhausted.
+#include <atomic>
 #include <type_traits>
 
 #include "pg_internal.h"
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restri
                                                         FastDiv* __restrict__ divR,
                                                         QRecip* __restrict__ recip, uint32_t nb,
                                                         uint32_t B, uint32_t rows, uint64_t e0,
+                                                        uint32_t force_wide,
                                                         uint32_t* __restrict__ wide_flag)
 {
     __shared__ uint64_t part[32][33];
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restri
             R[q] = acc;
             divR[q] = make_fastdiv(acc > 0 ? acc : 1);
             recip[q] = make_recip(acc, nb);
-            if (acc + e0 >= ((uint64_t)1 << 32)) atomicOr(wide_flag, 1u);
+            if (force_wide || acc + e0 >= ((uint64_t)1 << 32)) atomicOr(wide_flag, 1u);
         }
     }
     __syncthreads();
@@ -790,6 +792,23 @@ PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S)
     return w;
 }
 
+// When set, the serial and two-phase kernels take their 64-bit-index
+// variants for every input (the same output); a test hook that lets the
+// parity tests check those variants on graphs small enough for the oracle.
+// A workspace records the choice when it is prepared, so once the switch has
+// been on, every later emit also launches the 64-bit variant (which returns
+// at once unless the workspace's flag asks for it).
+namespace {
+std::atomic<bool> g_force_wide{false};
+std::atomic<bool> g_ever_forced{false};
+}
+void set_wide_path_forced(bool on)
+{
+    if (on) g_ever_forced.store(true);
+    g_force_wide.store(on);
+}
+bool wide_path_forced() { return g_force_wide.load(); }
+
 cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s)
 {
     const int sms = device_sm_count();
@@ -797,7 +816,7 @@ cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s)
     const uint64_t tiles = (g.N_e + tile - 1) / tile;
     const uint64_t full = (uint64_t)sms * 8;
     const int grid = (int)(tiles < full ? (tiles > 0 ? tiles : 1) : full);
-    const bool fast = g.N_e + g.e0 < ((uint64_t)1 << 32);
+    const bool fast = !wide_path_forced() && g.N_e + g.e0 < ((uint64_t)1 << 32);
     TraceScope trace("ba_chain", s);
     if (id64) {
         if (fast) ba_kernel<uint64_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out);
@@ -894,7 +913,7 @@ cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
         TraceScope trace("pba_scan", s);
         pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(W.cnt, W.off, W.R, W.divR, W.recip,
                                                           (uint32_t)g.n_b, g.B, g.B * g.S, g.e0,
-                                                          W.wide);
+                                                          wide_path_forced() ? 1u : 0u, W.wide);
     }
     return cudaGetLastError();
 }
@@ -909,7 +928,8 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
     const PbaBuffers W = pba_buffers(g, const_cast<void*>(d_ws));
     cudaError_t err;
     // every R_q + e0 < 2^32 is certain when all entries together are fewer
-    const bool surely_fast = (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);
+    const bool surely_fast =
+        !g_ever_forced.load() && (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);
     const uint32_t nblk = b_end - b_begin;
     const uint32_t chunks = hc ? hc->chunks : 1;
     const uint32_t per = (nblk + chunks - 1) / chunks;

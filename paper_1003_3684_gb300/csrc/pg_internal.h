@@ -72,6 +72,8 @@ uint32_t pba_segments(uint64_t N_e, uint32_t B, int sm_count);
 uint32_t pba_prefix_len(uint64_t N_e);
 uint64_t pba_segment_length(uint64_t N_e, uint32_t S);
 
+void set_wide_path_forced(bool on);
+bool wide_path_forced();
 cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s);
 int pba_setup(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t faction_width,
               double inter_frac, uint64_t seed, int id64, PbaGeom* g, uint64_t* n_edges);

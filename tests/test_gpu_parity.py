@@ -132,6 +132,60 @@ def test_pba(B, n_b, m, Wf, f, n0, seed):
     assert_same(host(got), ref)
 
 
+@pytest.fixture
+def wide_path():
+    pg.pg_force_wide_path(True)
+    try:
+        yield
+    finally:
+        pg.pg_force_wide_path(False)
+
+
+@pytest.mark.parametrize("B,n_b,m,Wf,f,n0,seed,id64", [
+    (8, 30_000, 5, 1, 0.1, 6, 3, False),
+    (5, 40_000, 2, 5, 0.5, 5, 2, True),
+    (1024, 100, 5, 1, 0.1, 6, 3, False),
+    (16, 2**14, 5, 1, 0.1, 6, 5, False),
+    (4, 5_000, 3, 1, 0.2, 40, 8, False),
+    (3, 1, 1, 1, 0.2, 2, 1, False),
+    (1, 60_000, 4, 1, 0.0, 5, 1, False),          # blocks = 1: the serial kernel
+    (1, 20_000, 3, 1, 0.0, 2, 2**33 + 1, True),
+])
+def test_pba_wide_index_variants_match_oracle(wide_path, B, n_b, m, Wf, f, n0, seed, id64):
+    """The 64-bit-index kernels (otherwise reached only past 2^32 entries per
+    block) give the oracle's graph."""
+    n = B * n_b
+    got = pg.gen_pba(n, m, B, n0, Wf, f, seed, id64=id64)
+    ref = o.ba(n, m, n0, seed) if B == 1 else o.pba(n, m, B, n0, Wf, f, seed)[0]
+    torch.cuda.synchronize()
+    assert_same(host(got, id64), np.asarray(ref).astype(np.uint64))
+
+
+def test_pba_wide_choice_follows_the_prepared_workspace():
+    """Prepared with the 64-bit variants forced, emitted after the switch is
+    off (and the reverse): every range still equals the oracle's graph."""
+    B, n_b, m, n0, seed = 6, 20_000, 4, 5, 17
+    n = B * n_b
+    ref, _, _ = o.pba(n, m, B, n0, 1, 0.1, seed)
+    ref = np.asarray(ref).astype(np.uint64)
+    per = ref.shape[0] // B
+    pg.pg_force_wide_path(True)
+    try:
+        ws_wide = pg.pg_pba_prepare(n, m, B, n0, seed=seed)
+    finally:
+        pg.pg_force_wide_path(False)
+    ws_fast = pg.pg_pba_prepare(n, m, B, n0, seed=seed)
+    pg.pg_force_wide_path(True)
+    try:
+        part_a = pg.gen_pba_blocks(ws_fast, n, m, B, 0, 3, n0=n0, seed=seed)
+    finally:
+        pg.pg_force_wide_path(False)
+    part_b = pg.gen_pba_blocks(ws_wide, n, m, B, 3, 6, n0=n0, seed=seed)
+    torch.cuda.synchronize()
+    assert_same(host(part_a), ref[:3 * per])
+    assert_same(host(part_b), ref[3 * per:])
+
+
 def test_pba_id64_and_repeat_is_identical():
     B, n_b, m = 12, 9_000, 3
     a = pg.gen_pba(B * n_b, m, B, 4, 2, 0.2, 77, id64=True)
