@@ -50,8 +50,8 @@ constexpr uint32_t kPassRun = 1024;             // entries per warp run in a pas
 constexpr uint32_t kPassChunk = (kPassThreads / 32) * kPassRun;   // 16384 per CTA
 constexpr int kEmitWarps = 8;
 constexpr int kEmitThreads = kEmitWarps * 32;
-constexpr int kEmitItems = 16;
-constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 512 entries per warp run
+constexpr int kEmitItems = 8;
+constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 256 entries per warp run
 constexpr uint32_t kMaxBlocks = 1024;
 constexpr int kBaThreads = 256;
 template <typename Id>
@@ -537,14 +537,19 @@ __device__ __forceinline__ void emit_run(Id* out, uint64_t e_first, uint32_t n, 
 //          by a warp match over 32 entries and per-warp cursors in smem;
 //   chain  the lanes resolve T_q[i] for the run's entries, pooled;
 //   emit   the run's (src, dst) pairs leave as vector stores.
-// Warps never wait on each other. kFast: 32-bit arithmetic, valid when every
-// R_q + e0 < 2^32 (the scan's flag says which variant does the work).
+// kFast (32-bit arithmetic, valid when every R_q + e0 < 2^32; the scan's flag
+// says which variant does the work) keeps two runs ranked at a time, in two
+// buffers: a lane that finishes an entry of run r takes the next unclaimed
+// entry of run r or r+1, so the pool drains once per segment rather than at
+// the end of every run. Run r is emitted as soon as all its entries are
+// resolved, and run r+2 is ranked into its buffer. Warps never wait on each
+// other.
 // ---------------------------------------------------------------------------
 template <typename CurT>
 struct EmitWarpSmem {
     CurT cur[kMaxBlocks];      // next unused index into T_q, per target block
-    CurT item[kEmitRun];       // slot index i, then the resolved local id
-    uint16_t qs[kEmitRun];     // target block of each entry of the run
+    CurT item[2][kEmitRun];    // slot index i, then the resolved local id
+    uint16_t qs[2][kEmitRun];  // target block of each entry of the run
 };
 
 template <typename Id, bool kFast>
@@ -581,17 +586,16 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     }
     __syncwarp();
 
-    // block ids of the first run; later runs are loaded one run ahead, while
-    // the chains of the current run execute
-    uint32_t qv[kEmitItems];
+    // block ids of run `run` of the segment (0xFFFF past its end)
+    auto load_run = [&](uint32_t run, uint32_t (&qv)[kEmitItems]) {
 #pragma unroll
-    for (int r = 0; r < kEmitItems; ++r) {
-        const uint64_t j = lo + r * 32 + lane;
-        qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
-    }
-    for (uint64_t base = lo; base < hi; base += kEmitRun) {
-        const uint32_t n = (uint32_t)((hi - base < kEmitRun) ? hi - base : kEmitRun);
-        // rank
+        for (int r = 0; r < kEmitItems; ++r) {
+            const uint64_t j = lo + (uint64_t)run * kEmitRun + r * 32 + lane;
+            qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
+        }
+    };
+    // rank: slot index of each entry in its target's list, in entry order
+    auto rank_run = [&](const uint32_t (&qv)[kEmitItems], CurT* item, uint16_t* qs) {
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
             const uint32_t q = qv[r];
@@ -601,47 +605,84 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             __syncwarp();
             if (q != 0xFFFFu && (peers & lt) == 0) ws.cur[q] = prev + __popc(peers);
             __syncwarp();
-            ws.item[r * 32 + lane] = prev + __popc(peers & lt);
-            ws.qs[r * 32 + lane] = (uint16_t)q;
+            item[r * 32 + lane] = prev + __popc(peers & lt);
+            qs[r * 32 + lane] = (uint16_t)q;
         }
         __syncwarp();
-#pragma unroll
-        for (int r = 0; r < kEmitItems; ++r) {
-            const uint64_t j = base + kEmitRun + r * 32 + lane;
-            qv[r] = (j < hi) ? Ap[j] : 0xFFFFu;
+    };
+    // emit: the run's n resolved entries, entry t at segment position base + t
+    auto emit_buf = [&](uint64_t base, uint32_t n, const CurT* item, const uint16_t* qs) {
+        auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
+            s_ = src_base + fdiv32((uint32_t)(base + t2), g.div_m32);
+            d_ = (uint64_t)qs[t2] * g.span + (uint32_t)item[t2];
+        };
+        emit_run(out, out_block + g.e0 + base, n, lane, edge_at);
+        __syncwarp();
+    };
+
+    const uint32_t total = (uint32_t)(hi - lo);   // entries of the segment
+    const uint32_t runs = (total + kEmitRun - 1) / kEmitRun;
+    uint32_t qv[kEmitItems];
+    if constexpr (kFast) {
+        load_run(0, qv);
+        rank_run(qv, ws.item[0], ws.qs[0]);
+        if (runs > 1) {
+            load_run(1, qv);
+            rank_run(qv, ws.item[1], ws.qs[1]);
         }
-        // chains: a lane that finishes an entry takes the next unclaimed one.
-        // The loop body is kept straight-line -- load the new entry, reconverge,
-        // then ONE link for every lane -- so a warp whose lanes are at
-        // different depths still runs the link code once per trip.
-        if constexpr (kFast) {
-            // items [0, n); a lane that finishes an entry stores its value and
-            // claims the next unclaimed item (claims are in lane order)
-            uint32_t k = lane, next = 32, q = 0, cur = 0;
-            bool active = k < n;
-            QRecip c{0, 0, 0, 0};
-            if (active) {
-                q = ws.qs[k];
-                cur = (uint32_t)ws.item[k];
+        if (runs > 2) load_run(2, qv);   // in flight during run 0's chains
+        // pooled chains over the segment: entry gk of the segment lives in
+        // buffer (gk / kEmitRun) & 1; claims are handed out in entry order
+        uint32_t gk = lane, next = 32, q = 0, cur = 0;
+        uint32_t res_cur = 0, res_next = 0;   // resolved entries of runs r, r+1
+        bool active = false;
+        QRecip c{0, 0, 0, 0};
+        for (uint32_t r = 0; r < runs; ++r) {
+            const uint32_t n_r = (total - r * kEmitRun < kEmitRun) ? total - r * kEmitRun : kEmitRun;
+            const uint32_t limit = (total - r * kEmitRun < 2 * kEmitRun) ? total
+                                                                        : (r + 2) * kEmitRun;
+            const uint32_t r_end = r * kEmitRun + n_r;
+            if (!active && gk < limit) {      // a claim in the newly ranked run
+                active = true;
+                q = ws.qs[(gk / kEmitRun) & 1][gk % kEmitRun];
+                cur = (uint32_t)ws.item[(gk / kEmitRun) & 1][gk % kEmitRun];
                 c = recip[q];
             }
-            while (__any_sync(0xFFFFFFFFu, active)) {
+            while (res_cur < n_r) {
                 uint32_t v;
                 const bool done = t_link32(cur, q, c, g, v) && active;
-                if (done) ws.item[k] = v;
+                if (done) ws.item[(gk / kEmitRun) & 1][gk % kEmitRun] = v;
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+                const uint32_t dr = __ballot_sync(0xFFFFFFFFu, done && gk < r_end);
+                res_cur += __popc(dr);
+                res_next += __popc(dm & ~dr);
                 if (done) {
-                    k = next + __popc(dm & lt);
-                    active = k < n;
+                    gk = next + __popc(dm & lt);
+                    active = gk < limit;
                     if (active) {
-                        q = ws.qs[k];
-                        cur = (uint32_t)ws.item[k];
+                        q = ws.qs[(gk / kEmitRun) & 1][gk % kEmitRun];
+                        cur = (uint32_t)ws.item[(gk / kEmitRun) & 1][gk % kEmitRun];
                         c = recip[q];
                     }
                 }
                 next += __popc(dm);
             }
-        } else {
+            __syncwarp();
+            emit_buf(lo + (uint64_t)r * kEmitRun, n_r, ws.item[r & 1], ws.qs[r & 1]);
+            if (r + 2 < runs) {
+                rank_run(qv, ws.item[r & 1], ws.qs[r & 1]);
+                if (r + 3 < runs) load_run(r + 3, qv);
+            }
+            res_cur = res_next;
+            res_next = 0;
+        }
+    } else {
+        // one run at a time in buffer 0, 64-bit links
+        load_run(0, qv);
+        for (uint32_t r = 0; r < runs; ++r) {
+            const uint32_t n = (total - r * kEmitRun < kEmitRun) ? total - r * kEmitRun : kEmitRun;
+            rank_run(qv, ws.item[0], ws.qs[0]);
+            if (r + 1 < runs) load_run(r + 1, qv);
             uint32_t k = lane, next = 32, q = 0xFFFFu;
             bool active = true, fresh = true;
             CurT cur = 0;
@@ -650,8 +691,8 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             qd.d = FastDiv{0, 0, 0};
             while (__any_sync(0xFFFFFFFFu, active)) {
                 if (active && fresh) {
-                    q = ws.qs[k];
-                    cur = ws.item[k];
+                    q = ws.qs[0][k];
+                    cur = ws.item[0][k];
                     if (q != 0xFFFFu) {
                         qd.R = R[q];
                         qd.d = divR[q];
@@ -665,7 +706,7 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                 uint64_t c64 = cur;
                 if (live) fin = t_step(c64, q, qd, g, v);
                 cur = c64;
-                if (fin) ws.item[k] = v;
+                if (fin) ws.item[0][k] = v;
                 const bool done = active && (fin || !live);
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
                 if (done) {
@@ -675,14 +716,9 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                 }
                 next += __popc(dm);
             }
+            __syncwarp();
+            emit_buf(lo + (uint64_t)r * kEmitRun, n, ws.item[0], ws.qs[0]);
         }
-        __syncwarp();
-        auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
-            s_ = src_base + fdiv32((uint32_t)(base + t2), g.div_m32);
-            d_ = (uint64_t)ws.qs[t2] * g.span + (uint32_t)ws.item[t2];
-        };
-        emit_run(out, out_block + g.e0 + base, n, lane, edge_at);
-        __syncwarp();
     }
 }
 
