@@ -634,7 +634,6 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
         // pooled chains over the segment: entry gk of the segment lives in
         // buffer (gk / kEmitRun) & 1; claims are handed out in entry order
         uint32_t gk = lane, next = 32, q = 0, cur = 0;
-        uint32_t res_cur = 0, res_next = 0;   // resolved entries of runs r, r+1
         bool active = false;
         QRecip c{0, 0, 0, 0};
         for (uint32_t r = 0; r < runs; ++r) {
@@ -648,14 +647,13 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                 cur = (uint32_t)ws.item[(gk / kEmitRun) & 1][gk % kEmitRun];
                 c = recip[q];
             }
-            while (res_cur < n_r) {
+            // run r is resolved once every entry before r_end has been claimed
+            // (claims go in entry order) and no active lane still holds one
+            while (next < r_end || __any_sync(0xFFFFFFFFu, active && gk < r_end)) {
                 uint32_t v;
                 const bool done = t_link32(cur, q, c, g, v) && active;
                 if (done) ws.item[(gk / kEmitRun) & 1][gk % kEmitRun] = v;
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
-                const uint32_t dr = __ballot_sync(0xFFFFFFFFu, done && gk < r_end);
-                res_cur += __popc(dr);
-                res_next += __popc(dm & ~dr);
                 if (done) {
                     gk = next + __popc(dm & lt);
                     active = gk < limit;
@@ -673,8 +671,6 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                 rank_run(qv, ws.item[r & 1], ws.qs[r & 1]);
                 if (r + 3 < runs) load_run(r + 3, qv);
             }
-            res_cur = res_next;
-            res_next = 0;
         }
     } else {
         // one run at a time in buffer 0, 64-bit links
