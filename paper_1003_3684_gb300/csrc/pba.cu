@@ -8,8 +8,12 @@
 //                shared memory level by level: entries [L, 2L) copy from
 //                [0, L) (already final) or follow their own chain inside
 //                [L, 2L). Writes A_p[0, P) and counts it.
-//   pba_pass     phase 1, one doubling level [L, min(2L, N_e)) of every block
-//                per launch. Entry j draws once (Philox, counter (j, p, 1)):
+//   pba_pass     phase 1, one level [L, hi) of every block per launch, with
+//                hi = L + L/kLevelDiv rounded up to whole granules (levels
+//                grow 1.5x: more copies land in the finished part than with
+//                doubling, so fewer chain links, and few enough launches that
+//                their partial last waves stay cheap). Entry j draws once
+//                (Philox, counter (j, p, 1)):
 //                an inter-faction pick, or a copy of entry r < j. A copy with
 //                r < L reads the finished A_p[r] from global memory (the
 //                grid is block-major, so the few blocks in flight keep their
@@ -50,6 +54,7 @@ constexpr uint32_t kPassRun = 1024;             // entries per warp run in a pas
 constexpr uint32_t kPassChunk = (kPassThreads / 32) * kPassRun;   // 16384 per CTA
 constexpr int kEmitWarps = 8;
 constexpr int kEmitThreads = kEmitWarps * 32;
+constexpr uint64_t kLevelDiv = 2;   // phase-1 level [L, L + L/kLevelDiv)
 constexpr int kEmitItems = 8;
 constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 256 entries per warp run
 constexpr uint32_t kMaxBlocks = 1024;
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Phase 1, one doubling level [L, hi) of every block; grid = (chunks, B),
+// Phase 1, one level [L, hi) of every block; grid = (chunks, B),
 // chunk c = [L + c*kPassChunk, ...). dynamic smem = B*4 (histogram) + one
 // staged run of kPassRun entries per warp.
 // A copy that lands below L loads A_p[r]; the load is consumed one loop trip
@@ -927,7 +932,9 @@ cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         TraceScope trace("pba_phase1", s);
         for (uint64_t lvl = g.P; lvl < g.N_e;) {
-            const uint64_t hi = (2 * lvl < g.N_e) ? 2 * lvl : g.N_e;
+            // level [lvl, hi): lvl / kLevelDiv more entries, in whole granules
+            const uint64_t grow = (lvl / kLevelDiv + kPassChunk - 1) / kPassChunk * kPassChunk;
+            const uint64_t hi = (lvl + grow < g.N_e) ? lvl + grow : g.N_e;
             const uint32_t chunks = (uint32_t)((hi - lvl + kPassChunk - 1) / kPassChunk);
             const size_t smem = (((size_t)g.B * 4 + 15) & ~(size_t)15) +
                                 (size_t)(kPassThreads / 32) * kPassRun * 2;
