@@ -120,6 +120,8 @@ PBA_CASES = [
     (16, 2**14, 5, 1, 0.1, 6, 5),      # n_b a power of two: shift instead of division
     (4, 5_000, 3, 1, 0.2, 40, 8),      # 780 seed edges: long seed-endpoint walks
     (8, 3_000, 48, 2, 0.25, 49, 21),   # many edges per vertex
+    (4, 3_329, 5, 1, 0.1, 6, 31),      # 16,645 entries: a last segment of one run + 5 entries
+    (9, 5, 5, 1, 0.3, 6, 4),           # 25 entries per block: fewer than a warp's lanes
 ]
 
 
