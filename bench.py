@@ -33,16 +33,20 @@ DEFAULT_WORKLOAD = "pba_n2p30_b1024_m5"
 # Algorithmic work per unit (32-bit lane operations and bytes), per kernel.
 # A Philox4x32-10 call is 60 lane ops (10 rounds of two 32x32->64 multiplies,
 # counted as two ops each, and two three-input XORs); a 64-bit uniform draw
-# adds 4. Chain links recomputed beyond the first draw of a unit are NOT
-# counted: they are the implementation's overhead, not the method's work.
+# adds 4. Where a kernel's counters keep words 1..3 fixed (phase 1's (j, 0, p, 1),
+# the serial method's (i, 0, 0, 2)), two of the twenty multiplies are done once
+# per fixed prefix, so such a draw counts 56. Chain links recomputed beyond the
+# first draw of a unit are NOT counted: they are the implementation's overhead,
+# not the method's work.
 PHILOX_OPS = 60
+PHILOX_HEADED_OPS = 56
 KERNEL_WORK = {
     # unit = one phase-1 entry: its own draw (coin + uniform index) + select
-    "pba_phase1": dict(ops=PHILOX_OPS + 4 + 6, bytes=2),
+    "pba_phase1": dict(ops=PHILOX_HEADED_OPS + 4 + 6, bytes=2),
     # unit = one edge: its endpoint draw + uniform + sigma/E index arithmetic
     # and the rank bookkeeping; bytes = the (src, dst) pair written
     "pba_emit": dict(ops=PHILOX_OPS + 4 + 16, bytes=8),
-    "ba_chain": dict(ops=PHILOX_OPS + 4 + 16, bytes=8),
+    "ba_chain": dict(ops=PHILOX_HEADED_OPS + 4 + 16, bytes=8),
 }
 
 

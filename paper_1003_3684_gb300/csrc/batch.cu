@@ -81,10 +81,10 @@ __device__ __forceinline__ void put_two(Id* out, uint64_t e, uint64_t s0, uint64
 
 // One serial-BA link with 32-bit indices (as in the single-graph kernel).
 __device__ __forceinline__ bool ba_link(uint32_t& cur, const BatchJob& J, const Key& key,
-                                        uint32_t& v)
+                                        const PhiloxHead& ph, uint32_t& v)
 {
     const uint32_t sig = fdiv32(cur, J.div_m);
-    const uint4 w = philox(make_uint4(cur, 0u, 0u, 2u), key);
+    const uint4 w = philox_headed(cur, ph, key);   // counter (cur, 0, 0, 2)
     const uint32_t X = (uint32_t)J.e0 + sig * J.m;
     const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
     const uint32_t e = (uint32_t)(s >> 32);
@@ -227,11 +227,12 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
             uint32_t next = 32, item = lane;
             uint32_t cur = (uint32_t)(t0 + r0 + item);
             bool active = item < n_items_w;
+            const PhiloxHead ph = philox_head(0u, 0u, 2u, key);
             while (__any_sync(0xFFFFFFFFu, active)) {
                 bool done = false;
                 if (active) {
                     uint32_t v;
-                    done = ba_link(cur, J, key, v);
+                    done = ba_link(cur, J, key, ph, v);
                     if (done) sDst[r0 + item] = (Id)v;
                 }
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((g.P * 2 + 15) & ~15u));
     const uint32_t p = blockIdx.x;
     const Faction<kTable> F(g, p);
+    const PhiloxHead ph = philox_head(0u, p, 1u, g.key);   // counters (j, 0, p, 1)
     const uint32_t P = g.P;
     const uint32_t s = F.s < P ? F.s : P;
     for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) sA[t] = (uint16_t)F.member(t);
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
         for (uint32_t j = L + threadIdx.x; j < hi; j += blockDim.x) {
             uint32_t cur = j, v;
             for (;;) {
-                const uint4 w = philox(make_uint4(cur, 0u, p, 1u), g.key);
+                const uint4 w = philox_headed(cur, ph, g.key);
                 if (F.coin && w.z < g.coin_thr) {
                     v = F.fresh(w.w, g);
                     break;
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const Faction<kTable> F(g, p);
+    const PhiloxHead ph = philox_head(0u, p, 1u, g.key);   // counters (j, 0, p, 1)
     uint16_t* Ap = A + (uint64_t)p * g.A_stride;
     uint16_t* my = stage + wid * kPassRun;              // this warp's run, staged
     const uint32_t chunk = L + blockIdx.x * kPassChunk;   // a granule: one segment
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     while (__any_sync(0xFFFFFFFFu, active || pend)) {
         // every lane draws (an idle lane's draw is discarded), so the trip is
         // straight-line code apart from the deferred store
-        const uint4 w = philox(make_uint4(cur, 0u, p, 1u), g.key);
+        const uint4 w = philox_headed(cur, ph, g.key);
         if (pend) my[pend_k] = (uint16_t)pend_v;   // the value loaded one trip ago
         const bool coin = coin_on && w.z < g.coin_thr;
         const uint32_t r = uniform32(w.x, w.y, cur);
@@ -433,10 +435,11 @@ __device__ __forceinline__ bool ba_step(uint64_t& cur, const PbaGeom& g, uint64_
 }
 
 // 32-bit serial BA link (n*m + e0 < 2^32).
-__device__ __forceinline__ bool ba_step32(uint32_t& cur, const PbaGeom& g, uint32_t& v)
+__device__ __forceinline__ bool ba_step32(uint32_t& cur, const PbaGeom& g, const PhiloxHead& ph,
+                                          uint32_t& v)
 {
     const uint32_t sig = fdiv32(cur, g.div_m32);
-    const uint4 w = philox(make_uint4(cur, 0u, 0u, 2u), g.key);
+    const uint4 w = philox_headed(cur, ph, g.key);   // counter (cur, 0, 0, 2)
     const uint32_t X = (uint32_t)g.e0 + sig * g.m;
     const uint64_t hi = (uint64_t)w.y * X, lo = (uint64_t)w.x * X;
     const uint64_t r = (hi + (lo >> 32)) >> 31;
@@ -738,6 +741,7 @@ __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ 
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t N = g.N_e;
+    const PhiloxHead ph = philox_head(0u, 0u, 2u, g.key);
     for (uint64_t base = (uint64_t)blockIdx.x * kBaTile; base < N;
          base += (uint64_t)gridDim.x * kBaTile) {
         const uint64_t run = base + wid * kBaRun;
@@ -751,7 +755,7 @@ __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ 
             if (active) {
                 if (kFast) {
                     uint32_t v;
-                    done = ba_step32(cur32, g, v);
+                    done = ba_step32(cur32, g, ph, v);
                     if (done) sDst[wid * kBaRun + item] = (Id)v;
                 } else {
                     uint64_t v;
