@@ -9,25 +9,27 @@
 // marks each row's end in row_ptr.
 //
 // Any other list: least-significant-digit radix sort of the (src, dst) keys,
-// first the digits of dst, then those of src, up to 10 bits per pass. Each
-// pass is three kernels:
-//   radix_hist     per-tile digit counts, stored digit-major H[d][tile];
-//   scan_rows      per digit, the exclusive scan of its counts over tiles,
-//                  and (by the last CTA to finish) the scan of the digit
-//                  totals: together, where each tile's run of each digit
-//                  starts in the output;
-//   radix_scatter  stable rank of each element within its tile among equal
-//                  digits (warp match + per-warp counters + cross-warp scan)
-//                  and a scattered write of the (src, dst) pair.
-// No atomics decide any position, so the result does not depend on the
-// schedule, and a power-law row (a hub with 10^5 edges) costs no more than
-// any other key. A final pass writes col and marks row ends. Both paths then
-// take a parallel prefix maximum over row_ptr, which fills the rows without
-// edges. The sort kernels read the sortedness flag and return at once when
-// the grouped path applied, so no host round trip decides the path.
+// first the digits of dst, then those of src, up to 10 bits per pass:
+//   radix_hist_all one read of the list counts the digits of every pass
+//                  (the totals do not depend on the order a pass leaves);
+//   radix_dstart   per pass, where each digit's run starts in the output;
+//   radix_scatter  per pass: stable rank of each element within its tile
+//                  among equal digits (warp match + per-warp counters +
+//                  cross-warp scan), a reorder in shared memory, the tile's
+//                  start in each digit's run by decoupled look-back over the
+//                  earlier tiles' published counts, and coalesced writes.
+// Ranks come from counts in entry order, never from atomics racing for a
+// slot, so the result does not depend on the schedule, and a power-law row
+// (a hub with 10^5 edges) costs no more than any other key. A final pass
+// writes col and marks row ends. Both paths then take a parallel prefix
+// maximum over row_ptr, which fills the rows without edges. The sort kernels
+// read the sortedness flag and return at once when the grouped path applied,
+// so no host round trip decides the path.
 //
 // Ids at or above n_vertices are never used as an index (such edges are
 // dropped), so a bad list cannot make a kernel write out of bounds.
+#include <cstring>
+
 #include "pg_internal.h"
 #include "pg_trace.h"
 
@@ -66,55 +68,74 @@ struct SortShape {
     static constexpr uint32_t tile = kSortThreads * items;
 };
 
-// Per-tile digit counts. Each warp counts into its own shared-memory
-// histogram with plain atomic increments (no cross-warp contention; a skewed
-// digit only meets the other lanes of its warp), then the warps' counts are
-// summed per digit. Dynamic shared memory: kSortWarps << bits counters.
+// The digits of every LSD pass, from the host: pass k sorts by `bits[k]`
+// bits of the source (field 1) or destination (field 0) at `shift[k]`.
+constexpr int kMaxPasses = 14;   // 64-bit ids: up to 7 digits per field
+struct PassList {
+    uint32_t n;
+    int field[kMaxPasses], shift[kMaxPasses], bits[kMaxPasses];
+};
+// Digit totals of every pass in one read of the list: tot[k][d] = number of
+// pairs whose pass-k digit is d. Each CTA counts into shared memory
+// (n passes x kMaxBuckets) and adds its counts once.
 template <typename Id>
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(
-    const typename PairOf<Id>::T* __restrict__ in, uint64_t M, int field, int shift, int bits,
-    uint32_t* __restrict__ H, uint32_t n_tiles, const uint32_t* __restrict__ sort_needed)
+__global__ void __launch_bounds__(256) radix_hist_all_kernel(
+    const typename PairOf<Id>::T* __restrict__ in, uint64_t M, const __grid_constant__ PassList pl,
+    unsigned long long* __restrict__ tot, const uint32_t* __restrict__ sort_needed)
 {
-    extern __shared__ uint32_t wh[];
+    extern __shared__ uint32_t h[];
     if (*sort_needed == 0) return;
-    const uint32_t nb = 1u << bits, mask = nb - 1;
-    const uint32_t wid = threadIdx.x >> 5;
-    for (uint32_t t = threadIdx.x; t < kSortWarps * nb; t += blockDim.x) wh[t] = 0;
+    const uint32_t cells = pl.n * kMaxBuckets;
+    for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x) h[t] = 0;
     __syncthreads();
-    constexpr uint32_t kTile = SortShape<Id>::tile;
-    const uint64_t base = (uint64_t)blockIdx.x * kTile;
-    const uint64_t end = (base + kTile < M) ? base + kTile : M;
-    uint32_t* mine = wh + wid * nb;
-    constexpr int kUnroll = 4;
-    for (uint64_t i0 = base + threadIdx.x; i0 < end; i0 += (uint64_t)kUnroll * blockDim.x) {
-        uint32_t d[kUnroll];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    constexpr int kU = 4;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += kU * stride) {
+        typename PairOf<Id>::T e[kU];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const uint64_t i = i0 + (uint64_t)u * blockDim.x;
-            d[u] = (i < end) ? digit_of(in[i], field, shift, mask) : 0xFFFFFFFFu;
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * stride < M) e[u] = in[i0 + u * stride];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (i0 + u * stride >= M) continue;
+            for (uint32_t k = 0; k < pl.n; ++k)
+                atomicAdd(&h[k * kMaxBuckets +
+                             digit_of(e[u], pl.field[k], pl.shift[k], (1u << pl.bits[k]) - 1)], 1u);
         }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (d[u] != 0xFFFFFFFFu) atomicAdd(&mine[d[u]], 1u);
     }
     __syncthreads();
-    for (uint32_t dd = threadIdx.x; dd < nb; dd += blockDim.x) {
-        uint32_t sum = 0;
-#pragma unroll 4
-        for (int w = 0; w < kSortWarps; ++w) sum += wh[w * nb + dd];
-        H[(uint64_t)dd * n_tiles + blockIdx.x] = sum;
-    }
+    for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x)
+        if (h[t]) atomicAdd(&tot[t], (unsigned long long)h[t]);
 }
+
+// Tile status words, one per (tile, digit): bits 63..60 the pass (1 + its
+// index, so the words of an earlier pass read as not ready), bits 59..58 the
+// kind, a pair count below. kAgg: the tile's own count of the digit; kInc: the
+// count of the digit in this tile and every earlier one. The array is zeroed
+// once per call.
+constexpr unsigned long long kAgg = 1ull << 58, kInc = 2ull << 58;
+constexpr unsigned long long kCountMask = (1ull << 58) - 1;
+constexpr uint32_t kSpinLimit = 1u << 18;   // polls of one status word
+constexpr int kLookWindow = 8;              // earlier tiles read per round trip
 
 // One LSD pass over a tile: load once, rank stably (per warp by match, then
 // across warps), reorder the tile by digit in shared memory, and write each
 // digit's run to its place in the output with consecutive threads on
-// consecutive elements.
+// consecutive elements. Where a tile's run of digit d starts is dstart[d]
+// (from the pass's digit totals) plus the count of d in earlier tiles, found
+// by decoupled look-back over the status words. A CTA takes its tile index
+// from a ticket, so every earlier tile belongs to a CTA already running or
+// done. It publishes its own counts before it waits on anything, and it sums
+// earlier tiles' counts, kLookWindow at a time, until it meets an inclusive
+// one. The look-back runs after the reorder, when the tile's pairs no longer
+// occupy registers. Every poll loop is bounded: after kSpinLimit polls of
+// one word it sets *err and goes on.
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const typename PairOf<Id>::T* __restrict__ in, typename PairOf<Id>::T* __restrict__ out,
-    uint64_t M, int field, int shift, int bits, const uint64_t* __restrict__ Hs,
-    const uint64_t* __restrict__ dstart, uint32_t n_tiles, const uint32_t* __restrict__ sort_needed)
+    uint64_t M, int field, int shift, int bits, unsigned long long* __restrict__ status,
+    uint32_t pass, const uint64_t* __restrict__ dstart, uint32_t* __restrict__ ticket,
+    uint32_t* __restrict__ err, const uint32_t* __restrict__ sort_needed)
 {
     using P = typename PairOf<Id>::T;
     constexpr int kItems = SortShape<Id>::items;
@@ -125,14 +146,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     uint32_t* loff = reinterpret_cast<uint32_t*>(tbase + kMaxBuckets);                  // 4 KB
     P* buf = reinterpret_cast<P*>(loff + kMaxBuckets);                                  // tile
     __shared__ uint32_t s_part[kSortWarps + 1];
+    __shared__ uint32_t s_tile;
     if (*sort_needed == 0) return;
     const uint32_t nb = 1u << bits, mask = nb - 1;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t tile = blockIdx.x;
-    for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x)
         for (int w = 0; w < kSortWarps; ++w) wcnt[w][d] = 0;
-        tbase[d] = dstart[d] + Hs[(uint64_t)d * n_tiles + tile];
-    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
     const uint64_t tile0 = (uint64_t)tile * kTile;
     const uint32_t n = (uint32_t)((M - tile0 < kTile) ? M - tile0 : kTile);
     const uint32_t wbase = wid * (32 * kItems);
@@ -169,7 +191,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
         else rk[r >> 1] = rank;
     }
     __syncthreads();
-    // per digit: prefix over warps (in wcnt) and the tile total (in loff)
+    // per digit: prefix over warps (in wcnt) and the tile total (in loff),
+    // published at once so that later tiles can sum it
+    const unsigned long long tag = (unsigned long long)(pass + 1) << 60;
+    volatile unsigned long long* st = status + (uint64_t)tile * nb;
     for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) {
         uint32_t acc = 0;
 #pragma unroll
@@ -179,6 +204,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
             acc += c;
         }
         loff[d] = acc;
+        st[d] = tag | (tile == 0 ? kInc : kAgg) | acc;
     }
     __syncthreads();
     // exclusive scan of the tile totals over digits (each thread a run of digits)
@@ -222,6 +248,53 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
             const uint32_t rank = (rk[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
             buf[loff[d] + wcnt[wid][d] + rank] = e[r];
         }
+    }
+    // look back through up to kLookWindow earlier tiles per round trip
+    for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) {
+        unsigned long long excl = 0;
+        if (tile > 0) {
+            uint32_t next = tile - 1;   // nearest tile not yet summed (tile 0 is inclusive)
+            uint32_t polls = 0;
+            bool found = false;
+            while (!found) {
+                unsigned long long w[kLookWindow];
+#pragma unroll
+                for (int u = 0; u < kLookWindow; ++u)
+                    w[u] = (next >= (uint32_t)u)
+                               ? *((volatile const unsigned long long*)status +
+                                   (uint64_t)(next - u) * nb + d)
+                               : 0ull;
+                int used = 0;
+                bool stalled = false;
+#pragma unroll
+                for (int u = 0; u < kLookWindow; ++u) {
+                    if (found || stalled) continue;
+                    const unsigned long long flag =
+                        (w[u] >> 60) == pass + 1 ? w[u] & (3ull << 58) : 0;
+                    if (flag == 0) {
+                        stalled = true;
+                        continue;
+                    }
+                    excl += w[u] & kCountMask;
+                    ++used;
+                    if (flag == kInc) found = true;
+                }
+                if (found) break;
+                next -= used;
+                if (stalled) {
+                    if (++polls > kSpinLimit) {
+                        atomicOr(err, 1u);
+                        break;
+                    }
+                    __nanosleep(32);
+                } else {
+                    polls = 0;
+                }
+            }
+            const uint32_t cnt_d = (d + 1 < nb ? loff[d + 1] : n) - loff[d];
+            st[d] = tag | kInc | (excl + cnt_d);
+        }
+        tbase[d] = dstart[d] + excl;
     }
     __syncthreads();
     // write runs: sorted position p goes to tbase[d] + (p - loff[d])
@@ -269,73 +342,28 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* s
     return before + x - v;
 }
 
-// Offsets of one LSD pass in one launch. H is digit-major: n_tiles counts
-// per digit. CTA d scans its row into Hs[d][t] = sum of H[d][t'] over t' < t
-// and writes the row total to tot[d]. The CTA that finishes last (it draws the
-// last ticket; no CTA waits on another) scans the totals into dstart[d], the
-// first output position of digit d, and puts the ticket back to zero. The
-// scatter adds dstart[d] and Hs[d][t].
-constexpr uint32_t kRowPer = 4;
-__global__ void __launch_bounds__(1024) scan_rows_kernel(const uint32_t* __restrict__ H,
-                                                         uint32_t n_tiles, uint32_t nb,
-                                                         uint64_t* __restrict__ Hs,
-                                                         uint64_t* __restrict__ tot,
-                                                         uint64_t* __restrict__ dstart,
-                                                         uint32_t* __restrict__ ticket,
-                                                         const uint32_t* __restrict__ sort_needed)
+// Zeroes the tile status words once per call (nothing when no sort runs).
+__global__ void __launch_bounds__(256) zero_status_kernel(uint4* __restrict__ p, uint64_t n16,
+                                                          const uint32_t* __restrict__ sort_needed)
+{
+    if (*sort_needed == 0) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+        p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+// Where each digit's run starts in pass k's output: the exclusive scan of
+// that pass's digit totals. grid = passes, block = kMaxBuckets threads.
+__global__ void __launch_bounds__(kMaxBuckets) radix_dstart_kernel(
+    const unsigned long long* __restrict__ tot, const __grid_constant__ PassList pl,
+    uint64_t* __restrict__ dstart, const uint32_t* __restrict__ sort_needed)
 {
     __shared__ uint64_t s_warp[32];
-    __shared__ uint32_t s_last;
     if (*sort_needed == 0) return;
-    const uint32_t d = blockIdx.x;
-    const uint32_t* row = H + (uint64_t)d * n_tiles;
-    uint64_t* out = Hs + (uint64_t)d * n_tiles;
-    uint64_t carry = 0;
-    for (uint32_t t0 = 0; t0 < n_tiles; t0 += blockDim.x * kRowPer) {
-        const uint32_t tb = t0 + threadIdx.x * kRowPer;
-        uint32_t v[kRowPer];
-        uint64_t sum = 0;
-#pragma unroll
-        for (uint32_t k = 0; k < kRowPer; ++k) {
-            v[k] = (tb + k < n_tiles) ? row[tb + k] : 0;
-            sum += v[k];
-        }
-        uint64_t total;
-        uint64_t run = carry + block_exclusive_scan(sum, s_warp, total);
-#pragma unroll
-        for (uint32_t k = 0; k < kRowPer; ++k) {
-            if (tb + k < n_tiles) out[tb + k] = run;
-            run += v[k];
-        }
-        carry += total;
-    }
-    if (threadIdx.x == 0) {
-        tot[d] = carry;
-        __threadfence();
-        s_last = (atomicAdd(ticket, 1u) == nb - 1) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (s_last == 0) return;
-    __threadfence();
-    const unsigned long long* tot_l2 = reinterpret_cast<const unsigned long long*>(tot);
-    uint64_t start = 0;
-    for (uint32_t d0 = 0; d0 < nb; d0 += blockDim.x) {
-        const uint32_t i = d0 + threadIdx.x;
-        const uint64_t c = i < nb ? (uint64_t)__ldcg(tot_l2 + i) : 0;   // not from L1
-        uint64_t total;
-        const uint64_t ex = block_exclusive_scan(c, s_warp, total);
-        if (i < nb) dstart[i] = start + ex;
-        start += total;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-}
-
-// Threads per CTA of scan_rows: enough for one trip over a row, 32 to 1024.
-uint32_t scan_rows_threads(uint32_t n_tiles)
-{
-    const uint32_t want = (n_tiles + kRowPer - 1) / kRowPer;
-    const uint32_t t = (want + 31) & ~31u;
-    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+    const uint32_t k = blockIdx.x, nb = 1u << pl.bits[k], d = threadIdx.x;
+    const uint64_t c = d < nb ? tot[(size_t)k * kMaxBuckets + d] : 0;
+    uint64_t total;
+    const uint64_t ex = block_exclusive_scan(c, s_warp, total);
+    if (d < nb) dstart[(size_t)k * kMaxBuckets + d] = ex;
 }
 
 // exclusive scan of n_parts sums in place, one CTA looping over chunks
@@ -661,9 +689,9 @@ int bit_length(uint64_t x)
 }
 
 struct CsrLayout {
-    size_t off_a, off_b, off_h, off_hs, off_flag, off_dig, off_rpart, total;
+    size_t off_a, off_b, off_status, off_flag, off_dig, off_rpart, total;
     uint32_t n_tiles, max_nb;
-    uint64_t n_h, n_rparts;
+    uint64_t n_status, n_rparts;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -677,20 +705,18 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
     const uint32_t tile = pair_bytes == 8 ? SortShape<uint32_t>::tile : SortShape<uint64_t>::tile;
     L.max_nb = 1u << dbits;
     L.n_tiles = (uint32_t)((M + tile - 1) / tile);
-    L.n_h = (uint64_t)L.max_nb * L.n_tiles;
+    L.n_status = (uint64_t)L.max_nb * L.n_tiles;
     size_t o = 0;
     L.off_a = o;
     o += a256(M * pair_bytes);
     L.off_b = o;
     o += a256(M * pair_bytes);
-    L.off_h = o;
-    o += a256(L.n_h * 4);
-    L.off_hs = o;
-    o += a256(L.n_h * 8);
-    L.off_flag = o;   // +0: sort-needed flag, +64: the row scan's ticket
+    L.off_status = o;   // tile status words of the pass being sorted
+    o += a256(L.n_status * 8);
+    L.off_flag = o;     // +0: sort-needed flag, +64: one ticket per pass, +128: look-back error
     o += 256;
-    L.off_dig = o;    // digit totals, then digit starts (kMaxBuckets each)
-    o += a256(2 * (size_t)kMaxBuckets * 8);
+    L.off_dig = o;      // digit totals, then digit starts, of every pass
+    o += a256(2 * (size_t)kMaxPasses * kMaxBuckets * 8);
     L.n_rparts = (N + 1 + kScanTile - 1) / kScanTile;
     L.off_rpart = o;
     o += a256((L.n_rparts + 1) * 8);
@@ -705,8 +731,8 @@ void set_csr_attributes()
     if (!attr) {
         cudaFuncSetAttribute(radix_scatter_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scatter_smem_bytes<Id>());
-        cudaFuncSetAttribute(radix_hist_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSortWarps * 4 * kMaxBuckets));
+        cudaFuncSetAttribute(radix_hist_all_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kMaxPasses * 4 * kMaxBuckets));
         attr = true;
     }
 }
@@ -714,6 +740,8 @@ void set_csr_attributes()
 // LSD radix passes over M pairs starting at `in` (dst digits, then src
 // digits). *sorted receives the sorted list (in itself when there is no
 // digit to sort), *spare a ping-pong buffer the result does not occupy.
+int sort_grid(uint64_t work);
+
 template <typename Id>
 cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t N, const CsrLayout& L,
                          unsigned char* ws, const uint32_t* sort_needed, cudaStream_t s,
@@ -721,47 +749,56 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
 {
     using P = typename PairOf<Id>::T;
     P* buf[2] = {(P*)(ws + L.off_a), (P*)(ws + L.off_b)};
-    uint32_t* H = (uint32_t*)(ws + L.off_h);
-    uint64_t* Hs = (uint64_t*)(ws + L.off_hs);
-    uint64_t* tot = (uint64_t*)(ws + L.off_dig);
-    uint64_t* dstart = tot + kMaxBuckets;
-    uint32_t* ticket = (uint32_t*)(ws + L.off_flag + 64);
-    cudaError_t err;
-    if (cudaMemsetAsync(ticket, 0, 4, s) != cudaSuccess) return cudaErrorUnknown;
+    unsigned long long* status = (unsigned long long*)(ws + L.off_status);
+    unsigned long long* tot = (unsigned long long*)(ws + L.off_dig);
+    uint64_t* dstart = (uint64_t*)(ws + L.off_dig) + (size_t)kMaxPasses * kMaxBuckets;
+    uint32_t* tickets = (uint32_t*)(ws + L.off_flag + 64);
+    uint32_t* err = (uint32_t*)(ws + L.off_flag + 128);
+    // the passes: dst digits, then src digits, at most kMaxDigitBits each
     const int bits = bit_length(N > 0 ? N - 1 : 0);
-    const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    const int per_field = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    PassList pl;
+    std::memset(&pl, 0, sizeof(pl));
+    for (int field = 0; field < 2; ++field) {
+        int shift = 0;
+        for (int ps = 0; ps < per_field; ++ps) {
+            const int b = (bits - shift < (bits + per_field - 1) / per_field)
+                              ? bits - shift
+                              : (bits + per_field - 1) / per_field;
+            if (b <= 0) break;
+            pl.field[pl.n] = field;
+            pl.shift[pl.n] = shift;
+            pl.bits[pl.n] = b;
+            ++pl.n;
+            shift += b;
+        }
+    }
     const P* cur = in;
     int which = 0;
-    if (M > 0) {
-        for (int field = 0; field < 2; ++field) {      // dst digits, then src digits
-            int shift = 0;
-            for (int ps = 0; ps < passes; ++ps) {
-                const int b = (bits - shift < (bits + passes - 1) / passes)
-                                  ? bits - shift
-                                  : (bits + passes - 1) / passes;
-                if (b <= 0) break;
-                {
-                    TraceScope trace("csr_radix_hist", s);
-                    radix_hist_kernel<Id><<<L.n_tiles, kSortThreads,
-                                            (size_t)kSortWarps * 4 << b, s>>>(
-                        cur, M, field, shift, b, H, L.n_tiles, sort_needed);
-                }
-                {
-                    TraceScope trace("csr_scan", s);
-                    scan_rows_kernel<<<1u << b, scan_rows_threads(L.n_tiles), 0, s>>>(
-                        H, L.n_tiles, 1u << b, Hs, tot, dstart, ticket, sort_needed);
-                }
-                {
-                    TraceScope trace("csr_radix_scatter", s);
-                    radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
-                        cur, buf[which], M, field, shift, b, Hs, dstart, L.n_tiles,
-                        sort_needed);
-                }
-                if ((err = cudaGetLastError()) != cudaSuccess) return err;
-                cur = buf[which];
-                which ^= 1;
-                shift += b;
-            }
+    cudaError_t err_c;
+    if (M > 0 && pl.n > 0) {
+        if (cudaMemsetAsync(ws + L.off_flag + 64, 0, 128, s) != cudaSuccess) return cudaErrorUnknown;
+        if (cudaMemsetAsync(tot, 0, (size_t)pl.n * kMaxBuckets * 8, s) != cudaSuccess)
+            return cudaErrorUnknown;
+        {
+            TraceScope trace("csr_radix_hist", s);
+            zero_status_kernel<<<sort_grid(L.n_status / 2 + 1), 256, 0, s>>>(
+                (uint4*)status, (L.n_status * 8 + 15) / 16, sort_needed);
+            radix_hist_all_kernel<Id><<<sort_grid(M), 256, (size_t)pl.n * kMaxBuckets * 4, s>>>(
+                cur, M, pl, tot, sort_needed);
+        }
+        {
+            TraceScope trace("csr_scan", s);
+            radix_dstart_kernel<<<pl.n, kMaxBuckets, 0, s>>>(tot, pl, dstart, sort_needed);
+        }
+        for (uint32_t k = 0; k < pl.n; ++k) {
+            TraceScope trace("csr_radix_scatter", s);
+            radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
+                cur, buf[which], M, pl.field[k], pl.shift[k], pl.bits[k], status, k,
+                dstart + (size_t)k * kMaxBuckets, tickets + k, err, sort_needed);
+            if ((err_c = cudaGetLastError()) != cudaSuccess) return err_c;
+            cur = buf[which];
+            which ^= 1;
         }
     }
     *sorted = cur;
