@@ -280,7 +280,8 @@ pg_status gen_kronecker_range(const double* h_initiator, uint32_t n0, uint32_t k
  *              ascending within each row (duplicates kept). The result does
  *              not depend on scheduling.
  * d_ws         workspace of pg_csr_workspace_size() bytes, 256-byte aligned
- *              (two copies of the list plus per-tile digit counts).
+ *              (two copies of the list plus a status word per tile and
+ *              digit).
  * Every id must be < n_vertices (the generators above always satisfy it).
  * The device does not report a violation, but it never indexes memory with
  * such an id: an edge whose src is out of range is dropped, and the rows
