@@ -45,15 +45,16 @@ __device__ __forceinline__ uint4 philox(uint4 c, const Key& key)
 }
 
 // Philox4x32-10 for counters (x0, x1, x2, x3) whose words 1..3 stay fixed
-// over many calls (a block's phase-1 entries, a target's list, a level group).
-// In round 1 the product of word 2 depends only on the fixed words, and so
-// does round 2's product of word 0; PhiloxHead holds what those two products
-// contribute, so a call does 18 of the 20 multiplies. Same output as philox().
+// over many calls (a block's phase-1 entries, the serial method's copy draws).
+// In the first round the product of word 2 depends only on the fixed words,
+// and so does the second round's product of word 0; PhiloxHead holds what
+// those two products contribute, so a call does 18 of the 20 multiplies.
+// Same output as philox().
 struct PhiloxHead {
-    uint32_t f2;   // x3 ^ k1[0]: XORed into word 2 after round 1
-    uint32_t f3;   // lo(M1 x2) ^ k0[1]: XORed into word 0 after round 2
-    uint32_t f4;   // hi(M0 w0) ^ k1[1], w0 = hi(M1 x2) ^ x1 ^ k0[0]: into word 2 after round 2
-    uint32_t f5;   // lo(M0 w0): word 3 after round 2
+    uint32_t f2;   // x3 ^ k1[0]: XORed into word 2 after the first round
+    uint32_t f3;   // lo(M1 x2) ^ k0[1]: XORed into word 0 after the second round
+    uint32_t f4;   // hi(M0 w0) ^ k1[1], w0 = hi(M1 x2) ^ x1 ^ k0[0]: into word 2, second round
+    uint32_t f5;   // lo(M0 w0): word 3 after the second round
 };
 
 __host__ __device__ __forceinline__ PhiloxHead philox_head(uint32_t x1, uint32_t x2, uint32_t x3,
@@ -72,9 +73,9 @@ __host__ __device__ __forceinline__ PhiloxHead philox_head(uint32_t x1, uint32_t
 
 __device__ __forceinline__ uint4 philox_headed(uint32_t x0, const PhiloxHead& h, const Key& key)
 {
-    const uint64_t p0 = (uint64_t)0xD2511F53u * x0;          // round 1, word 0
+    const uint64_t p0 = (uint64_t)0xD2511F53u * x0;          // first round, word 0
     const uint32_t y2 = (uint32_t)(p0 >> 32) ^ h.f2, y3 = (uint32_t)p0;
-    const uint64_t q1 = (uint64_t)0xCD9E8D57u * y2;          // round 2, word 2
+    const uint64_t q1 = (uint64_t)0xCD9E8D57u * y2;          // second round, word 2
     uint4 c = make_uint4((uint32_t)(q1 >> 32) ^ h.f3, (uint32_t)q1, y3 ^ h.f4, h.f5);
 #pragma unroll
     for (int r = 2; r < 10; ++r) {
