@@ -246,6 +246,46 @@ FACTION_LISTS = [[0, 1, 4, 5, 0], [0, 1, 1, 2, 3], [1, 2, 3], [1, 2, 3, 3, 4], [
                  [4, 5, 0]]
 
 
+def _received_by_target(edges, B, n_b, m, n0):
+    """Local ids each target block q handed out, requester by requester in
+    ascending block order and, within a requester, in entry order."""
+    e0, N_e, span = n0 * (n0 - 1) // 2, n_b * m, n0 + n_b
+    got = {q: [] for q in range(B)}
+    for p in range(B):
+        for dst in edges[p * (e0 + N_e) + e0:(p + 1) * (e0 + N_e), 1].astype(np.int64):
+            got[int(dst // span)].append(int(dst % span))
+    return got
+
+
+@pytest.mark.parametrize("B,W,f,seed", [(4, 1, 0.5, 13), (6, 2, 0.3, 5), (3, 1, 1.0, 8)])
+def test_pba_requesters_take_consecutive_slices_of_each_list(B, W, f, seed):
+    """Reading R4 (Sec. 3, substitution; Fig. 1(b)): q's endpoint list T_q is
+    split among its requesters in ascending block order, each consuming its
+    slice in entry order. So the endpoints that blocks 0, 1, ... received from
+    q, read in that order, are T_q from its start, with T_q computed on its
+    own by phase 2."""
+    n_b, m, n0 = 300, 3, 4
+    edges, counts, _ = o.pba(B * n_b, m, B, n0, W, f, seed)
+    R = counts.astype(np.int64).sum(axis=0)
+    got = _received_by_target(edges, B, n_b, m, n0)
+    for q in range(B):
+        assert len(got[q]) == R[q]
+        assert got[q] == [int(x) for x in o.pba_endpoints(q, int(R[q]), n_b, n0, seed)]
+    # several requesters per target, or the split would not be exercised
+    assert ((counts > 0).sum(axis=0) > 1).any()
+
+
+def test_pba_factions_requesters_take_consecutive_slices():
+    """The same split with overlapping faction lists in the manner of Fig. 1."""
+    B, n_b, m, n0, seed = 3, 200, 2, 3, 4
+    lists = [[1, 2, 0, 1], [1, 2, 1, 0], [2, 0, 1, 2]]
+    edges, counts, _ = o.pba_factions(B * n_b, m, B, n0, lists, 0.2, seed)
+    R = np.asarray(counts).astype(np.int64).sum(axis=0)
+    got = _received_by_target(edges, B, n_b, m, n0)
+    for q in range(B):
+        assert got[q] == [int(x) for x in o.pba_endpoints(q, int(R[q]), n_b, n0, seed)]
+
+
 def test_pba_factions_closure_without_inter_faction_picks():
     """f = 0: phase 1 only copies earlier entries, so block p's targets stay
     inside its own list (copies of the list itself)."""
