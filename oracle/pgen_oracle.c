@@ -29,21 +29,30 @@
  *      E(sigma(i)) = ceil(sigma(i)*R_q/n_b) edges of earlier source times.
  *  R4  q's endpoint list is split among requesters in ascending block order;
  *      each requester consumes its slice in increasing edge order.
- *  R5  factions are aligned groups of W consecutive blocks (s = W); an
- *      inter-faction draw picks uniformly among the blocks outside p's
- *      faction, with probability f per entry j >= s.
- *  R6  random draws: Philox4x32-10 (Salmon et al., SC'11) with key
+ *  R5  factions: by default aligned groups of W consecutive blocks (s = W);
+ *      general lists give block p the member lists of every faction it
+ *      belongs to, in order, and the first s_p entries of A_p copy them.
+ *  R6  inter-faction picks: each entry j >= s is, with probability f
+ *      (coin w2 < T_f, T_f = min(2^32 - 1, round_half_even(f * 2^32))), the
+ *      x-th block outside p's list in ascending order, x = floor(w3 * n_out
+ *      / 2^32); otherwise it copies a uniform earlier entry. No coin is
+ *      drawn when no block lies outside the list.
+ *  R7  random streams: Philox4x32-10 (Salmon et al., SC'11) with key
  *      (seed_lo, seed_hi) and counter (idx_lo, idx_hi, stream, tag);
  *      tag 1 = phase-1 entry, tag 2 = phase-2 local edge, tag 3 = Kronecker
- *      level group. A uniform integer in [0, R) is the high 64 bits of
- *      ((w1 << 32) | w0) * R; the coin is w2 < T_f with
- *      T_f = min(2^32 - 1, round_half_even(f * 2^32)).
- *  R7  Kronecker: thresholds T_c = round_half_even(2^32 * cum_c / S) where
+ *      level group, tag 4 = random-graph cell. A uniform integer in [0, R)
+ *      is the high 64 bits of ((w1 << 32) | w0) * R.
+ *  R8  Kronecker: thresholds T_c = round_half_even(2^32 * cum_c / S) where
  *      cum_c is the left-to-right double sum of the initiator's first c+1
  *      row-major cells and S the sum of all of them; level l (most
  *      significant first) takes word (l mod 4) of the Philox block for
  *      counter (e_lo, e_hi, l div 4, 3) and picks cell #{c : w >= T_c}.
- *  R8  CSR rows hold their destinations in ascending order.
+ *  R9  deterministic PK: a depth-first stack of meta-edges whose children
+ *      are pushed in reverse, so that they pop in seed order.
+ *  R10 CSR rows hold their destinations in ascending order, duplicates kept.
+ *  R11 PK randomisation: exclusive-or with a G(N, M) random graph drawn
+ *      with replacement; on multigraphs a cell is kept when its total
+ *      multiplicity is odd.
  */
 #include "pgen_oracle.h"
 
@@ -86,7 +95,7 @@ static void draw(uint64_t seed, uint64_t idx, uint32_t stream, uint32_t tag, uin
     or_philox4x32_10(c, k, w);
 }
 
-/* Uniform integer in [0, R): high half of the 128-bit product (R6). */
+/* Uniform integer in [0, R): high half of the 128-bit product (R7). */
 uint64_t or_uniform(uint32_t w0, uint32_t w1, uint64_t R)
 {
     unsigned __int128 x = ((unsigned __int128)(((uint64_t)w1 << 32) | w0)) * R;
@@ -392,7 +401,7 @@ int or_pba(uint64_t n, uint32_t m, uint32_t B, uint32_t n0, uint32_t W, double f
 }
 
 /* ------------------------------------------------------------------------ */
-/* Kronecker initiator quantiser (reading R7). T has n0*n0 - 1 entries,     */
+/* Kronecker initiator quantiser (reading R8). T has n0*n0 - 1 entries,     */
 /* each in [0, 2^32]. Returns 1 on a bad initiator (negative, non-finite,   */
 /* or zero sum).                                                            */
 /* ------------------------------------------------------------------------ */
@@ -414,7 +423,7 @@ int or_kron_thresholds(const double* P, uint32_t n0, uint64_t* T)
     return 0;
 }
 
-/* Cell picked by one 32-bit word: #{c : w >= T_c} (reading R7). */
+/* Cell picked by one 32-bit word: #{c : w >= T_c} (reading R8). */
 uint32_t or_kron_pick(const uint64_t* T, uint32_t n_thr, uint32_t w)
 {
     uint32_t cell = 0;
@@ -526,7 +535,7 @@ int or_kron_det(const double* P, uint32_t n0, uint32_t k, uint64_t* out, uint64_
 }
 
 /* ------------------------------------------------------------------------ */
-/* CSR of an edge list (not in the paper; reading R8): sort the (src, dst)  */
+/* CSR of an edge list (not in the paper; reading R10): sort the (src, dst) */
 /* pairs, then row_ptr[v] = number of edges with src < v.                   */
 /* ------------------------------------------------------------------------ */
 static int cmp_pair(const void* a, const void* b)

@@ -370,6 +370,26 @@ def test_pba_fresh_targets_uniform_outside_faction():
     assert stats.chisquare(obs).pvalue > 1e-4
 
 
+def test_pba_first_fresh_pick_uniform_at_small_f():
+    """With f small the inter-faction pick must still be uniform over all
+    blocks outside the factions, whatever the coin that chose it (Sec. 3).
+    With W = 1 every entry before the first fresh pick copies A[0] = p, so
+    the first entry other than p is that pick; pooled over blocks and seeds,
+    its rank among the B - 1 outside blocks is uniform."""
+    B, f = 16, 0.1
+    ranks = []
+    for seed in range(50):
+        for p in range(B):
+            A, _, _ = o.pba_phase1(p, B, 1, 300, f, seed=seed)
+            other = A[A != p]
+            assert len(other) > 0
+            q = int(other[0])
+            ranks.append(q if q < p else q - 1)
+    obs = np.bincount(ranks, minlength=B - 1)
+    assert len(obs) == B - 1
+    assert stats.chisquare(obs).pvalue > 1e-4, obs
+
+
 def test_pba_phase1_polya_urn_law():
     """W=2, f=0: a two-colour Polya urn started with one ball of each colour.
 
@@ -457,6 +477,32 @@ def test_kron_thresholds_exact_cases():
         o.kron_thresholds([[1, -1], [1, 1]])
 
 
+@pytest.mark.parametrize("Pm", [
+    [[1, 1], [1, 0]],
+    [[3, 1, 2], [1, 5, 1], [2, 2, 4]],
+    [[7, 3], [3, 1]],
+    [[1, 2, 3, 4], [5, 6, 7, 8], [9, 10, 11, 12], [13, 14, 15, 17]],
+])
+def test_kron_thresholds_round_to_nearest(Pm):
+    """Reading R8: each threshold is 2^32 times the cumulative share of the
+    cells before it, rounded to the NEAREST integer. With integer initiator
+    entries the exact value is a rational number, so the error is checked
+    exactly: at most one half (a floor or a ceiling would reach up to 1)."""
+    from fractions import Fraction
+    flat = [int(x) for row in Pm for x in row]
+    S = sum(flat)
+    T = o.kron_thresholds(Pm)
+    assert len(T) == len(flat) - 1
+    cum = 0
+    worst = Fraction(0)
+    for c in range(len(flat) - 1):
+        cum += flat[c]
+        err = abs(Fraction(int(T[c])) - Fraction(cum * 2**32, S))
+        worst = max(worst, err)
+        assert err <= Fraction(1, 2) + Fraction(1, 10**6), (c, float(err))
+    assert worst > Fraction(1, 4)      # the cases do exercise the rounding
+
+
 def test_kron_pick_boundaries():
     T = o.kron_thresholds([[0.57, 0.19], [0.19, 0.05]])
     for c, t in enumerate(T.tolist()):
@@ -495,6 +541,26 @@ def test_kron_cell_law_vs_kronecker_power(Pm, k):
     keep = exp > 0
     chi2 = ((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum()
     assert chi2 < stats.chi2.ppf(1 - 1e-4, keep.sum() - 1), chi2
+
+
+def test_kron_counter_layout():
+    """Reading R8: level l of edge e (most significant first) reads word
+    l mod 4 of the Philox block with counter (e_lo, e_hi, l div 4, 3). With
+    the 2x2 initiator [[1, 1], [1, 1]] the thresholds are 2^30, 2^31 and
+    3*2^30, so the cell of a level is the top two bits of its word: the row
+    bit is bit 31 and the column bit is bit 30."""
+    seed, k, M = 0x0F0E_0D0C_0B0A, 10, 48
+    e_list = o.kron([[1, 1], [1, 1]], k, M, seed)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for e in range(M):
+        row = col = 0
+        for g in range((k + 3) // 4):
+            w = o.philox4x32_10([e, 0, g, 3], key)
+            for t in range(4):
+                if 4 * g + t < k:
+                    row = 2 * row + (int(w[t]) >> 31)
+                    col = 2 * col + ((int(w[t]) >> 30) & 1)
+        assert (int(e_list[e, 0]), int(e_list[e, 1])) == (row, col), e
 
 
 def test_kron_row_popcount_binomial():
