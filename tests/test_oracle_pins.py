@@ -581,6 +581,29 @@ def test_kron_row_popcount_binomial():
     assert abs(p1 - 0.24) < 1e-9
 
 
+def test_kron_expected_degrees_closed_form():
+    """Expected degrees of the stochastic Kronecker model (Sec. 2, the model
+    the PK method cites): a vertex whose base-n0 digits are a_0..a_{k-1} has
+    expected out-degree M * prod_l sum_b Q[a_l][b] and expected in-degree
+    M * prod_l sum_a Q[a][a_l], for Q the quantised initiator. Checked
+    with a chi-square over all 3^7 rows and all 3^7 columns, at a depth where
+    the full Kronecker power has 4.8e6 cells."""
+    Pm = [[0.30, 0.15, 0.05], [0.10, 0.12, 0.08], [0.02, 0.08, 0.10]]
+    Q = _quantised(Pm)
+    n0, k, M = 3, 7, 600000
+    e = o.kron(Pm, k, M, seed=21).astype(np.int64)
+    digits = np.array([[(v // n0 ** (k - 1 - l)) % n0 for l in range(k)]
+                       for v in range(n0 ** k)])
+    for col, share in ((0, Q.sum(axis=1)), (1, Q.sum(axis=0))):
+        exp = M * np.prod(share[digits], axis=1)
+        assert abs(exp.sum() - M) < 1e-6 * M
+        obs = np.bincount(e[:, col], minlength=n0 ** k).astype(float)
+        assert len(obs) == n0 ** k
+        assert exp.min() > 5
+        chi2 = ((obs - exp) ** 2 / exp).sum()
+        assert chi2 < stats.chi2.ppf(1 - 1e-4, n0 ** k - 1), (col, chi2)
+
+
 def _fig2_seed(golden):
     return np.array([[float(x) for x in r] for r in golden("pk_fig2_seed.txt")])
 
