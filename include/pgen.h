@@ -318,6 +318,23 @@ pg_status edges_to_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
                             pg_idwidth w, uint32_t flags, uint64_t* d_row_ptr, void* d_col,
                             uint64_t cap_col, void* d_ws, size_t ws_bytes, void* stream);
 
+/* The sort's wait status (host only; no device call). The digit pass of the
+ * sort finds where each tile's run of a digit starts by reading counts that
+ * earlier tiles publish. Tiles are handed out in order, so every count it
+ * waits for is written by a CTA already running. Each wait still gives up
+ * after a fixed number of polls and then sets a uint32 word of the
+ * workspace to nonzero. That word is zeroed by every edges_to_csr or
+ * edges_to_csr_opts call that sorts, which is any call with n_edges > 0 and
+ * n_vertices > 1. When the word is nonzero after such a call, the CSR it
+ * wrote is unspecified.
+ * Returns the byte offset of the word within the workspace of a call with
+ * these arguments (flags = 0: edges_to_csr), 4-byte aligned and inside
+ * the workspace size that the call requires. Read it after the stream has
+ * finished the call. Returns SIZE_MAX when such a call does not sort (then
+ * nothing is waited for) or when w or flags are invalid. */
+size_t pg_csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                                uint32_t flags);
+
 /* Random graph G(N, M) with replacement, for the exclusive-or randomisation
  * of PK graphs (Sec. 3, PK method): edge e (e < n_edges) is the cell
  * (row, col) = (floor((w1:w0) * N / 2^64), floor((w3:w2) * N / 2^64)) of the

@@ -36,6 +36,7 @@ __all__ = [
     "path_length_stats",
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
+    "pg_csr_wait_error_offset", "csr_wait_error",
 ]
 
 PG_OK, PG_EINVAL, PG_ENOSPC, PG_ECUDA, PG_ETIMEOUT, PG_ENOMEM = range(6)
@@ -546,6 +547,8 @@ def _opts_lib():
         L.pg_csr_opts_workspace_size.restype = sz
         L.edges_to_csr_opts.argtypes = [vp, u64, u64, i32, u32, vp, vp, u64, vp, sz, vp]
         L.edges_to_csr_opts.restype = i32
+        L.pg_csr_wait_error_offset.argtypes = [u64, u64, i32, u32]
+        L.pg_csr_wait_error_offset.restype = sz
         L.gen_random_cells.argtypes = [u64, u64, u64, i32, vp, u64, vp]
         L.gen_random_cells.restype = i32
         L._opts_ready = True
@@ -576,6 +579,28 @@ def edges_to_csr_opts(edges, n_vertices: int, flags: int, row_ptr=None, col=None
                              workspace.numel(), _stream(stream))
     _check("edges_to_csr_opts", st)
     return row_ptr, col
+
+
+def pg_csr_wait_error_offset(n_edges: int, n_vertices: int, id64: bool = False,
+                             flags: int = 0):
+    """Byte offset, in the workspace of a CSR call with these arguments, of
+    the word its sort's bounded waits set when they give up; None when the
+    call sorts nothing (no word is written) or the arguments are invalid."""
+    off = int(_opts_lib().pg_csr_wait_error_offset(n_edges, n_vertices,
+                                                   PG_ID64 if id64 else PG_ID32, flags))
+    return None if off == C.c_size_t(-1).value else off
+
+
+def csr_wait_error(workspace, n_edges: int, n_vertices: int, id64: bool = False,
+                   flags: int = 0) -> int:
+    """The sort's wait word after a CSR call that used `workspace` (a uint8
+    tensor), read once the stream has finished the call: 0 when every wait
+    ended normally, nonzero when one gave up (the CSR is then unspecified)."""
+    off = pg_csr_wait_error_offset(n_edges, n_vertices, id64, flags)
+    if off is None:
+        return 0
+    word = workspace[off:off + 4].cpu().numpy().tobytes()
+    return int.from_bytes(word, "little")
 
 
 def gen_random_cells(n_vertices: int, n_edges: int, seed: int = 0, id64: bool = False, out=None,

@@ -3,6 +3,7 @@
 // Every check happens before the first launch, so an invalid call leaves the
 // device untouched.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 #include <mutex>
@@ -511,6 +512,16 @@ pg_status edges_to_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
                                     d_ws, ws_bytes, s));
     return from_cuda(launch_csr_opts(d_edges, n_edges, n_vertices, w == PG_ID64, flags, d_row_ptr,
                                      d_col, d_ws, s));
+}
+
+size_t pg_csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                                uint32_t flags)
+{
+    if (flags & ~(uint32_t)(PG_CSR_SYMMETRIZE | PG_CSR_DEDUP | PG_CSR_NO_LOOPS | PG_CSR_ODD))
+        return SIZE_MAX;
+    if (w != PG_ID32 && w != PG_ID64) return SIZE_MAX;
+    if (n_edges == 0 || n_vertices < 2 || (n_edges >> 62)) return SIZE_MAX;
+    return csr_wait_error_offset(n_edges, n_vertices, flags, w == PG_ID64);
 }
 
 size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices)

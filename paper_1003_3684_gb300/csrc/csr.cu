@@ -940,6 +940,16 @@ size_t csr_opts_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint32_t 
     return a > b ? a : b;
 }
 
+// Byte offset of the look-back error word in the workspace of a call with
+// these arguments (the layout the call itself uses).
+size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64)
+{
+    const size_t pair_bytes = id64 ? 16 : 8;
+    const CsrLayout L = flags ? opts_layout(n_edges, n_vertices, flags, pair_bytes).L
+                              : csr_layout(n_edges, n_vertices, pair_bytes);
+    return L.off_flag + 128;
+}
+
 cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                             uint32_t flags, uint64_t* d_row_ptr, void* d_col, void* d_ws,
                             cudaStream_t s)

@@ -102,6 +102,7 @@ cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
                             uint32_t flags, uint64_t* d_row_ptr, void* d_col, void* d_ws,
                             cudaStream_t s);
 size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices);
+size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64);
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                        uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,
                        cudaStream_t s);

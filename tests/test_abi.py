@@ -160,3 +160,29 @@ def test_range_entry_points_reject_bad_ranges(L):
     # an empty range is valid and launches nothing
     assert R.gen_pba_blocks(4000, 2, 4, 3, 1, 0, 2, 2, None, 0, C.byref(cnt), None, 0, None) == pg.PG_OK
     assert cnt.value == 0
+
+
+@pytest.mark.parametrize("M,N", [(1, 2), (100_000, 2**20), (8_191, 3), (70_000, 2**33 + 5),
+                                 (3 * 2**20 + 7, 5_000)])
+@pytest.mark.parametrize("id64", [False, True])
+@pytest.mark.parametrize("flags", [0, 1, 2, 1 | 2 | 4, 8])
+def test_csr_wait_error_word_lies_in_the_workspace(L, M, N, id64, flags):
+    import paper_1003_3684_gb300 as pg
+    if not id64 and N > 2**32:
+        return
+    off = pg.pg_csr_wait_error_offset(M, N, id64, flags)
+    ws = (pg.pg_csr_workspace_size(M, N) if flags == 0 else
+          int(pg._opts_lib().pg_csr_opts_workspace_size(M, N, flags)))
+    listed = 2 * M if flags & pg.CSR_SYMMETRIZE else M
+    assert off is not None and off % 4 == 0
+    assert off + 4 <= ws
+    # past the two copies of the list that the sort writes
+    assert off >= 2 * listed * (16 if id64 else 8)
+
+
+def test_csr_wait_error_word_absent_when_nothing_is_sorted(L):
+    import paper_1003_3684_gb300 as pg
+    assert pg.pg_csr_wait_error_offset(0, 10) is None          # no edges
+    assert pg.pg_csr_wait_error_offset(50, 1) is None          # a single row
+    assert pg.pg_csr_wait_error_offset(50, 10, flags=16) is None
+    assert pg.pg_csr_wait_error_offset(50, 10, flags=1) is not None

@@ -465,6 +465,38 @@ def test_csr_options_match_oracle(flags, M, N, id64):
     assert_same(host(col, id64)[:k], ref_col)
 
 
+@pytest.mark.parametrize("flags,id64,grouped", [(0, False, False), (0, True, False),
+                                                 (0, False, True), (1 | 2, False, False),
+                                                 (8, True, False)])
+def test_csr_ignores_workspace_contents_and_clears_its_wait_word(flags, id64, grouped):
+    """Every workspace word a CSR call reads is written earlier in the same
+    call: a workspace filled with 0xFF gives the oracle's CSR. The sort's
+    wait word reads 0 afterwards (no look-back wait gave up), also when the
+    list is already grouped and the sort passes have nothing to do."""
+    M, N = (100_000, 50_000) if grouped else (300_001, 5_000)
+    if grouped:
+        e = np.random.default_rng(3).integers(0, N, size=(M, 2), dtype=np.uint64)
+        e = e[np.lexsort((e[:, 1], e[:, 0]))].astype(np.uint64 if id64 else np.uint32)
+        assert np.bincount(e[:, 0].astype(np.int64)).max() <= 32
+    else:
+        e = _multigraph(7 + flags, M, N, id64)
+    t = torch.from_numpy(e.view(np.int64 if id64 else np.int32)).cuda()
+    size = (pg.pg_csr_workspace_size(M, N) if flags == 0 else
+            int(pg._opts_lib().pg_csr_opts_workspace_size(M, N, flags)))
+    ws = torch.full((size,), 255, dtype=torch.uint8, device="cuda")
+    if flags == 0:
+        rp, col = pg.edges_to_csr(t, N, workspace=ws)
+        ref_rp, ref_col = o.csr(e.astype(np.uint64), N)
+    else:
+        rp, col = pg.edges_to_csr_opts(t, N, flags, workspace=ws)
+        ref_rp, ref_col = o.csr_opts(e.astype(np.uint64), N, flags)
+    torch.cuda.synchronize()
+    assert pg.csr_wait_error(ws, M, N, id64, flags) == 0
+    got_rp = rp.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got_rp, ref_rp)
+    assert_same(host(col, id64)[:int(got_rp[-1])], ref_col)
+
+
 @pytest.mark.parametrize("N,M,id64", [(1000, 100_001, False), (2**40 + 7, 50_000, True), (1, 33, False)])
 def test_random_cells_match_oracle(N, M, id64):
     got = pg.gen_random_cells(N, M, seed=2**33 + 9, id64=id64)
