@@ -56,10 +56,11 @@ typedef enum { PG_ID32 = 0, PG_ID64 = 1 } pg_idwidth;
 
 typedef enum { PG_KRON_STOCHASTIC = 0, PG_KRON_DETERMINISTIC = 1 } pg_kron_mode;
 
-/* Human-readable name of a status code (static string). */
+/* Human-readable name of a status code (static string; library plumbing, not
+ * part of the method). */
 const char* pg_status_string(pg_status s);
 
-/* Number of SMs and library version, for logging. */
+/* Number of SMs and library version, for logging (not part of the method). */
 int pg_device_sm_count(void);
 const char* pg_version(void);
 
@@ -132,10 +133,11 @@ pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t
                   uint64_t cap_edges, uint64_t* n_edges_out, void* d_ws, size_t ws_bytes,
                   void* stream);
 
-/* gen_pba, and a copy of the edge list into host memory h_edges (pinned,
- * B*(e0+n_b*m) pairs). The copy of each range of blocks starts on a second,
- * library-owned stream as soon as that range is written, so the transfer
- * overlaps generation; `stream` waits for the last copy, so synchronising
+/* gen_pba (Sec. 3, PBA method), and a copy of the edge list into host memory
+ * h_edges (pinned, B*(e0+n_b*m) pairs; the paper has no counterpart, as it
+ * excludes writing the graph out from its timings). The copy of each range
+ * of blocks starts on a second, library-owned stream as soon as that range
+ * is written, so the transfer overlaps generation; `stream` waits for the last copy, so synchronising
  * `stream` covers both. d_edges still receives the full edge list. */
 pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
                           uint32_t faction_width, double inter_frac, uint64_t seed, pg_idwidth w,
@@ -255,8 +257,9 @@ pg_status gen_kronecker(const double* h_initiator, uint32_t n0, uint32_t k, uint
                         uint64_t seed, pg_kron_mode mode, pg_idwidth w, void* d_edges,
                         uint64_t cap_edges, uint64_t* n_edges_out, void* stream);
 
-/* Edges [e_begin, e_end) of the graph gen_kronecker makes with the same
- * arguments (e_end <= n_edges, or <= e0^k when deterministic), written to
+/* Edges [e_begin, e_end) of the graph gen_kronecker (Sec. 3, PK method)
+ * makes with the same arguments (ranges are not in the paper): e_end <=
+ * n_edges, or <= e0^k when deterministic; written to
  * d_edges[0 .. e_end - e_begin). Every edge depends only on its index, so
  * ranges may be generated in any order, on any device, and concatenate to
  * the whole list. */
@@ -318,9 +321,9 @@ pg_status edges_to_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
                             pg_idwidth w, uint32_t flags, uint64_t* d_row_ptr, void* d_col,
                             uint64_t cap_col, void* d_ws, size_t ws_bytes, void* stream);
 
-/* The sort's wait status (host only; no device call). The digit pass of the
- * sort finds where each tile's run of a digit starts by reading counts that
- * earlier tiles publish. Tiles are handed out in order, so every count it
+/* The sort's wait status (not in the paper; host only, no device call). The
+ * digit pass of the sort finds where each tile's run of a digit starts by
+ * reading counts that earlier tiles publish. Tiles are handed out in order, so every count it
  * waits for is written by a CTA already running. Each wait still gives up
  * after a fixed number of polls and then sets a uint32 word of the
  * workspace to nonzero. That word is zeroed by every edges_to_csr or
@@ -377,7 +380,10 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
                  uint32_t* levels_out, uint64_t* scanned_out, void* stream);
 
 /* ------------------------------------------------------------------------
- * Batched generation: many independent graphs in one persistent launch.
+ * Batched generation: many independent graphs in one persistent launch. The
+ * batching is not in the paper; each job is one of its generators (Sec. 3,
+ * the O(1) preferential attachment of the PBA method with one block, or the
+ * stochastic Kronecker model that the PK method cites in Sec. 2).
  *
  * A job is a serial BA graph (gen_pba with blocks = 1: n new vertices, m
  * edges each, seed clique K_{n0}) or a stochastic Kronecker graph (as
