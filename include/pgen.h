@@ -137,8 +137,9 @@ pg_status gen_pba(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t
  * h_edges (pinned, B*(e0+n_b*m) pairs; the paper has no counterpart, as it
  * excludes writing the graph out from its timings). The copy of each range
  * of blocks starts on a second, library-owned stream as soon as that range
- * is written, so the transfer overlaps generation; `stream` waits for the last copy, so synchronising
- * `stream` covers both. d_edges still receives the full edge list. */
+ * is written, so the transfer overlaps generation. `stream` waits for the
+ * last copy, so synchronising `stream` covers both. d_edges still receives
+ * the full edge list. */
 pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
                           uint32_t faction_width, double inter_frac, uint64_t seed, pg_idwidth w,
                           void* h_edges, void* d_edges, uint64_t cap_edges, uint64_t* n_edges_out,
