@@ -390,6 +390,31 @@ def test_pba_first_fresh_pick_uniform_at_small_f():
     assert stats.chisquare(obs).pvalue > 1e-4, obs
 
 
+@pytest.mark.parametrize("W,f", [(1, 0.3), (2, 0.1)])
+def test_pba_in_faction_count_mean_closed_form(W, f):
+    """Sec. 3, phase 1 with inter-faction picks: the first s = W entries are
+    the faction. A later entry j is a fresh pick (never in the faction) with
+    probability f' = T_f/2^32, and otherwise a copy of a uniform earlier
+    entry, in the faction with probability in_j/j. So the expected count
+    after N entries is E[in_N] = s * prod_{j=s}^{N-1} (1 + (1 - f')/j), about
+    N (s/N)^f: the realised share outside the faction is much larger than f.
+    The sample mean over blocks and seeds is compared with it (z-test with
+    the sample's own spread: the urn's limit is random)."""
+    B, N = 16, 3000
+    fp = o.coin_threshold(f) / 2**32
+    expect = W * np.prod(1.0 + (1.0 - fp) / np.arange(W, N, dtype=np.float64))
+    got = []
+    for seed in range(40):
+        for p in range(B):
+            A, _, _ = o.pba_phase1(p, B, W, N, f, seed=seed)
+            phi = (p // W) * W
+            got.append(int(((A >= phi) & (A < phi + W)).sum()))
+    got = np.asarray(got, dtype=np.float64)
+    z = (got.mean() - expect) / (got.std(ddof=1) / math.sqrt(got.size))
+    assert abs(z) < 4.5, (got.mean(), expect, z)
+    assert expect / N < 1 - f          # far more than f of the entries are outside
+
+
 def test_pba_phase1_polya_urn_law():
     """W=2, f=0: a two-colour Polya urn started with one ball of each colour.
 
