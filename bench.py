@@ -96,6 +96,12 @@ def kron_work(k: int, id_bytes: int = 4):
     return dict(ops=PHILOX_OPS * ((k + 3) // 4) + 5 * k, bytes=2 * id_bytes)
 
 
+def kron_det_work(k: int, id_bytes: int = 4):
+    # per level: one base-e0 digit (a fixed-point divide), one seed lookup,
+    # two multiply-adds into the ids; no random draws
+    return dict(ops=6 * k, bytes=2 * id_bytes)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -265,6 +271,14 @@ def oracle_sample(name: str, cfg: dict, budget_s: float):
             edges_total += M + Mr
             desc = (f"or_kron k={cfg['k']} ({M} edges) + or_random_cells ({Mr}) + "
                     "or_csr_opts (odd multiplicity) per sample")
+        elif cfg["kind"] == "kron_det":
+            ks = min(cfg["k"], 6)
+            t0 = time.perf_counter()
+            e, _ = o.kron_det(cfg["initiator"], ks)
+            t_total += time.perf_counter() - t0
+            edges_total += e.shape[0]
+            desc = (f"or_kron_det (the literal meta-edge stack) of the same seed at k={ks} "
+                    f"({e.shape[0]} edges) per sample")
         elif cfg["kind"] == "pba" and cfg["blocks"] > 1 and cfg.get("factions"):
             B = 2
             n = B * (cfg["n"] // cfg["blocks"])
@@ -671,6 +685,20 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                         csr_entries=2 * Ep, sources=len(sources),
                         metric_note="adjacency entries scanned per second over BFS from "
                                     "each source (undirected CSR)", id_width=32)
+    elif kind == "kron_det":
+        k, P = cfg["k"], cfg["initiator"]
+        N = len(P) ** k
+        E = pg.pg_kron_edge_count(P, k, 0, deterministic=True)
+        out = torch.empty((E, 2), dtype=torch.int32, device=dev)
+
+        def step():
+            pg.gen_kronecker(P, k, deterministic=True, out=out)
+        units = {"kron_det": E}
+        work = {"kron_det": kron_det_work(k)}
+        out_bytes = E * 8
+        cfg_json = dict(workload=args.workload, initiator="Fig. 2(b) seed: 5 vertices, 11 edges",
+                        k=k, vertices=N, edges_per_step=E, order="stack (seed-digit) order",
+                        id_width=32)
     elif kind == "kron_xor":
         k, M, Mr = cfg["k"], cfg["n_edges"], cfg["n_random"]
         N = 2**k
@@ -960,7 +988,7 @@ def measure_e2e(args, step, out, cfg, E, dev, world, rank):
     host = torch.empty(chunk, dtype=torch.uint8, pin_memory=True)
     flat = out.view(torch.uint8).view(-1)
     h2d = 0
-    if cfg["kind"] == "kron":
+    if cfg["kind"] in ("kron", "kron_det"):
         init = torch.tensor(cfg["initiator"], dtype=torch.float64).pin_memory()
         h2d = init.numel() * 8
 

@@ -439,6 +439,7 @@ pg_status kron_common(const double* h_initiator, uint32_t n0, uint32_t k, uint64
     p.k = k;
     p.e0 = e0;
     p.div_e0 = make_fastdiv(e0);
+    p.div_e0_32 = make_fastdiv32(e0);
     if (e_end == ~(uint64_t)0) e_end = (uint64_t)total;
     if (e_begin > e_end || e_end > (uint64_t)total) return PG_EINVAL;
     const uint64_t count = e_end - e_begin;

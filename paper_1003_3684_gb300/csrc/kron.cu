@@ -216,7 +216,28 @@ __device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint
     }
 }
 
-template <typename Id>
+// The same digits in 32-bit arithmetic, for edge indices and ids below 2^32
+// (e0^k edges of n0^k vertices, both at most 2^32). The digit is clamped to
+// the table, so the lookup stays inside it whatever the arithmetic gives.
+__device__ __forceinline__ void kron_det_edge32(const KronDetParams& p, const uint16_t* ab,
+                                                uint32_t e, uint32_t& row, uint32_t& col)
+{
+    row = 0;
+    col = 0;
+    uint32_t mul = 1;
+    for (uint32_t l = 0; l < p.k; ++l) {   // least significant digit first
+        const uint32_t q = fdiv32(e, p.div_e0_32);
+        const uint32_t r = e - q * p.e0;
+        const uint32_t d = r < p.e0 ? r : p.e0 - 1;
+        e = q;
+        const uint32_t v = ab[d];
+        row += (v & 0xFFu) * mul;
+        col += (v >> 8) * mul;
+        mul *= p.n0;
+    }
+}
+
+template <typename Id, bool kNarrow>
 __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ KronDetParams p,
                                                        Id* __restrict__ out, uint64_t e_begin,
                                                        uint64_t n_edges)
@@ -228,15 +249,21 @@ __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ K
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
         const uint64_t e = 2 * t;
-        uint64_t r0, c0;
-        kron_det_edge(p, ab, e_begin + e, r0, c0);
-        if (e + 1 < n_edges) {
-            uint64_t r1, c1;
-            kron_det_edge(p, ab, e_begin + e + 1, r1, c1);
-            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        const bool two = e + 1 < n_edges;
+        uint64_t r0, c0, r1 = 0, c1 = 0;
+        if constexpr (kNarrow) {
+            uint32_t a0, b0, a1 = 0, b1 = 0;
+            kron_det_edge32(p, ab, (uint32_t)(e_begin + e), a0, b0);
+            if (two) kron_det_edge32(p, ab, (uint32_t)(e_begin + e + 1), a1, b1);
+            r0 = a0; c0 = b0; r1 = a1; c1 = b1;
         } else {
-            Pair2<Id>::store1(out, e, r0, c0);
+            kron_det_edge(p, ab, e_begin + e, r0, c0);
+            if (two) kron_det_edge(p, ab, e_begin + e + 1, r1, c1);
         }
+        if (two)
+            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        else
+            Pair2<Id>::store1(out, e, r0, c0);
     }
 }
 
@@ -314,12 +341,17 @@ cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint6
 {
     if (n_edges == 0) return cudaSuccess;
     const uint64_t pairs = (n_edges + 1) / 2;
+    // 32-bit digits when every edge index of the launch and every id is below 2^32
+    uint64_t n_vertices = 1;
+    for (uint32_t l = 0; l < p.k && n_vertices <= ((uint64_t)1 << 32); ++l) n_vertices *= p.n0;
+    const bool narrow = e_begin + n_edges <= ((uint64_t)1 << 32) &&
+                        n_vertices <= ((uint64_t)1 << 32);
     TraceScope trace("kron_det", s);
     if (id64) {
-        auto k = kron_det_kernel<uint64_t>;
+        auto k = narrow ? kron_det_kernel<uint64_t, true> : kron_det_kernel<uint64_t, false>;
         k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
     } else {
-        auto k = kron_det_kernel<uint32_t>;
+        auto k = narrow ? kron_det_kernel<uint32_t, true> : kron_det_kernel<uint32_t, false>;
         k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
     }
     return cudaGetLastError();

@@ -30,6 +30,7 @@ constexpr int kMaxDetSeedEdges = 8192;
 struct KronDetParams {
     uint32_t n0, k, e0, pad;
     FastDiv div_e0;
+    FastDiv32 div_e0_32;   // for edge indices below 2^32
     uint16_t ab[kMaxDetSeedEdges];
 };
 

@@ -12,6 +12,11 @@ import numpy as np
 # Initiator of the stochastic Kronecker configuration (2x2, row-major).
 KRON_INITIATOR = [[0.57, 0.19], [0.19, 0.05]]
 
+# Seed graph of the deterministic Kronecker example (Sec. 3, PK method, Fig.
+# 2(b)): 5 vertices, 11 edges including the self-loops, row-major 0/1.
+PK_FIG2_SEED = [[1, 1, 1, 1, 0], [1, 1, 0, 0, 0], [1, 0, 1, 0, 0], [1, 0, 0, 1, 0],
+                [0, 0, 0, 0, 1]]
+
 CONFIGS = {
     # serial BA: 100,000 new vertices, 4 edges each, seed clique K5
     "ba_n100k_m4": dict(kind="pba", n=100_000, m=4, blocks=1, n0=5, faction_width=1,
@@ -19,6 +24,9 @@ CONFIGS = {
     # stochastic Kronecker, k = 20 levels (2^20 vertices), 16 * 2^20 edges, plus CSR
     "kron_k20_m16x_csr": dict(kind="kron", initiator=KRON_INITIATOR, k=20,
                               n_edges=16 * 2**20, seed=7, csr=True),
+    # deterministic Kronecker of the Fig. 2 seed at k = 8: 5^8 = 390,625
+    # vertices, 11^8 = 214,358,881 edges (1.7 GB of pairs), in stack order
+    "kron_det_fig2_k8": dict(kind="kron_det", initiator=PK_FIG2_SEED, k=8, seed=0),
     # the same initiator at k = 26 (2^26 vertices, 2^30 edges: 8.6 GB of pairs)
     "kron_k26_m16x_csr": dict(kind="kron", initiator=KRON_INITIATOR, k=26,
                               n_edges=16 * 2**26, seed=7, csr=True),

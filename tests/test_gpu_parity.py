@@ -75,6 +75,18 @@ def test_kron_deterministic(P, k, id64):
     assert_same(host(got, id64), ref)
 
 
+@pytest.mark.slow
+def test_kron_deterministic_benchmark_size():
+    """The launch the benchmark times: the Fig. 2 seed at k = 8, all
+    11^8 = 214,358,881 edges compared with the oracle's literal stack."""
+    cfg = W.CONFIGS["kron_det_fig2_k8"]
+    got = pg.gen_kronecker(cfg["initiator"], cfg["k"], deterministic=True)
+    torch.cuda.synchronize()
+    ref, peak = o.kron_det(np.asarray(cfg["initiator"], float), cfg["k"])
+    assert ref.shape[0] == 11 ** 8 and peak <= cfg["k"] * 10 + 1
+    assert np.array_equal(host(got), ref)
+
+
 def test_kron_deterministic_large_seed():
     rng = np.random.default_rng(9)
     P = (rng.random((40, 40)) < 0.15).astype(float)
@@ -367,6 +379,37 @@ def test_deterministic_kronecker_ranges(golden):
              for a, b in zip(cuts[:-1], cuts[1:])]
     torch.cuda.synchronize()
     assert torch.equal(torch.cat(parts), full)
+
+
+@pytest.mark.parametrize("id64", [False, True])
+def test_deterministic_kronecker_across_2p32(golden, id64):
+    """Fig. 2 seed at k = 10: 11^10 edges, more than 2^32. A range ending at
+    edge 2^32 takes the 32-bit digit path, and one reaching past it the
+    64-bit path. Both must give every edge its base-e0 digits, most
+    significant first, applied to the seed's edges in row-major order
+    (reading R9; the oracle's stack order, pinned on the CPU)."""
+    G = np.array([[float(x) for x in r] for r in golden("pk_fig2_seed.txt")])
+    k, n0 = 10, G.shape[0]
+    seed_edges = [(a, b) for a in range(n0) for b in range(n0) if G[a, b] > 0]
+    e0 = len(seed_edges)
+    lo, mid, hi = 2**32 - 1000, 2**32, 2**32 + 1000
+    narrow = pg.gen_kronecker_range(G, k, 0, lo, mid, deterministic=True, id64=id64)
+    wide = pg.gen_kronecker_range(G, k, 0, lo, hi, deterministic=True, id64=id64)
+    torch.cuda.synchronize()
+    got_n, got_w = host(narrow, id64), host(wide, id64)
+    assert np.array_equal(got_n, got_w[:mid - lo])
+    want = np.zeros((hi - lo, 2), np.uint64)
+    for i, e in enumerate(range(lo, hi)):
+        row = col = 0
+        mul = 1
+        for _ in range(k):
+            a, b = seed_edges[e % e0]
+            e //= e0
+            row += a * mul
+            col += b * mul
+            mul *= n0
+        want[i] = (row, col)
+    assert_same(got_w, want)
 
 
 def test_pba_block_ranges_from_one_prepare():
