@@ -44,3 +44,16 @@ def test_all_cores_estimate_is_labelled():
     e = bench.all_cores_estimate(2.0)
     assert e["value"] == 2.0 * e["host_cores"] and e["host_cores"] >= 1
     assert "estimate" in e["note"]
+
+
+def test_deterministic_kronecker_workload_is_the_fig2_seed():
+    # the workload's seed is the cited Fig. 2(b) fixture, and its size is e0^k
+    from paper_1003_3684_gb300 import build, workloads as W
+    build.build()
+    import paper_1003_3684_gb300 as pg
+    rows = [ln.split() for ln in open(os.path.join(ROOT, "tests", "golden", "pk_fig2_seed.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    cfg = W.CONFIGS["kron_det_fig2_k8"]
+    assert [[int(x) for x in r] for r in rows] == cfg["initiator"]
+    assert pg.pg_kron_edge_count(cfg["initiator"], cfg["k"], 0, deterministic=True) == 11 ** 8
+    assert bench.kron_det_work(cfg["k"]) == dict(ops=48, bytes=8)
