@@ -62,32 +62,28 @@ CSR_WORK = {
 
 
 def dram_traffic_table():
-    """DRAM bytes per unit measured by ncu, from profiles/dram_traffic.md.
+    """DRAM bytes per unit measured by ncu, from profiles/dram_traffic.json.
 
-    Each row names the kernel, the source file it is compiled from and that
-    file's sha256 prefix at capture time; a row whose file has changed since
+    Each entry names the kernel, the source file it is compiled from and that
+    file's sha256 prefix at capture time; an entry whose file has changed since
     is ignored (the counters no longer describe the kernel that runs).
     """
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     table = {}
     try:
-        lines = open(path).read().splitlines()
-    except OSError:
+        with open(path) as fh:
+            rows = json.load(fh)["kernels"]
+    except (OSError, ValueError, KeyError):
         return table
-    for ln in lines:
-        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) < 4 or not cells[0].startswith("`"):
-            continue
-        kernel, src, sha = cells[0].strip("`"), cells[1].strip("`"), cells[2].strip("`")
+    for row in rows:
         try:
-            per_unit = float(cells[3])
-            with open(os.path.join(ROOT, src), "rb") as fh:
+            with open(os.path.join(ROOT, row["source"]), "rb") as fh:
                 cur = hashlib.sha256(fh.read()).hexdigest()[:12]
-        except (OSError, ValueError):
+            if cur == row["sha256"]:
+                table[row["kernel"]] = float(row["bytes_per_unit"])
+        except (OSError, KeyError, TypeError, ValueError):
             continue
-        if cur == sha:
-            table[kernel] = per_unit
     return table
 
 
@@ -521,11 +517,9 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         line["cpu_baseline"] = dict(value=e_cpu / t_cpu, unit="edges/s", cores=1, kind="oracle",
                                     sample=f"{i} jobs of the batch (every 97th), {t_cpu:.1f} s",
                                     all_cores_estimate=all_cores_estimate(e_cpu / t_cpu))
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def run_serve(args, rank: int, world: int, local_rank: int):
@@ -555,6 +549,9 @@ def run_serve(args, rank: int, world: int, local_rank: int):
         wall = time.perf_counter() - t0
         lat = np.array([r.latency for r in done]) * 1000.0
         edges = sum(serve.job_edges(r.job) for r in done)
+        if srv.failed:
+            raise RuntimeError(f"serving: {len(srv.failed)} request(s) failed: "
+                               f"{srv.failed[0].error}")
         return dict(value=edges / wall, unit="edges/s", completed=len(done),
                     offered=len(arrivals), wall_s=wall,
                     p50_ms=float(np.percentile(lat, 50)) if lat.size else None,
@@ -571,7 +568,7 @@ def run_serve(args, rank: int, world: int, local_rank: int):
     clocks = sampler.stop() if sampler else None
     pg.pg_trace_enable(False)
     kernels = pg.pg_trace_dump()
-    per_graph = replay(True, trace, max_wall=3 * duration)
+    per_graph = replay(True, trace, max_wall=args.serve_per_graph_wall * duration)
     offered = sum(serve.job_edges(j) for _, j in trace) / duration
     line = dict(metric="edges/sec", value=served["value"], unit="edges/s", n_gpus=world,
                 steps=1, warmup=1, ms_per_step=served["wall_s"] * 1000.0, higher_is_better=True,
@@ -585,9 +582,7 @@ def run_serve(args, rank: int, world: int, local_rank: int):
                 gpu_launches=sum(v[0] for v in kernels.values()),
                 kernels={kk: [v[0], round(v[1], 3)] for kk, v in kernels.items()},
                 clocks=clocks)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line if rank == 0 else None
 
 
 def run_pgen(args, rank: int, world: int, local_rank: int):
@@ -610,6 +605,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     seed = replica_seed(cfg["seed"], rank)
     stream = torch.cuda.current_stream()
     kind = cfg["kind"]
+    csr_call = None   # (workspace, edges, vertices, flags) of a timed CSR call
 
     if kind == "pba":
         n, m, B, n0 = cfg["n"], cfg["m"], cfg["blocks"], cfg["n0"]
@@ -713,6 +709,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             pg.gen_kronecker(cfg["initiator"], k, M, seed, out=out[:M])
             pg.gen_random_cells(N, Mr, seed, out=out[M:])
             pg.edges_to_csr_opts(out, N, pg.CSR_ODD, row_ptr=row_ptr, col=col, workspace=ws)
+        csr_call = (ws, E, N, pg.CSR_ODD)
         units = {"kron_descent_n0_2": M}
         work = {"kron_descent_n0_2": kron_work(k)}
         units.update({kk: E for kk in CSR_WORK})
@@ -735,6 +732,8 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             pg.gen_kronecker(cfg["initiator"], k, M, seed, out=out)
             if cfg.get("csr"):
                 pg.edges_to_csr(out, N, row_ptr=row_ptr, col=col, workspace=ws)
+        if cfg.get("csr"):
+            csr_call = (ws, M, N, 0)
         units = {"kron_descent_n0_2": M}
         work = {"kron_descent_n0_2": kron_work(k)}
         if cfg.get("csr"):
@@ -799,6 +798,13 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     clocks = sampler.stop() if sampler else None
     pg.pg_trace_enable(False)
     kernels = pg.pg_trace_dump()
+    csr_wait = None
+    if csr_call is not None:
+        # the sort's bounded waits: a nonzero word means the last timed CSR
+        # is unspecified, so the run is not a measurement
+        csr_wait = pg.csr_wait_error(csr_call[0], csr_call[1], csr_call[2], flags=csr_call[3])
+        if csr_wait:
+            raise RuntimeError("edges_to_csr: a bounded wait of the sort gave up (PG_ETIMEOUT)")
     ms_max = max_over_ranks(ms, dev, world)
     value = job_throughput(E, args.steps, world, ms_max)
     launches = sum(v[0] for v in kernels.values())
@@ -860,7 +866,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u32",
                 data="synthetic", config=cfg_json, roofline=roof, gpu_launches=launches,
                 kernels={kk: [v[0], round(v[1], 4)] for kk, v in kernels.items()},
-                clocks=clocks,
+                clocks=clocks, csr_wait_error=csr_wait,
                 step_ms=dict(best=round(min(per_step), 4),
                              median=round(statistics.median(per_step), 4),
                              mean=round(ms / args.steps, 4), rank=0))
@@ -885,11 +891,9 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
         line["cpu_baseline"] = dict(value=v, unit=unit, cores=1, kind="oracle",
                                     sample=f"{desc}; {ns} samples, {tsec:.1f} s",
                                     all_cores_estimate=all_cores_estimate(v))
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world):
@@ -1019,6 +1023,38 @@ def measure_e2e(args, step, out, cfg, E, dev, world, rank):
                             f"{(out_bytes + chunk - 1) // chunk} chunk(s) per step")
 
 
+# The default run's line also carries the metric's other parts, measured in
+# the same process after the headline (N = 1 only): Kronecker k = 20 with CSR,
+# the 4096-job batch against per-graph launches, and the Poisson serving
+# trace against a per-graph server. Each is a shortened run of its workload.
+SUB_RECORDS = (
+    ("kron", "kron_k20_m16x_csr", dict(steps=20, warmup=3)),
+    ("batch", "batch_4096_mixed", dict(steps=3, warmup=1, no_cpu_baseline=True)),
+    ("serve", "serve_poisson_2000", dict(serve_seconds=4.0, serve_per_graph_wall=2.0)),
+)
+SUB_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "roofline",
+            "per_graph", "served", "latency_ms", "e2e", "step_ms", "kernels", "gpu_launches",
+            "clocks", "csr_wait_error")
+
+
+def run_sub_records(args, local_rank: int) -> dict:
+    import torch
+    subs = {}
+    for key, workload, over in SUB_RECORDS:
+        torch.cuda.empty_cache()
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.blocks, a.batch_jobs = workload, 0, 0
+        a.no_cpu_baseline = True
+        for k, v in over.items():
+            setattr(a, k, v)
+        kind = W.CONFIGS[workload]["kind"]
+        runner = run_batch if kind == "batch" else run_serve if kind == "serve" else run_pgen
+        line = runner(a, 0, 1, local_rank)
+        subs[key] = {k: line[k] for k in SUB_KEYS if k in line}
+    torch.cuda.empty_cache()
+    return subs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1028,11 +1064,16 @@ def main():
     ap.add_argument("--workload", choices=sorted(W.CONFIGS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload only: leave out the kron/batch/serve sub-records")
     ap.add_argument("--blocks", type=int, default=0,
                     help="PBA only: run this many blocks of the workload's block size "
                          "(a smaller case, e.g. for profiler captures)")
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="serve workload only: seconds of arrivals (default: the workload's)")
+    ap.add_argument("--serve-per-graph-wall", type=float, default=3.0,
+                    help="serve workload only: the per-graph server stops after this many "
+                         "times the arrival window")
     ap.add_argument("--batch-jobs", type=int, default=0,
                     help="batch workload only: use this many of its jobs (a smaller case)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
@@ -1043,11 +1084,21 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if W.CONFIGS[args.workload]["kind"] == "batch":
-        return run_batch(args, rank, world, local_rank)
-    if W.CONFIGS[args.workload]["kind"] == "serve":
-        return run_serve(args, rank, world, local_rank)
-    return run_pgen(args, rank, world, local_rank)
+    kind = W.CONFIGS[args.workload]["kind"]
+    if kind == "batch":
+        line = run_batch(args, rank, world, local_rank)
+    elif kind == "serve":
+        line = run_serve(args, rank, world, local_rank)
+    else:
+        line = run_pgen(args, rank, world, local_rank)
+    if (line is not None and args.workload == DEFAULT_WORKLOAD and world == 1 and
+            not args.no_sub and not args.blocks):
+        line.update(run_sub_records(args, local_rank))
+        line["sub_records"] = ("kron, batch and serve: the metric's other parts, measured after "
+                               "the headline in the same process, each with its own clocks")
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -76,6 +76,17 @@ const char* pg_version(void);
  * at once for workspaces prepared without it). Default off; cannot fail. */
 void pg_force_wide_path(int on);
 
+/* Test hook (not part of the method; host only, no GPU needed): exercises the
+ * bookkeeping that sets kernel attributes once per device. `threads` host
+ * threads (1..64) each run the device ids devs[0..n) in order through one
+ * shared instance, whose set-up step counts its calls per device and fails
+ * for device fail_dev (-1: never). Writes calls[d] (64 ints) = number of
+ * set-up calls for device d, and status[i] (n ints) = the cudaError_t that
+ * thread 0 got for devs[i] (ids outside 0..63 fail). Returns PG_EINVAL for
+ * bad arguments, else PG_OK. */
+int pg_test_per_device_once(const int* devs, int n, int threads, int fail_dev, int* calls,
+                            int* status);
+
 /* Throughput probe (not part of the method): launches one kernel in which
  * each of pg_philox_probe_threads() threads (8 CTAs of 256 per SM) makes
  * calls_per_thread Philox4x32-10 calls and writes one folded word to
@@ -338,6 +349,25 @@ pg_status edges_to_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
  * nothing is waited for) or when w or flags are invalid. */
 size_t pg_csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
                                 uint32_t flags);
+
+/* Checked completion of an edges_to_csr / edges_to_csr_opts call (not in the
+ * paper). Waits for `stream` (the call's stream), then reads the wait word
+ * described above from d_ws (the call's workspace; the other arguments are
+ * the call's). Returns PG_OK when no wait gave up (or the call had nothing
+ * to sort), PG_ETIMEOUT when one did, so that the CSR the call wrote must not
+ * be used, PG_EINVAL for invalid w or flags, PG_ECUDA when the copy or the
+ * synchronisation fails. After a wait gives up, the call's remaining sort
+ * passes do nothing and every write stays inside its output buffers. */
+pg_status pg_csr_check(const void* d_ws, uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                       uint32_t flags, void* stream);
+
+/* Test hook (not part of the method): spin_limit (0 = the default, 2^18)
+ * is the number of polls after which a wait of the sort gives up, and tile
+ * withhold_tile (0xffffffff = none) of every digit pass never publishes its
+ * counts, so that the tiles after it wait in vain. Lets a test make the
+ * bounded wait run out on purpose and check pg_csr_check's PG_ETIMEOUT.
+ * Process-wide, read at each call; cannot fail. */
+void pg_csr_test_wait_hook(uint32_t spin_limit, uint32_t withhold_tile);
 
 /* Random graph G(N, M) with replacement, for the exclusive-or randomisation
  * of PK graphs (Sec. 3, PK method): edge e (e < n_edges) is the cell

@@ -36,7 +36,7 @@ __all__ = [
     "path_length_stats",
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
-    "pg_csr_wait_error_offset", "csr_wait_error",
+    "pg_csr_wait_error_offset", "csr_wait_error", "pg_csr_check", "pg_csr_test_wait_hook",
 ]
 
 PG_OK, PG_EINVAL, PG_ENOSPC, PG_ECUDA, PG_ETIMEOUT, PG_ENOMEM = range(6)
@@ -518,8 +518,12 @@ def pg_csr_workspace_size(n_edges: int, n_vertices: int) -> int:
     return int(lib().pg_csr_workspace_size(n_edges, n_vertices))
 
 
-def edges_to_csr(edges, n_vertices: int, row_ptr=None, col=None, workspace=None, stream=None):
-    """CSR of an (E, 2) edge tensor: (row_ptr int64[N+1], col[E]) with rows sorted."""
+def edges_to_csr(edges, n_vertices: int, row_ptr=None, col=None, workspace=None, stream=None,
+                 check: bool = False):
+    """CSR of an (E, 2) edge tensor: (row_ptr int64[N+1], col[E]) with rows sorted.
+
+    check=True waits for the stream and raises PgenError(PG_ETIMEOUT) when a
+    bounded wait of the sort gave up (pg_csr_check)."""
     import torch
     id64 = edges.dtype == torch.int64
     E = edges.shape[0]
@@ -534,7 +538,33 @@ def edges_to_csr(edges, n_vertices: int, row_ptr=None, col=None, workspace=None,
                             _ptr(row_ptr), _ptr(col), _ptr(workspace), workspace.numel(),
                             _stream(stream))
     _check("edges_to_csr", st)
+    if check:
+        pg_csr_check(workspace, E, n_vertices, id64=id64, stream=stream)
     return row_ptr, col[:E]
+
+
+def pg_csr_check(workspace, n_edges: int, n_vertices: int, id64: bool = False, flags: int = 0,
+                 stream=None) -> None:
+    """Wait for `stream`, then raise PgenError(PG_ETIMEOUT) if the CSR call
+    with these arguments that used `workspace` had a bounded wait give up."""
+    L = lib()
+    if not getattr(L, "_check_ready", False):
+        L.pg_csr_check.argtypes = [vp, u64, u64, i32, u32, vp]
+        L.pg_csr_check.restype = i32
+        L.pg_csr_test_wait_hook.argtypes = [u32, u32]
+        L.pg_csr_test_wait_hook.restype = None
+        L._check_ready = True
+    _check("pg_csr_check", L.pg_csr_check(_ptr(workspace), n_edges, n_vertices,
+                                          PG_ID64 if id64 else PG_ID32, flags, _stream(stream)))
+
+
+def pg_csr_test_wait_hook(spin_limit: int = 0, withhold_tile: int = 0xFFFFFFFF) -> None:
+    """Test hook: sort waits give up after spin_limit polls (0: the default)
+    and tile withhold_tile of every digit pass never publishes its counts."""
+    L = lib()
+    L.pg_csr_test_wait_hook.argtypes = [u32, u32]
+    L.pg_csr_test_wait_hook.restype = None
+    L.pg_csr_test_wait_hook(spin_limit, withhold_tile)
 
 
 CSR_SYMMETRIZE, CSR_DEDUP, CSR_NO_LOOPS, CSR_ODD = 1, 2, 4, 8

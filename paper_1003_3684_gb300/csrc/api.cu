@@ -2,9 +2,11 @@
 // set-up (thresholds, divisors, geometry) and dispatch to the kernels.
 // Every check happens before the first launch, so an invalid call leaves the
 // device untouched.
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 #include <mutex>
 
@@ -158,6 +160,32 @@ const char* pg_version(void) { return "pgen 0.1 (sm_103a)"; }
 
 void pg_force_wide_path(int on) { set_wide_path_forced(on != 0); }
 
+int pg_test_per_device_once(const int* devs, int n, int threads, int fail_dev, int* calls,
+                            int* status)
+{
+    if (!devs || !calls || !status || n < 0 || threads < 1 || threads > 64) return PG_EINVAL;
+    PerDeviceOnce once;
+    std::atomic<int> count[kMaxDevices];
+    for (int d = 0; d < kMaxDevices; ++d) count[d].store(0);
+    // every thread runs the whole sequence on the one shared instance
+    auto body = [&](int t) {
+        for (int i = 0; i < n; ++i) {
+            const int dev = devs[i];
+            const cudaError_t e = once.run(dev, [&] {
+                count[dev].fetch_add(1);
+                return dev == fail_dev ? cudaErrorInvalidValue : cudaSuccess;
+            });
+            if (t == 0) status[i] = (int)e;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(body, t);
+    body(0);
+    for (auto& th : pool) th.join();
+    for (int d = 0; d < kMaxDevices; ++d) calls[d] = count[d].load();
+    return PG_OK;
+}
+
 uint64_t pg_pba_edge_count(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0)
 {
     const PbaCheck c = check_pba(n, m, blocks, n0, blocks ? blocks : 1, 0.0, PG_ID64);
@@ -309,6 +337,34 @@ int pba_setup(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0, uint32_t fac
 
 }  // namespace pgen
 
+namespace {
+
+// The copy stream and events of gen_pba_to_host on the current device. On a
+// failure every handle already created is destroyed again.
+cudaError_t make_host_copy(HostCopy* h)
+{
+    *h = HostCopy{};
+    cudaError_t e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    uint32_t n_done = 0;
+    bool copied = false;
+    if (e == cudaSuccess)
+        for (; n_done < kMaxCopyChunks; ++n_done)
+            if ((e = cudaEventCreateWithFlags(&h->done[n_done], cudaEventDisableTiming)) !=
+                cudaSuccess)
+                break;
+    if (e == cudaSuccess)
+        copied = (e = cudaEventCreateWithFlags(&h->copied, cudaEventDisableTiming)) == cudaSuccess;
+    if (e != cudaSuccess) {
+        for (uint32_t i = 0; i < n_done; ++i) cudaEventDestroy(h->done[i]);
+        if (copied) cudaEventDestroy(h->copied);
+        if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+        *h = HostCopy{};
+    }
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
@@ -333,28 +389,15 @@ pg_status gen_pba_to_host(uint64_t n, uint32_t m, uint32_t blocks, uint32_t n0,
     const size_t need = pba_workspace_layout(g.A_stride, blocks, g.S).total;
     if (!d_ws || ws_bytes < need) return PG_ENOMEM;
     if (!aligned(d_ws, 256)) return PG_EINVAL;
-    // one copy stream and its events per device, made on first use
-    static std::mutex mu;
-    static HostCopy per_dev[64];
-    static bool made[64] = {};
+    // one copy stream and its events per device, made on first use; a
+    // set-up that fails destroys what it made, and its status is kept
+    static PerDeviceOnce once;
+    static HostCopy per_dev[kMaxDevices];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PG_ECUDA;
-    HostCopy hc;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!made[dev]) {
-            HostCopy& h = per_dev[dev];
-            if (cudaStreamCreateWithFlags(&h.copy_stream, cudaStreamNonBlocking) != cudaSuccess)
-                return PG_ECUDA;
-            for (uint32_t i = 0; i < kMaxCopyChunks; ++i)
-                if (cudaEventCreateWithFlags(&h.done[i], cudaEventDisableTiming) != cudaSuccess)
-                    return PG_ECUDA;
-            if (cudaEventCreateWithFlags(&h.copied, cudaEventDisableTiming) != cudaSuccess)
-                return PG_ECUDA;
-            made[dev] = true;
-        }
-        hc = per_dev[dev];
-    }
+    if (cudaGetDevice(&dev) != cudaSuccess) return PG_ECUDA;
+    const cudaError_t made = once.run(dev, [dev] { return make_host_copy(&per_dev[dev]); });
+    if (made != cudaSuccess) return PG_ECUDA;
+    HostCopy hc = per_dev[dev];
     hc.h_edges = h_edges;
     // about one wave of emit CTAs per chunk
     const uint64_t ctas_per_block = (g.S + 7) / 8;
@@ -523,6 +566,29 @@ size_t pg_csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, pg_idwidt
     if (w != PG_ID32 && w != PG_ID64) return SIZE_MAX;
     if (n_edges == 0 || n_vertices < 2 || (n_edges >> 62)) return SIZE_MAX;
     return csr_wait_error_offset(n_edges, n_vertices, flags, w == PG_ID64);
+}
+
+pg_status pg_csr_check(const void* d_ws, uint64_t n_edges, uint64_t n_vertices, pg_idwidth w,
+                       uint32_t flags, void* stream)
+{
+    if (flags & ~(uint32_t)(PG_CSR_SYMMETRIZE | PG_CSR_DEDUP | PG_CSR_NO_LOOPS | PG_CSR_ODD))
+        return PG_EINVAL;
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    const size_t off = pg_csr_wait_error_offset(n_edges, n_vertices, w, flags);
+    if (off == SIZE_MAX) return PG_OK;   // no edges to sort: the call had no wait
+    if (!d_ws) return PG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, (const unsigned char*)d_ws + off, 4, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return PG_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PG_ECUDA;
+    return word ? PG_ETIMEOUT : PG_OK;
+}
+
+void pg_csr_test_wait_hook(uint32_t spin_limit, uint32_t withhold_tile)
+{
+    set_csr_wait_hook(spin_limit, withhold_tile);
 }
 
 size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices)

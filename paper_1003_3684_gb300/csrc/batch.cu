@@ -412,14 +412,16 @@ pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_a
     cudaStream_t s = (cudaStream_t)stream;
     const size_t id_bytes = w == PG_ID64 ? 8 : 4;
     const size_t smem = kMaxTile * id_bytes + (size_t)(n_jobs + 1) * 4;
-    static bool attrs = false;
-    if (!attrs) {
-        cudaFuncSetAttribute(batch_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kMaxTile * 4 + (kMaxBatchJobs + 1) * 4));
-        cudaFuncSetAttribute(batch_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kMaxTile * 8 + (kMaxBatchJobs + 1) * 4));
-        attrs = true;
-    }
+    // the opt-in shared-memory sizes, set once per device
+    static PerDeviceOnce attrs;
+    const cudaError_t ae = attrs.run_current([] {
+        return first_error({
+            cudaFuncSetAttribute(batch_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kMaxTile * 4 + (kMaxBatchJobs + 1) * 4)),
+            cudaFuncSetAttribute(batch_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kMaxTile * 8 + (kMaxBatchJobs + 1) * 4))});
+    });
+    if (ae != cudaSuccess) return PG_ECUDA;
     int per_sm = 0;
     if (w == PG_ID64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint64_t>, kBatchThreads, smem);

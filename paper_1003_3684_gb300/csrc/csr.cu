@@ -28,6 +28,7 @@
 //
 // Ids at or above n_vertices are never used as an index (such edges are
 // dropped), so a bad list cannot make a kernel write out of bounds.
+#include <atomic>
 #include <cstring>
 
 #include "pg_internal.h"
@@ -118,6 +119,16 @@ constexpr unsigned long long kCountMask = (1ull << 58) - 1;
 constexpr uint32_t kSpinLimit = 1u << 18;   // polls of one status word
 constexpr int kLookWindow = 8;              // earlier tiles read per round trip
 
+// Test hook (host-set, off by default): a shorter poll limit, and one tile
+// per pass that never publishes its counts, so that the tiles after it give
+// up waiting and set the error word. The values are passed to each launch.
+struct CsrWaitHook {
+    uint32_t spin_limit, withhold;
+};
+std::atomic<uint32_t> g_hook_spin{kSpinLimit};
+std::atomic<uint32_t> g_hook_withhold{0xFFFFFFFFu};
+CsrWaitHook csr_wait_hook() { return CsrWaitHook{g_hook_spin.load(), g_hook_withhold.load()}; }
+
 // One LSD pass over a tile: load once, rank stably (per warp by match, then
 // across warps), reorder the tile by digit in shared memory, and write each
 // digit's run to its place in the output with consecutive threads on
@@ -128,14 +139,17 @@ constexpr int kLookWindow = 8;              // earlier tiles read per round trip
 // done. It publishes its own counts before it waits on anything, and it sums
 // earlier tiles' counts, kLookWindow at a time, until it meets an inclusive
 // one. The look-back runs after the reorder, when the tile's pairs no longer
-// occupy registers. Every poll loop is bounded: after kSpinLimit polls of
-// one word it sets *err and goes on.
+// occupy registers. Every poll loop is bounded: after spin_limit polls of
+// one word (kSpinLimit unless a test hook shortened it) it sets *err and
+// goes on with the partial sum, which can only be too small, so every write
+// stays inside the output.
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const typename PairOf<Id>::T* __restrict__ in, typename PairOf<Id>::T* __restrict__ out,
     uint64_t M, int field, int shift, int bits, unsigned long long* __restrict__ status,
     uint32_t pass, const uint64_t* __restrict__ dstart, uint32_t* __restrict__ ticket,
-    uint32_t* __restrict__ err, const uint32_t* __restrict__ sort_needed)
+    uint32_t* __restrict__ err, const uint32_t* __restrict__ sort_needed, uint32_t spin_limit,
+    uint32_t withhold)
 {
     using P = typename PairOf<Id>::T;
     constexpr int kItems = SortShape<Id>::items;
@@ -147,7 +161,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     P* buf = reinterpret_cast<P*>(loff + kMaxBuckets);                                  // tile
     __shared__ uint32_t s_part[kSortWarps + 1];
     __shared__ uint32_t s_tile;
-    if (*sort_needed == 0) return;
+    // after a wait that gave up in an earlier pass the list this pass reads
+    // no longer has the digit totals dstart was made from, so a scatter
+    // could leave the output: the remaining passes do nothing
+    if (*sort_needed == 0 || *(volatile const uint32_t*)err != 0) return;
     const uint32_t nb = 1u << bits, mask = nb - 1;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
@@ -204,7 +221,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
             acc += c;
         }
         loff[d] = acc;
-        st[d] = tag | (tile == 0 ? kInc : kAgg) | acc;
+        if (tile != withhold) st[d] = tag | (tile == 0 ? kInc : kAgg) | acc;
     }
     __syncthreads();
     // exclusive scan of the tile totals over digits (each thread a run of digits)
@@ -282,7 +299,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
                 if (found) break;
                 next -= used;
                 if (stalled) {
-                    if (++polls > kSpinLimit) {
+                    if (++polls > spin_limit) {
                         atomicOr(err, 1u);
                         break;
                     }
@@ -292,7 +309,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
                 }
             }
             const uint32_t cnt_d = (d + 1 < nb ? loff[d + 1] : n) - loff[d];
-            st[d] = tag | kInc | (excl + cnt_d);
+            if (tile != withhold) st[d] = tag | kInc | (excl + cnt_d);
         }
         tbase[d] = dstart[d] + excl;
     }
@@ -724,17 +741,21 @@ CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
     return L;
 }
 
+// The opt-in shared-memory sizes of the sort kernels, set once per device
+// for each id width.
+PerDeviceOnce g_csr_attrs[2];
 template <typename Id>
-void set_csr_attributes()
+cudaError_t set_csr_attributes()
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(radix_scatter_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem_bytes<Id>());
-        cudaFuncSetAttribute(radix_hist_all_kernel<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kMaxPasses * 4 * kMaxBuckets));
-        attr = true;
-    }
+    return g_csr_attrs[sizeof(Id) == 8].run_current([] {
+        return first_error({
+            cudaFuncSetAttribute(radix_scatter_kernel<Id>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)scatter_smem_bytes<Id>()),
+            cudaFuncSetAttribute(radix_hist_all_kernel<Id>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kMaxPasses * 4 * kMaxBuckets))});
+    });
 }
 
 // LSD radix passes over M pairs starting at `in` (dst digits, then src
@@ -776,8 +797,12 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
     const P* cur = in;
     int which = 0;
     cudaError_t err_c;
+    const CsrWaitHook hk = csr_wait_hook();
+    // the tickets and the wait error word start at zero on every call that
+    // has edges (a call without edges has nothing to sort and no wait)
+    if (M > 0 && cudaMemsetAsync(ws + L.off_flag + 64, 0, 128, s) != cudaSuccess)
+        return cudaErrorUnknown;
     if (M > 0 && pl.n > 0) {
-        if (cudaMemsetAsync(ws + L.off_flag + 64, 0, 128, s) != cudaSuccess) return cudaErrorUnknown;
         if (cudaMemsetAsync(tot, 0, (size_t)pl.n * kMaxBuckets * 8, s) != cudaSuccess)
             return cudaErrorUnknown;
         {
@@ -795,7 +820,8 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
             TraceScope trace("csr_radix_scatter", s);
             radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
                 cur, buf[which], M, pl.field[k], pl.shift[k], pl.bits[k], status, k,
-                dstart + (size_t)k * kMaxBuckets, tickets + k, err, sort_needed);
+                dstart + (size_t)k * kMaxBuckets, tickets + k, err, sort_needed, hk.spin_limit,
+                hk.withhold);
             if ((err_c = cudaGetLastError()) != cudaSuccess) return err_c;
             cur = buf[which];
             which ^= 1;
@@ -831,10 +857,10 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
 {
     using P = typename PairOf<Id>::T;
     const CsrLayout L = csr_layout(M, N, sizeof(P));
-    set_csr_attributes<Id>();
+    cudaError_t err;
+    if ((err = set_csr_attributes<Id>()) != cudaSuccess) return err;
     unsigned char* ws = (unsigned char*)d_ws;
     uint32_t* sort_needed = (uint32_t*)(ws + L.off_flag);
-    cudaError_t err;
     const int grid = sort_grid(M + 1);
     if (cudaMemsetAsync(sort_needed, 0, 4, s) != cudaSuccess) return cudaErrorUnknown;
     if (cudaMemsetAsync(d_row_ptr, 0, (N + 1) * 8, s) != cudaSuccess) return cudaErrorUnknown;
@@ -886,10 +912,10 @@ cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t 
 {
     using P = typename PairOf<Id>::T;
     const OptsLayout O = opts_layout(M, N, flags, sizeof(P));
-    set_csr_attributes<Id>();
+    cudaError_t err;
+    if ((err = set_csr_attributes<Id>()) != cudaSuccess) return err;
     unsigned char* ws = (unsigned char*)d_ws;
     uint32_t* sort_needed = (uint32_t*)(ws + O.L.off_flag);
-    cudaError_t err;
     const uint64_t M2 = O.M2;
     // every option needs the sorted list: the sort kernels run unconditionally
     if (cudaMemsetAsync(sort_needed, 1, 4, s) != cudaSuccess) return cudaErrorUnknown;
@@ -924,6 +950,12 @@ cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t 
 }
 
 }  // namespace
+
+void set_csr_wait_hook(uint32_t spin_limit, uint32_t withhold_tile)
+{
+    g_hook_spin.store(spin_limit ? spin_limit : kSpinLimit);
+    g_hook_withhold.store(withhold_tile);
+}
 
 size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices)
 {

@@ -19,7 +19,6 @@ namespace pgen {
 namespace {
 
 constexpr size_t kScratchBytes = (size_t)32 << 20;   // 32 MiB, see pgen.h
-constexpr int kMaxDevices = 64;
 
 // Device-side scratch for gen_pba_noalloc. Every GPU that loads this part of
 // the library holds it until the process exits.

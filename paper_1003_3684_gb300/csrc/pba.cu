@@ -893,23 +893,27 @@ PbaBuffers pba_buffers(const PbaGeom& g, void* d_ws)
 constexpr size_t kSmemFast = kEmitWarps * sizeof(EmitWarpSmem<uint32_t>);
 constexpr size_t kSmemWide = kEmitWarps * sizeof(EmitWarpSmem<uint64_t>);
 
-void set_pba_attributes()
+// The opt-in shared-memory sizes of the kernels that need more than the
+// default, set once per device.
+PerDeviceOnce g_pba_attrs;
+cudaError_t set_pba_attributes()
 {
-    static bool done = false;
-    if (done) return;
-    cudaFuncSetAttribute(pba_prefix_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kPrefixMax * 2 + kMaxBlocks * 4));
-    cudaFuncSetAttribute(pba_prefix_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kPrefixMax * 2 + kMaxBlocks * 4));
-    cudaFuncSetAttribute(pba_emit_kernel<uint32_t, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast);
-    cudaFuncSetAttribute(pba_emit_kernel<uint64_t, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast);
-    cudaFuncSetAttribute(pba_emit_kernel<uint32_t, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide);
-    cudaFuncSetAttribute(pba_emit_kernel<uint64_t, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide);
-    done = true;
+    return g_pba_attrs.run_current([] {
+        const int prefix = (int)(kPrefixMax * 2 + kMaxBlocks * 4);
+        return first_error({
+            cudaFuncSetAttribute(pba_prefix_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, prefix),
+            cudaFuncSetAttribute(pba_prefix_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, prefix),
+            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast),
+            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast),
+            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide),
+            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide)});
+    });
 }
 
 }  // namespace
@@ -919,9 +923,9 @@ void set_pba_attributes()
 cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
 {
     if (g.B > kMaxBlocks) return cudaErrorInvalidValue;
-    set_pba_attributes();
-    const PbaBuffers W = pba_buffers(g, d_ws);
     cudaError_t err;
+    if ((err = set_pba_attributes()) != cudaSuccess) return err;
+    const PbaBuffers W = pba_buffers(g, d_ws);
     if ((err = cudaMemsetAsync(W.cnt, 0, (size_t)g.B * g.S * g.B * 4, s)) != cudaSuccess) return err;
     if ((err = cudaMemsetAsync(W.wide, 0, 4, s)) != cudaSuccess) return err;
     if (g.N_e > 0) {
@@ -967,9 +971,9 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
 {
     if (g.B > kMaxBlocks || b_begin > b_end || b_end > g.B) return cudaErrorInvalidValue;
     if (b_begin == b_end) return cudaSuccess;
-    set_pba_attributes();
-    const PbaBuffers W = pba_buffers(g, const_cast<void*>(d_ws));
     cudaError_t err;
+    if ((err = set_pba_attributes()) != cudaSuccess) return err;
+    const PbaBuffers W = pba_buffers(g, const_cast<void*>(d_ws));
     // every R_q + e0 < 2^32 is certain when all entries together are fewer
     const bool surely_fast =
         !g_ever_forced.load() && (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);

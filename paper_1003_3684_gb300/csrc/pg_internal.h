@@ -5,11 +5,56 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <initializer_list>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "pg_common.cuh"
 
 namespace pgen {
+
+// Once-per-device set-up (kernel attributes such as the opt-in shared-memory
+// size apply to the device that is current when they are set). run() calls
+// `setup` the first time it sees a device id, under a mutex, and remembers
+// its status: every later call for that device returns the same status
+// without calling it again. Ids outside [0, kMaxDevices) fail.
+constexpr int kMaxDevices = 64;
+class PerDeviceOnce {
+public:
+    template <class F>
+    cudaError_t run(int dev, F&& setup)
+    {
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu_);
+        if (!done_[dev]) {
+            status_[dev] = setup();
+            done_[dev] = true;
+        }
+        return status_[dev];
+    }
+    // The same, for the device that is current on this host thread.
+    template <class F>
+    cudaError_t run_current(F&& setup)
+    {
+        int dev = 0;
+        const cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        return run(dev, setup);
+    }
+
+private:
+    std::mutex mu_;
+    bool done_[kMaxDevices] = {};
+    cudaError_t status_[kMaxDevices] = {};
+};
+
+// The first failure among several CUDA calls (cudaSuccess when none failed).
+inline cudaError_t first_error(std::initializer_list<cudaError_t> errs)
+{
+    for (cudaError_t e : errs)
+        if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
 
 constexpr int kMaxKronThr = 255;   // n0 <= 16 -> at most 255 thresholds
 
@@ -104,6 +149,7 @@ cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
                             cudaStream_t s);
 size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices);
 size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64);
+void set_csr_wait_hook(uint32_t spin_limit, uint32_t withhold_tile);
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                        uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,
                        cudaStream_t s);

@@ -5,8 +5,8 @@ time. The server keeps a FIFO of waiting requests and a byte budget of device
 memory. At every scheduling step it
   1. retires batches whose CUDA event has completed (their requests are done;
      latency = completion - arrival),
-  2. admits waiting requests, in arrival order, while their bytes (edge list
-     while generating + CSR kept on the device) fit the remaining budget,
+  2. drops waiting requests whose deadline has passed, then admits waiting
+     requests, in arrival order, while their bytes fit the remaining budget,
   3. launches the admitted requests as one batch on a free stream: one
      persistent generation launch for all of them (gen_batch), then each
      request's CSR (edges_to_csr) on the same stream, then an event.
@@ -14,6 +14,15 @@ Batches on different streams overlap on the GPU, so requests that arrive
 while others are running are admitted and started as soon as a stream and
 memory free up -- continuous batching rather than a queue drained in rounds.
 Results stay on the device until the client releases them.
+
+A request's bytes are its edge list, its CSR and the CSR call's workspace;
+the edge list and the workspace are given back when its batch retires, the
+CSR when the client releases it. A request can be cancelled at any time (a
+running one still finishes on the device, and its results are dropped when
+its batch retires) and can carry a deadline, the latest time it may start:
+a request still waiting at its deadline expires without running. Each CSR
+call's bounded-wait status is copied to pinned host memory on the batch's
+stream; a request whose sort gave up waiting is reported failed, not done.
 
 The server never synchronises the device except through event queries; the
 only host work per request is planning and launching.
@@ -51,11 +60,22 @@ def job_vertices(job) -> int:
     return job["initiator_n0"] ** job["k"] if "initiator_n0" in job else len(job["initiator"]) ** job["k"]
 
 
+def job_csr_bytes(job) -> int:
+    """Device bytes of a request's CSR: row_ptr (8 B/vertex) and col (4 B/edge)."""
+    return (job_vertices(job) + 1) * 8 + job_edges(job) * 4
+
+
+def job_transient_bytes(job) -> int:
+    """Device bytes a request needs only until its batch retires: the edge
+    list (8 B/edge) and the workspace of its CSR call."""
+    import paper_1003_3684_gb300 as pg
+    E = job_edges(job)
+    return E * 8 + pg.pg_csr_workspace_size(E, job_vertices(job))
+
+
 def job_bytes(job) -> int:
-    """Device bytes a request holds: edge list (8 B/edge, freed after CSR) and
-    its CSR (row_ptr 8 B/vertex, col 4 B/edge)."""
-    E, N = job_edges(job), job_vertices(job)
-    return E * 8 + (N + 1) * 8 + E * 4
+    """Device bytes a request holds at its peak: edge list, CSR workspace and CSR."""
+    return job_transient_bytes(job) + job_csr_bytes(job)
 
 
 @dataclass
@@ -64,6 +84,9 @@ class Request:
     job: dict
     arrival: float
     nbytes: int
+    deadline: float | None = None   # latest start time (server clock); None: no limit
+    state: str = "waiting"          # waiting, admitted, running, done, cancelled, expired, failed
+    error: str | None = None
     admitted: float | None = None
     launched: float | None = None
     done: float | None = None
@@ -82,6 +105,7 @@ class _Batch:
     stream: object
     event: object
     keep: list = field(default_factory=list)
+    status: object = None   # per request: the CSR call's wait word (pinned host memory)
 
 
 class Server:
@@ -104,6 +128,9 @@ class Server:
         self.waiting: deque[Request] = deque()
         self.admitted: deque[Request] = deque()
         self.completed: list[Request] = []
+        self.cancelled: list[Request] = []
+        self.expired: list[Request] = []
+        self.failed: list[Request] = []
         self._next_id = 0
         self.launches = 0
         self._cuda = False
@@ -116,46 +143,89 @@ class Server:
         self.pg, self.torch = pg, torch
         self.device = torch.device(self.device_name)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.n_streams)]
+        # the batch workspaces are held for the server's lifetime
         self.batch_ws = [torch.empty(pg.pg_batch_workspace_size(), dtype=torch.uint8,
                                      device=self.device) for _ in range(self.n_streams)]
-        self.csr_ws = [None] * self.n_streams
+        self.in_use += sum(w.numel() for w in self.batch_ws)
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
         self._cuda = True
 
     # ------------------------------------------------------------------
-    def submit(self, job: dict, now: float | None = None) -> Request:
+    def submit(self, job: dict, now: float | None = None, deadline: float | None = None) -> Request:
+        """Queue a request. `deadline` (server clock) is the latest time it may
+        start; a request still waiting then expires without running."""
         now = self.clock() if now is None else now
-        r = Request(self._next_id, job, now, job_bytes(job))
+        r = Request(self._next_id, job, now, job_bytes(job), deadline=deadline)
         if r.nbytes > self.budget:
             raise ValueError(f"request of {r.nbytes} bytes exceeds the {self.budget}-byte budget")
         self._next_id += 1
         self.waiting.append(r)
         return r
 
+    def cancel(self, r: Request) -> bool:
+        """Withdraw a request. A waiting or admitted one is dropped at once (its
+        budget is returned); a running one still finishes on the device, and
+        its results and bytes are dropped when its batch retires. Returns
+        False when the request had already finished or left the server."""
+        if r.state == "waiting":
+            self.waiting.remove(r)
+        elif r.state == "admitted":
+            self.admitted.remove(r)
+            self._give_back(r, r.held)
+        elif r.state != "running":
+            return False
+        r.state = "cancelled"
+        if r not in self.cancelled:
+            self.cancelled.append(r)
+        return True
+
     def release(self, r: Request):
         """Client is done with a result: free its device memory and budget."""
         r.row_ptr = r.col = None
-        self.in_use -= r.held
-        r.held = 0
+        self._give_back(r, r.held)
 
     def pending(self) -> int:
         return len(self.waiting) + len(self.admitted) + sum(b is not None for b in self.busy.values())
 
     # ------------------------------------------------------------------
+    def _give_back(self, r: Request, nbytes: int):
+        self.in_use -= nbytes
+        r.held -= nbytes
+
     def _retire(self, now):
         for i, b in self.busy.items():
-            if b is not None and b.event.query():
-                for r in b.requests:
-                    r.done = now
-                    # the edge list is dropped once its CSR exists
-                    self.in_use -= job_edges(r.job) * 8
-                    r.held -= job_edges(r.job) * 8
-                    self.completed.append(r)
-                self.busy[i] = None
+            if b is None or not b.event.query():
+                continue
+            for k, r in enumerate(b.requests):
+                # the edge list and the CSR workspace are dropped once the CSR exists
+                self._give_back(r, job_transient_bytes(r.job))
+                if r.state == "cancelled":
+                    self.release(r)
+                    continue
+                r.done = now
+                if b.status is not None and int(b.status[k]) != 0:
+                    r.state, r.error = "failed", "CSR sort: a bounded wait gave up (PG_ETIMEOUT)"
+                    self.release(r)
+                    self.failed.append(r)
+                    continue
+                r.state = "done"
+                self.completed.append(r)
+            self.busy[i] = None
+
+    def _expire(self, now):
+        for q in (self.waiting, self.admitted):
+            for r in [r for r in q if r.deadline is not None and now > r.deadline]:
+                q.remove(r)
+                if r.held:
+                    self._give_back(r, r.held)
+                r.state = "expired"
+                self.expired.append(r)
 
     def _admit(self, now):
         while self.waiting and self.in_use + self.waiting[0].nbytes <= self.budget:
             r = self.waiting.popleft()
             r.admitted = now
+            r.state = "admitted"
             r.held = r.nbytes
             self.in_use += r.nbytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
@@ -205,26 +275,33 @@ class Server:
                     pg.gen_batch(plan, arena=arena, workspace=self.batch_ws[i], stream=s)
                     self.launches += 1
                     offsets = [int(x) for x in plan.offsets]
+                # one CSR workspace for the batch, sized for its largest
+                # request (each request's share is counted in its bytes)
                 need = max(pg.pg_csr_workspace_size(job_edges(r.job), job_vertices(r.job))
                            for r in batch)
-                if self.csr_ws[i] is None or self.csr_ws[i].numel() < need:
-                    self.csr_ws[i] = torch.empty(need, dtype=torch.uint8, device=self.device)
+                ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+                status = torch.zeros(len(batch), dtype=torch.int32, pin_memory=True)
                 for k, r in enumerate(batch):
                     a = offsets[k]
                     z = a + job_edges(r.job)
-                    r.row_ptr, r.col = pg.edges_to_csr(arena[a:z], job_vertices(r.job),
-                                                       workspace=self.csr_ws[i], stream=s)
+                    E, N = job_edges(r.job), job_vertices(r.job)
+                    r.row_ptr, r.col = pg.edges_to_csr(arena[a:z], N, workspace=ws, stream=s)
+                    off = pg.pg_csr_wait_error_offset(E, N)
+                    if off is not None:   # the call's wait word, to pinned memory
+                        status[k:k + 1].copy_(ws[off:off + 4].view(torch.int32), non_blocking=True)
                     r.launched = now
+                    r.state = "running"
                     self.launches += 1
                 ev = torch.cuda.Event()
                 ev.record(s)
-            self.busy[i] = _Batch(batch, s, ev, keep=[plan, arena])
+            self.busy[i] = _Batch(batch, s, ev, keep=[plan, arena, ws], status=status)
 
     def step(self, now: float | None = None) -> int:
         """One scheduling step; returns the number of requests completed."""
         now = self.clock() if now is None else now
         before = len(self.completed)
         self._retire(now)
+        self._expire(now)
         self._admit(now)
         self._launch(now)
         return len(self.completed) - before

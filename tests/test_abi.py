@@ -186,3 +186,51 @@ def test_csr_wait_error_word_absent_when_nothing_is_sorted(L):
     assert pg.pg_csr_wait_error_offset(50, 1) is None          # a single row
     assert pg.pg_csr_wait_error_offset(50, 10, flags=16) is None
     assert pg.pg_csr_wait_error_offset(50, 10, flags=1) is not None
+
+
+def _per_device_once(L, devs, threads, fail_dev):
+    n = len(devs)
+    d = (C.c_int * max(n, 1))(*devs)
+    calls = (C.c_int * 64)()
+    status = (C.c_int * max(n, 1))()
+    L.pg_test_per_device_once.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                          C.c_void_p]
+    L.pg_test_per_device_once.restype = C.c_int
+    st = L.pg_test_per_device_once(d, n, threads, fail_dev, calls, status)
+    return st, list(calls), list(status)[:n]
+
+
+def test_kernel_attributes_are_set_once_per_device(L):
+    # the bookkeeping that guards cudaFuncSetAttribute: every device gets its
+    # own set-up, exactly once, however many host threads race for it
+    devs = [0, 1, 0, 3, 1, 7, 63, 0, 3]
+    for threads in (1, 8, 64):
+        st, calls, status = _per_device_once(L, devs, threads, -1)
+        assert st == 0
+        assert calls[0] == calls[1] == calls[3] == calls[7] == calls[63] == 1
+        assert sum(calls) == 5
+        assert status == [0] * len(devs)
+
+
+def test_failed_device_setup_is_remembered(L):
+    # a device whose set-up failed keeps failing (no retry, no partial state),
+    # other devices are unaffected; ids outside 0..63 fail without a set-up
+    st, calls, status = _per_device_once(L, [2, 5, 2, 5, 64, -1], 16, 5)
+    assert st == 0
+    assert calls[2] == 1 and calls[5] == 1 and sum(calls) == 2
+    assert status[0] == status[2] == 0
+    assert status[1] != 0 and status[3] == status[1]
+    assert status[4] != 0 and status[5] != 0
+    assert _per_device_once(L, [0], 0, -1)[0] == 1        # threads < 1: invalid
+
+
+def test_csr_check_arguments_on_host(L):
+    L.pg_csr_check.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_uint32,
+                               C.c_void_p]
+    L.pg_csr_check.restype = C.c_int
+    assert L.pg_csr_check(None, 10, 10, 0, 16, None) == 1    # unknown flag
+    assert L.pg_csr_check(None, 10, 10, 7, 0, None) == 1     # bad id width
+    # nothing to sort (no edges, or one vertex): no wait, nothing read
+    assert L.pg_csr_check(None, 0, 10, 0, 0, None) == 0
+    assert L.pg_csr_check(None, 10, 1, 0, 0, None) == 0
+    assert L.pg_csr_check(None, 10, 10, 0, 0, None) == 1     # a sorting call needs its workspace

@@ -1,5 +1,6 @@
 """Host-side pieces of the benchmark that need no GPU: the DRAM-traffic table
 the roofline reads, and the labelled all-cores estimate of the CPU baseline."""
+import json
 import os
 import re
 
@@ -9,35 +10,41 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _traffic_rows():
-    rows = []
-    for ln in open(os.path.join(ROOT, "profiles", "dram_traffic.md")).read().splitlines():
-        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 6 and cells[0].startswith("`"):
-            rows.append(cells)
-    return rows
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
+        return json.load(fh)["kernels"]
 
 
 def test_traffic_table_rows_are_well_formed():
     rows = _traffic_rows()
     assert rows, "no rows"
-    for kernel, src, sha, per_unit, unit, capture in (r[:6] for r in rows):
-        assert os.path.isfile(os.path.join(ROOT, src.strip("`"))), src
-        assert re.fullmatch(r"`[0-9a-f]{12}`", sha), sha
-        assert float(per_unit) > 0
-        name = re.search(r"`([^`]+\.md)`", capture).group(1)
-        assert os.path.isfile(os.path.join(ROOT, "profiles", name)), capture
+    for r in rows:
+        assert os.path.isfile(os.path.join(ROOT, r["source"])), r["source"]
+        assert re.fullmatch(r"[0-9a-f]{12}", r["sha256"]), r["sha256"]
+        assert float(r["bytes_per_unit"]) > 0 and r["unit"]
+        name = re.match(r"([\w.-]+\.md)", r["capture"]).group(1)
+        assert os.path.isfile(os.path.join(ROOT, "profiles", name)), r["capture"]
 
 
 def test_traffic_table_keeps_only_rows_of_the_current_sources():
     # a row applies only while its source still has the recorded hash
     got = bench.dram_traffic_table()
     import hashlib
-    for kernel, src, sha, per_unit, *_ in _traffic_rows():
-        cur = hashlib.sha256(open(os.path.join(ROOT, src.strip("`")), "rb").read()).hexdigest()[:12]
-        if cur == sha.strip("`"):
-            assert got[kernel.strip("`")] == float(per_unit)
+    for r in _traffic_rows():
+        cur = hashlib.sha256(open(os.path.join(ROOT, r["source"]), "rb").read()).hexdigest()[:12]
+        if cur == r["sha256"]:
+            assert got[r["kernel"]] == float(r["bytes_per_unit"])
         else:
-            assert kernel.strip("`") not in got
+            assert r["kernel"] not in got
+
+
+def test_default_run_names_its_sub_records():
+    # the default line carries the metric's other parts, each a known workload
+    from paper_1003_3684_gb300 import workloads as W
+    keys = [k for k, _, _ in bench.SUB_RECORDS]
+    assert keys == ["kron", "batch", "serve"]
+    for _, workload, over in bench.SUB_RECORDS:
+        assert workload in W.CONFIGS
+        assert W.CONFIGS[workload]["kind"] in ("kron", "batch", "serve")
 
 
 def test_all_cores_estimate_is_labelled():

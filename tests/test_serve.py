@@ -15,7 +15,10 @@ class FakeEvent:
 
 
 class FakeServer(serve.Server):
-    """Server whose 'device' finishes a batch 1 ms per million edges later."""
+    """Server whose 'device' finishes a batch 1 ms per million edges later.
+    `fail` holds request ids whose CSR sort reports a wait that gave up."""
+
+    fail = ()
 
     def _launch(self, now):
         for i, b in self.busy.items():
@@ -24,8 +27,11 @@ class FakeServer(serve.Server):
             batch = self._next_batch()
             for r in batch:
                 r.launched = now
+                r.state = "running"
             cost = sum(serve.job_edges(r.job) for r in batch) / 1e9
-            self.busy[i] = serve._Batch(batch, None, FakeEvent(self.clock, now + cost))
+            status = np.array([1 if r.rid in self.fail else 0 for r in batch], np.int32)
+            self.busy[i] = serve._Batch(batch, None, FakeEvent(self.clock, now + cost),
+                                        status=status)
             self.launches += 1
 
 
@@ -76,6 +82,78 @@ def test_requests_arriving_while_busy_are_started_without_waiting_for_all():
         advance(1e-3)
         srv.step()
     assert small.done < big.done
+
+
+def run_until_idle(srv, advance, release=True):
+    while srv.pending():
+        srv.step()
+        if release:
+            for r in srv.completed:
+                srv.release(r)
+        advance(1e-3)
+
+
+def test_cancel_waiting_admitted_and_running_requests():
+    clock, advance = fake_clock()
+    jobs = [serve.job_for_edges("kron", 2**22, seed=i) for i in range(4)]
+    one = serve.job_bytes(jobs[0])
+    srv = FakeServer(budget_bytes=2 * one, n_streams=1, max_batch_jobs=1, clock=clock)
+    a, b, c, d = [srv.submit(j, now=0.0) for j in jobs]
+    srv.step()                       # a running, b admitted (budget for two), c and d waiting
+    assert (a.state, b.state, c.state, d.state) == ("running", "admitted", "waiting", "waiting")
+    assert srv.cancel(c) and c.state == "cancelled" and c not in srv.waiting
+    held_before = srv.in_use
+    assert srv.cancel(b) and srv.in_use == held_before - one and b.held == 0
+    assert srv.cancel(a) and a.state == "cancelled"     # still on the device
+    assert srv.in_use == one                             # a's bytes stay until its batch retires
+    run_until_idle(srv, advance)
+    assert a.done is None and a not in srv.completed and a.held == 0
+    assert d.state == "done" and srv.completed == [d]
+    assert srv.in_use == 0 and srv.peak_in_use <= 2 * one
+    assert not srv.cancel(d)                             # finished: nothing to cancel
+    assert all(r.launched is None for r in (b, c))
+
+
+def test_deadline_expires_waiting_requests_only():
+    clock, advance = fake_clock()
+    big = serve.job_for_edges("kron", 2**24, seed=0)
+    small = serve.job_for_edges("pba", 2**12, seed=1)
+    srv = FakeServer(budget_bytes=serve.job_bytes(big) + serve.job_bytes(small) // 2,
+                     n_streams=1, clock=clock)
+    r0 = srv.submit(big, now=0.0, deadline=0.0)          # starts at once: no expiry
+    r1 = srv.submit(small, now=0.0, deadline=5e-3)       # waits for budget, expires at 5 ms
+    r2 = srv.submit(small, now=0.0)                      # no deadline: waits and runs
+    srv.step()
+    assert r0.state == "running" and r1.state == "waiting"
+    run_until_idle(srv, advance)
+    assert r0.state == "done" and r2.state == "done"
+    assert r1.state == "expired" and r1.launched is None and r1 in srv.expired
+    assert r2.launched > r1.deadline
+    assert srv.in_use == 0
+
+
+def test_failed_csr_wait_is_reported_not_completed():
+    clock, advance = fake_clock()
+    jobs = [serve.job_for_edges("pba", 2**14, seed=i) for i in range(6)]
+    srv = FakeServer(budget_bytes=1 << 40, n_streams=2, clock=clock)
+    srv.fail = {2, 4}
+    reqs = [srv.submit(j, now=0.0) for j in jobs]
+    run_until_idle(srv, advance)
+    assert [r.rid for r in srv.failed] == [2, 4]
+    assert all(r.state == "failed" and "PG_ETIMEOUT" in r.error and r.held == 0
+               for r in srv.failed)
+    assert sorted(r.rid for r in srv.completed) == [0, 1, 3, 5]
+    assert srv.in_use == 0 and len(reqs) == 6
+
+
+def test_request_bytes_count_the_csr_workspace():
+    import paper_1003_3684_gb300 as pg
+    for kind, E in (("pba", 2**12), ("kron", 2**20)):
+        j = serve.job_for_edges(kind, E, seed=0)
+        N = serve.job_vertices(j)
+        ws = pg.pg_csr_workspace_size(serve.job_edges(j), N)
+        assert ws > 0
+        assert serve.job_bytes(j) == serve.job_edges(j) * 12 + (N + 1) * 8 + ws
 
 
 def test_oversized_request_is_rejected():
