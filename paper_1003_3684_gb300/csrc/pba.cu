@@ -58,6 +58,7 @@ constexpr uint64_t kLevelDiv = 2;   // phase-1 level [L, L + L/kLevelDiv)
 constexpr int kEmitItems = 8;
 constexpr uint32_t kEmitRun = 32 * kEmitItems;                   // 256 entries per warp run
 constexpr uint32_t kMaxBlocks = 1024;
+constexpr uint32_t kSeedTab = 256;   // seed clique edges in the lean links' table: n0 <= 23
 constexpr int kBaThreads = 256;
 template <typename Id>
 struct BaShape {   // 32 KB of staging for either id width
@@ -213,9 +214,9 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     bool pend = false;
     uint32_t pend_k = 0, pend_v = 0;
     uint32_t own = 0;   // entries equal to p (the most frequent value) counted here
-    while (__any_sync(0xFFFFFFFFu, active || pend)) {
-        // every lane draws (an idle lane's draw is discarded), so the trip is
-        // straight-line code apart from the deferred store
+    // every lane draws (an idle lane's draw is discarded), so the trip is
+    // straight-line code apart from the deferred store
+    auto trip = [&]() {
         const uint4 w = philox_headed(cur, ph, g.key);
         if (pend) my[pend_k] = (uint16_t)pend_v;   // the value loaded one trip ago
         const bool coin = coin_on && w.z < g.coin_thr;
@@ -229,20 +230,21 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
             v = F.fresh(w.w, g);
         }
         if (active && hit) v = __ldg(Ap + r);
-        if (done) {
-            pend_v = v;
-            pend_k = item;
-        }
+        pend_v = done ? v : pend_v;
+        pend_k = done ? item : pend_k;
         pend = done;
-        if (active && !done) cur = r;
+        cur = (active && !done) ? r : cur;
         const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
-        if (done) {
-            item = next + __popc(dm & lt);
-            cur = run + item;
-            active = item < n_items;
-        }
+        const uint32_t nit = next + __popc(dm & lt);
         next += __popc(dm);
-    }
+        item = done ? nit : item;
+        cur = done ? run + nit : cur;
+        active = done ? nit < n_items : active;
+    };
+    // trips while unclaimed entries remain (`next` is the same in every
+    // lane), then until every lane's chain and deferred store are done
+    while (next < n_items) trip();
+    while (__any_sync(0xFFFFFFFFu, active || pend)) trip();
     __syncwarp();
     // counts of the finished run, outside the pooled loop (converged lanes)
     for (uint32_t t = lane; t < n_items; t += 32) {
@@ -309,8 +311,13 @@ __global__ void __launch_bounds__(1024) pba_scan_kernel(const uint32_t* __restri
                                                         QRecip* __restrict__ recip, uint32_t nb,
                                                         uint32_t B, uint32_t rows, uint64_t e0,
                                                         uint32_t force_wide,
-                                                        uint32_t* __restrict__ wide_flag)
+                                                        uint32_t* __restrict__ wide_flag,
+                                                        uint32_t n0, uint32_t* __restrict__ stab)
 {
+    // the seed clique's edges for the emit's lean links (a | b << 16)
+    if (blockIdx.x == 0)
+        for (uint32_t e = threadIdx.x; e < kSeedTab; e += blockDim.x)
+            stab[e] = e < e0 ? seed_endpoint(e, 0, n0) | (seed_endpoint(e, 1, n0) << 16) : 0u;
     __shared__ uint64_t part[32][33];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t q = blockIdx.x * 32 + lane;
@@ -411,6 +418,37 @@ __device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip
     v = seed ? vs : g.n0 + sigma32(e2, c);
     const bool fin = seed || side == 0;
     cur = fin ? cur : e2;
+    return fin;
+}
+
+// The same link with sigma(cur) carried in from the previous link (the
+// side-0 value of a link is sigma of the edge the chain moves to, so each
+// link computes one sigma instead of two), n_b a power of two, and the seed
+// clique's edges read from a table in the workspace (stab[e] = a | b << 16;
+// every lane reads entry 0 unless it hit a seed slot, so the load is a
+// broadcast from L1)
+// instead of a branch: straight-line code apart from nothing.
+__device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, uint32_t q,
+                                            const QRecip& c, const PbaGeom& g,
+                                            const uint32_t* __restrict__ stab, uint32_t& v)
+{
+    const uint32_t nb = (uint32_t)g.n_b;
+    const uint32_t before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
+    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
+    const uint32_t e0 = (uint32_t)g.e0;
+    const uint32_t X = e0 + before;
+    const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
+    const uint32_t e = (uint32_t)(s >> 32);
+    const uint32_t side = ((uint32_t)s) >> 31;
+    const uint32_t e2 = e - e0;
+    const uint32_t sig2 = sigma32(e2, c);
+    const bool seed = e < e0;
+    const uint32_t ab = __ldg(stab + (seed ? e : 0));
+    const uint32_t vs = side ? (ab >> 16) : (ab & 0xFFFFu);
+    v = seed ? vs : g.n0 + sig2;
+    const bool fin = seed || side == 0;
+    cur = fin ? cur : e2;
+    sig = fin ? sig : sig2;
     return fin;
 }
 
@@ -560,14 +598,17 @@ struct EmitWarpSmem {
     uint16_t qs[2][kEmitRun];  // target block of each entry of the run
 };
 
-template <typename Id, bool kFast>
+// kMode 0: 64-bit links (some R_q + e0 >= 2^32); 1: 32-bit links; 2: 32-bit
+// lean links (n_b a power of two, n0 <= 23).
+template <typename Id, int kMode>
 __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const __grid_constant__ PbaGeom g, const uint16_t* __restrict__ A,
     const uint64_t* __restrict__ off, const uint64_t* __restrict__ R,
     const FastDiv* __restrict__ divR, const QRecip* __restrict__ recip,
-    const uint32_t* __restrict__ wide_flag, Id* __restrict__ out, uint32_t block_off,
-    uint32_t out_block0)
+    const uint32_t* __restrict__ wide_flag, const uint32_t* __restrict__ stab,
+    Id* __restrict__ out, uint32_t block_off, uint32_t out_block0)
 {
+    constexpr bool kFast = kMode != 0;
     using CurT = typename std::conditional<kFast, uint32_t, uint64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if ((*wide_flag == 0) != kFast) return;   // the other variant does the work
@@ -640,10 +681,39 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
         }
         if (runs > 2) load_run(2, qv);   // in flight during run 0's chains
         // pooled chains over the segment: entry gk of the segment lives in
-        // buffer (gk / kEmitRun) & 1; claims are handed out in entry order
-        uint32_t gk = lane, next = 32, q = 0, cur = 0;
+        // buffer (gk / kEmitRun) & 1, at flat index gk % (2 * kEmitRun);
+        // claims are handed out in entry order
+        CurT* item_all = &ws.item[0][0];
+        const uint16_t* qs_all = &ws.qs[0][0];
+        uint32_t gk = lane, next = 32, q = 0, cur = 0, sig = 0, k = 0;
         bool active = false;
         QRecip c{0, 0, 0, 0};
+        auto take = [&](uint32_t pos) {
+            k = pos % (2 * kEmitRun);
+            q = qs_all[k];
+            cur = (uint32_t)item_all[k];
+            c = recip[q];
+            if constexpr (kMode == 2) sig = sigma32(cur, c);
+        };
+        // one link for every lane; a lane whose chain ended stores its value
+        // and takes the next unclaimed entry (below `limit`)
+        auto trip = [&](uint32_t limit) {
+            uint32_t v;
+            bool fin;
+            if constexpr (kMode == 2) fin = t_link_lean(cur, sig, q, c, g, stab, v);
+            else fin = t_link32(cur, q, c, g, v);
+            const bool done = fin && active;
+            if (done) item_all[k] = v;
+            const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
+            const uint32_t pos = next + __popc(dm & lt);
+            next += __popc(dm);
+            const bool tk = done && pos < limit;
+            if (done) {
+                gk = pos;
+                active = tk;
+            }
+            if (tk) take(pos);
+        };
         for (uint32_t r = 0; r < runs; ++r) {
             const uint32_t n_r = (total - r * kEmitRun < kEmitRun) ? total - r * kEmitRun : kEmitRun;
             const uint32_t limit = (total - r * kEmitRun < 2 * kEmitRun) ? total
@@ -651,28 +721,15 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             const uint32_t r_end = r * kEmitRun + n_r;
             if (!active && gk < limit) {      // a claim in the newly ranked run
                 active = true;
-                q = ws.qs[(gk / kEmitRun) & 1][gk % kEmitRun];
-                cur = (uint32_t)ws.item[(gk / kEmitRun) & 1][gk % kEmitRun];
-                c = recip[q];
+                take(gk);
             }
             // run r is resolved once every entry before r_end has been claimed
-            // (claims go in entry order) and no active lane still holds one
-            while (next < r_end || __any_sync(0xFFFFFFFFu, active && gk < r_end)) {
-                uint32_t v;
-                const bool done = t_link32(cur, q, c, g, v) && active;
-                if (done) ws.item[(gk / kEmitRun) & 1][gk % kEmitRun] = v;
-                const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
-                if (done) {
-                    gk = next + __popc(dm & lt);
-                    active = gk < limit;
-                    if (active) {
-                        q = ws.qs[(gk / kEmitRun) & 1][gk % kEmitRun];
-                        cur = (uint32_t)ws.item[(gk / kEmitRun) & 1][gk % kEmitRun];
-                        c = recip[q];
-                    }
-                }
-                next += __popc(dm);
-            }
+            // (claims go in entry order) and no active lane still holds one:
+            // trips while entries of run r remain unclaimed (`next` is the same
+            // in every lane), then trips until the lanes holding its last
+            // entries are done
+            while (next < r_end) trip(limit);
+            while (__any_sync(0xFFFFFFFFu, active && gk < r_end)) trip(limit);
             __syncwarp();
             emit_buf(lo + (uint64_t)r * kEmitRun, n_r, ws.item[r & 1], ws.qs[r & 1]);
             if (r + 2 < runs) {
@@ -829,6 +886,8 @@ PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S)
     o += align256((size_t)B * sizeof(QRecip));
     w.off_flag = o;
     o += 256;
+    w.off_stab = o;
+    o += align256(kSeedTab * 4);
     w.total = o;
     return w;
 }
@@ -878,6 +937,7 @@ struct PbaBuffers {
     FastDiv* divR;
     QRecip* recip;
     uint32_t* wide;
+    uint32_t* stab;
 };
 
 PbaBuffers pba_buffers(const PbaGeom& g, void* d_ws)
@@ -887,11 +947,18 @@ PbaBuffers pba_buffers(const PbaGeom& g, void* d_ws)
     return PbaBuffers{(uint16_t*)(ws + L.off_A), (uint32_t*)(ws + L.off_cnt),
                       (uint64_t*)(ws + L.off_off), (uint64_t*)(ws + L.off_R),
                       (FastDiv*)(ws + L.off_magic), (QRecip*)(ws + L.off_recip),
-                      (uint32_t*)(ws + L.off_flag)};
+                      (uint32_t*)(ws + L.off_flag), (uint32_t*)(ws + L.off_stab)};
 }
 
 constexpr size_t kSmemFast = kEmitWarps * sizeof(EmitWarpSmem<uint32_t>);
 constexpr size_t kSmemWide = kEmitWarps * sizeof(EmitWarpSmem<uint64_t>);
+
+// the 32-bit emit variant for this geometry: lean links when n_b is a power
+// of two and the seed clique's edges fit the table
+bool lean_links(const PbaGeom& g)
+{
+    return g.nb_shift != 0xFFFFFFFFu && g.e0 <= kSeedTab;
+}
 
 // The opt-in shared-memory sizes of the kernels that need more than the
 // default, set once per device.
@@ -905,13 +972,17 @@ cudaError_t set_pba_attributes()
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, prefix),
             cudaFuncSetAttribute(pba_prefix_kernel<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, prefix),
-            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, true>,
+            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, 2>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast),
-            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, true>,
+            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, 2>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast),
-            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, false>,
+            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast),
+            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFast),
+            cudaFuncSetAttribute(pba_emit_kernel<uint32_t, 0>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide),
-            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, false>,
+            cudaFuncSetAttribute(pba_emit_kernel<uint64_t, 0>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWide)});
     });
 }
@@ -960,7 +1031,8 @@ cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
         TraceScope trace("pba_scan", s);
         pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(W.cnt, W.off, W.R, W.divR, W.recip,
                                                           (uint32_t)g.n_b, g.B, g.B * g.S, g.e0,
-                                                          wide_path_forced() ? 1u : 0u, W.wide);
+                                                          wide_path_forced() ? 1u : 0u, W.wide,
+                                                          g.n0, W.stab);
     }
     return cudaGetLastError();
 }
@@ -978,6 +1050,7 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
     const bool surely_fast =
         !g_ever_forced.load() && (uint64_t)g.B * g.N_e + g.e0 < ((uint64_t)1 << 32);
     const uint32_t nblk = b_end - b_begin;
+    const bool lean = lean_links(g);
     const uint32_t chunks = hc ? hc->chunks : 1;
     const uint32_t per = (nblk + chunks - 1) / chunks;
     const uint64_t edges_per_block = g.e0 + g.N_e;
@@ -988,17 +1061,25 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
         {
             TraceScope trace("pba_emit", s);
             if (id64) {
-                pba_emit_kernel<uint64_t, true><<<grid, kEmitThreads, kSmemFast, s>>>(
-                    g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint64_t*)d_out, b0, b_begin);
+                if (lean)
+                    pba_emit_kernel<uint64_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin);
+                else
+                    pba_emit_kernel<uint64_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin);
                 if (!surely_fast)
-                    pba_emit_kernel<uint64_t, false><<<grid, kEmitThreads, kSmemWide, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint64_t*)d_out, b0, b_begin);
+                    pba_emit_kernel<uint64_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin);
             } else {
-                pba_emit_kernel<uint32_t, true><<<grid, kEmitThreads, kSmemFast, s>>>(
-                    g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint32_t*)d_out, b0, b_begin);
+                if (lean)
+                    pba_emit_kernel<uint32_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin);
+                else
+                    pba_emit_kernel<uint32_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin);
                 if (!surely_fast)
-                    pba_emit_kernel<uint32_t, false><<<grid, kEmitThreads, kSmemWide, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, (uint32_t*)d_out, b0, b_begin);
+                    pba_emit_kernel<uint32_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin);
             }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

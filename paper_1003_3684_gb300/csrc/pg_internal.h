@@ -111,7 +111,7 @@ constexpr uint32_t kFacStride = kFacHeader + 2 * kFacSlots;
 
 // Workspace layout for B > 1 (all offsets 256-byte aligned).
 struct PbaWorkspace {
-    size_t off_A, off_cnt, off_off, off_R, off_magic, off_recip, off_flag, total;
+    size_t off_A, off_cnt, off_off, off_R, off_magic, off_recip, off_flag, off_stab, total;
 };
 PbaWorkspace pba_workspace_layout(uint64_t A_stride, uint32_t B, uint32_t S);
 uint32_t pba_segments(uint64_t N_e, uint32_t B, int sm_count);

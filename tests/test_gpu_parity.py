@@ -231,79 +231,6 @@ def test_pba_other_stream():
     assert_same(host(got), ref)
 
 
-@pytest.mark.slow
-def test_pba_headline_size_sampled():
-    """2^30 new vertices, 1024 blocks, m = 5, f = 0.1 -- the launch the
-    benchmark times. The oracle runs phase 1 for every block (threads over
-    independent blocks); blocks 0..7 are compared edge for edge (their slices
-    open every target's endpoint list, so the oracle's lists are short
-    prefixes), blocks 511 and 1023 on their own and one other target."""
-    cfg = W.CONFIGS["pba_n2p30_b1024_m5"]
-    n, m, B, n0, Wf, f, seed = (cfg[k] for k in ("n", "m", "blocks", "n0", "faction_width",
-                                                 "inter_frac", "seed"))
-    n_b, N_e, e0 = n // B, (n // B) * m, n0 * (n0 - 1) // 2
-    span, per = n0 + n_b, e0 + N_e
-    edges = pg.gen_pba(n, m, B, n0, Wf, f, seed)
-    torch.cuda.synchronize()
-    assert edges.shape[0] == B * per
-
-    # oracle phase 1 on every block
-    counts = np.zeros((B, B), np.uint64)
-    n_full = 8
-    sampled = {p: None for p in list(range(n_full)) + [511, B - 1]}
-
-    def run(p):
-        A, c, _ = o.pba_phase1(p, B, Wf, N_e, f, seed)
-        return p, (A if p in sampled else None), c
-
-    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
-        for p, A, c in ex.map(run, range(B)):
-            counts[p] = c
-            if A is not None:
-                sampled[p] = A
-    R = counts.sum(axis=0)
-    assert R.sum() == n * m
-
-    # per-block target counts of the GPU output (computed on the device)
-    e = edges.view(B, per, 2)
-    gpu_counts = np.zeros((B, B), np.int64)
-    for p in range(B):
-        q = (e[p, e0:, 1].to(torch.int64) & 0xFFFFFFFF) // span
-        gpu_counts[p] = torch.bincount(q, minlength=B).cpu().numpy()
-    assert np.array_equal(gpu_counts, counts.astype(np.int64))
-
-    start_all = np.concatenate([np.zeros((1, B), np.uint64), np.cumsum(counts, axis=0)[:-1]])
-    # every target's list up to the end of block n_full-1's slice, once
-    upto = start_all[n_full]
-
-    def prefix(q):
-        return q, o.pba_endpoints(q, int(R[q]), n_b, n0, seed, int(upto[q]))
-
-    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
-        T_pre = dict(ex.map(prefix, range(B)))
-    for p, A in sampled.items():
-        blk = host(e[p])
-        ids = np.arange(n0)
-        assert np.array_equal(blk[:e0], np.array([[p * span + a, p * span + b] for a in ids
-                                                  for b in ids if a < b], np.uint64))
-        gen = blk[e0:]
-        assert np.array_equal(gen[:, 0], p * span + n0 + np.arange(N_e, dtype=np.uint64) // m)
-        assert np.array_equal(gen[:, 1] // span, A.astype(np.uint64))
-        local = gen[:, 1] % span
-        if p < n_full:
-            for q in range(B):
-                sel = np.nonzero(A == q)[0]
-                s0 = int(start_all[p, q])
-                T = T_pre[q][s0:s0 + sel.size]
-                assert np.array_equal(local[sel], T.astype(np.uint64)), (p, q)
-            continue
-        for q in sorted({p, int(A[-1]), 0}):
-            sel = np.nonzero(A == q)[0]
-            s0 = int(start_all[p, q])
-            T = o.pba_endpoints(q, int(R[q]), n_b, n0, seed, s0 + sel.size)
-            assert np.array_equal(local[sel], T[s0:].astype(np.uint64)), (p, q)
-
-
 # --------------------------------------------------------------------------
 # PBA with general faction lists
 # --------------------------------------------------------------------------
