@@ -122,6 +122,38 @@ __device__ __forceinline__ void kron_level_full(uint32_t w, uint32_t u0, uint32_
     col = col * 2 + b;
 }
 
+// The full-initiator 2x2 pick for a job whose ids and edge indices fit 32
+// bits (k <= 32 levels, fewer than 2^32 edges): the same values with 32-bit
+// rows, columns and counters (e, 0, g, 3), the thresholds and k in registers
+// for the whole tile, whole groups of four levels unrolled.
+__device__ __forceinline__ void kron_edge_full32(const Key& key, uint32_t k, uint32_t u0,
+                                                 uint32_t u1, uint32_t u2, uint32_t e,
+                                                 uint32_t& row, uint32_t& col)
+{
+    row = 0;
+    col = 0;
+    uint32_t l = 0;
+    auto level = [&](uint32_t w) {
+        const uint32_t a = w > u1 ? 1u : 0u;
+        const uint32_t b = (w > u0 ? 1u : 0u) ^ a ^ (w > u2 ? 1u : 0u);
+        row = row * 2 + a;
+        col = col * 2 + b;
+    };
+    for (uint32_t g = 0; l + 4 <= k; ++g, l += 4) {
+        const uint4 w = philox(make_uint4(e, 0u, g, 3u), key);
+        level(w.x);
+        level(w.y);
+        level(w.z);
+        level(w.w);
+    }
+    if (l < k) {
+        const uint4 w = philox(make_uint4(e, 0u, l >> 2, 3u), key);
+        level(w.x);
+        if (l + 1 < k) level(w.y);
+        if (l + 2 < k) level(w.z);
+    }
+}
+
 __device__ __forceinline__ void kron_edge(const BatchJob& J, const Key& key,
                                           const uint32_t* pool, uint64_t e, uint64_t& row,
                                           uint64_t& col)
@@ -255,6 +287,28 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
                             J.n0 + fdiv32((uint32_t)(t0 + t2 + 1), J.div_m), (uint64_t)sDst[t2 + 1]);
                 else
                     put_pair(arena, e_first + t2, s0, (uint64_t)sDst[t2]);
+            }
+        } else if (J.n0 == 2 && J.n_zero == 0 && J.n_u == 3 && J.k <= 32 &&
+                   J.n_units <= 0xFFFFFFFFull) {
+            // 32-bit full-initiator descent (the kron2 kernel's arithmetic)
+            const uint32_t k = J.k, u0 = J.u0, u1 = J.u1, u2 = J.u2;
+            const uint64_t e_first = J.out_edge + t0;
+            const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
+            if (head && threadIdx.x == 0) {
+                uint32_t r, c;
+                kron_edge_full32(key, k, u0, u1, u2, (uint32_t)t0, r, c);
+                put_pair(arena, e_first, r, c);
+            }
+            for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
+                uint32_t r0, c0;
+                kron_edge_full32(key, k, u0, u1, u2, (uint32_t)(t0 + t2), r0, c0);
+                if (t2 + 1 < n) {
+                    uint32_t r1, c1;
+                    kron_edge_full32(key, k, u0, u1, u2, (uint32_t)(t0 + t2 + 1), r1, c1);
+                    put_two(arena, e_first + t2, r0, c0, r1, c1);
+                } else {
+                    put_pair(arena, e_first + t2, r0, c0);
+                }
             }
         } else {
             const uint64_t e_first = J.out_edge + t0;

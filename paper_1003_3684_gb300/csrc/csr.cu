@@ -186,15 +186,27 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    // item r of every lane, in lane order: the lowest lane of each group of
-    // equal digits reads and advances the warp's counter, the group gets the
-    // old value by shuffle; the counter is touched by one thread per group
-    // and the syncwarp orders it before the next item's read
+    // item r of every lane, in lane order: the lanes holding equal digits
+    // find each other through a word per digit (each ORs in its lane bit,
+    // then all read the word back and clear it; the word table is the
+    // reorder buffer, unused until the ranks are done, one 1024-word slab
+    // per warp); the lowest lane of each group reads and advances the
+    // warp's counter, the group gets the old value by shuffle; the counter
+    // is touched by one thread per group and the syncwarp orders it before
+    // the next item's read
+    uint32_t* pmask = reinterpret_cast<uint32_t*>(buf) + wid * kMaxBuckets;
+    for (uint32_t d = lane; d < nb; d += 32) pmask[d] = 0;
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const uint32_t t = wbase + r * 32 + lane;
-        const uint32_t d = (t < n) ? digit_of(e[r], field, shift, mask) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const bool valid = t < n;
+        const uint32_t d = valid ? digit_of(e[r], field, shift, mask) : 0xFFFFFFFFu;
+        if (valid) atomicOr(&pmask[d], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = valid ? pmask[d] : 0u;
+        __syncwarp();
+        if (valid) pmask[d] = 0;
         const uint32_t leader = __ffs(peers) - 1;
         uint32_t prev = 0;
         if (lane == leader && d != 0xFFFFFFFFu) {
@@ -321,6 +333,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
         out[tbase[d] + (p - loff[d])] = v;
     }
 }
+
+static_assert(SortShape<uint32_t>::tile * sizeof(uint2) >= kSortWarps * kMaxBuckets * 4 &&
+                  SortShape<uint64_t>::tile * sizeof(ulonglong2) >= kSortWarps * kMaxBuckets * 4,
+              "the reorder buffer holds every warp's digit words");
 
 template <typename Id>
 size_t scatter_smem_bytes()

@@ -149,6 +149,59 @@ __global__ void __launch_bounds__(256) kron2_kernel(const __grid_constant__ Kron
     }
 }
 
+// The same descent with 32-bit edge indices, counters (e, 0, g, 3), ids and
+// loop arithmetic, for launches whose edge indices all lie below 2^32 and
+// whose ids fit 32 bits (k <= 32): the same values, less index arithmetic.
+template <bool kFull>
+__device__ __forceinline__ void kron2_edge32(const KronParams& p, uint32_t e, uint32_t u0,
+                                             uint32_t u1, uint32_t u2, uint32_t& row,
+                                             uint32_t& col)
+{
+    row = 0;
+    col = 0;
+    const uint32_t k = p.k;
+    auto level = [&](uint32_t w) {
+        if constexpr (kFull) descend2_full(w, u0, u1, u2, row, col);
+        else descend2(w, u0, u1, u2, p.n_zero, row, col);
+    };
+    uint32_t l = 0;
+    for (uint32_t g = 0; l + 4 <= k; ++g, l += 4) {
+        const uint4 w = philox(make_uint4(e, 0u, g, 3u), p.key);
+        level(w.x);
+        level(w.y);
+        level(w.z);
+        level(w.w);
+    }
+    if (l < k) {
+        const uint4 w = philox(make_uint4(e, 0u, l >> 2, 3u), p.key);
+        level(w.x);
+        if (l + 1 < k) level(w.y);
+        if (l + 2 < k) level(w.z);
+    }
+}
+
+template <typename Id, bool kFull>
+__global__ void __launch_bounds__(256) kron2_kernel32(const __grid_constant__ KronParams p,
+                                                      Id* __restrict__ out, uint32_t e_begin,
+                                                      uint32_t n_edges)
+{
+    const uint32_t u0 = p.u[0], u1 = p.u[1], u2 = p.u[2];   // padded to three
+    const uint32_t n_pairs = (n_edges >> 1) + (n_edges & 1);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
+        const uint32_t e = 2 * t;
+        uint32_t r0, c0;
+        kron2_edge32<kFull>(p, e_begin + e, u0, u1, u2, r0, c0);
+        if (e + 1 < n_edges) {
+            uint32_t r1, c1;
+            kron2_edge32<kFull>(p, e_begin + e + 1, u0, u1, u2, r1, c1);
+            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        } else {
+            Pair2<Id>::store1(out, e, r0, c0);
+        }
+    }
+}
+
 // ---- stochastic descent, any order n0 <= 16 (binary search in smem) -------
 __device__ __forceinline__ void kron_edge_generic(const KronParams& p, const uint32_t* u,
                                                   uint32_t n_u, uint64_t e, uint64_t& row,
@@ -293,7 +346,7 @@ __global__ void __launch_bounds__(256) random_cells_kernel(const Key key, uint64
 template <typename K>
 int grid_for(K kernel, uint64_t work_items, int threads)
 {
-    static int sms = device_sm_count();
+    const int sms = device_sm_count();   // of the current device
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
         per_sm < 1)
@@ -314,7 +367,17 @@ cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, u
     if (p.n0 == 2) {
         // 32-bit descent state when every id fits (k <= 32)
         const bool full = p.n_zero == 0 && p.n_u == 3;
-        if (id64 && p.k > 32) {
+        if (p.k <= 32 && e_begin + n_edges < ((uint64_t)1 << 32)) {
+            // every edge index below 2^32: 32-bit indices and counters
+            const uint32_t b = (uint32_t)e_begin, n = (uint32_t)n_edges;
+            if (id64) {
+                auto k = full ? kron2_kernel32<uint64_t, true> : kron2_kernel32<uint64_t, false>;
+                k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, b, n);
+            } else {
+                auto k = full ? kron2_kernel32<uint32_t, true> : kron2_kernel32<uint32_t, false>;
+                k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, b, n);
+            }
+        } else if (id64 && p.k > 32) {
             auto k = full ? kron2_kernel<uint64_t, uint64_t, true> : kron2_kernel<uint64_t, uint64_t, false>;
             k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
         } else if (id64) {
