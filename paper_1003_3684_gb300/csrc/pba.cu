@@ -211,26 +211,27 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     uint32_t next = 32, item = lane;
     uint32_t cur = run + item;
     bool active = item < n_items;
-    bool pend = false;
-    uint32_t pend_k = 0, pend_v = 0;
+    bool pend = false, pend_load = false;
+    uint32_t pend_k = 0, pend_v = 0, lv = 0;
     uint32_t own = 0;   // entries equal to p (the most frequent value) counted here
     // every lane draws (an idle lane's draw is discarded), so the trip is
-    // straight-line code apart from the deferred store
+    // straight-line code apart from the deferred store. A copy of the
+    // finished prefix is loaded into lv and first read one trip later, by
+    // that store, so the load's latency overlaps a whole trip.
     auto trip = [&]() {
         const uint4 w = philox_headed(cur, ph, g.key);
-        if (pend) my[pend_k] = (uint16_t)pend_v;   // the value loaded one trip ago
+        if (pend) my[pend_k] = (uint16_t)(pend_load ? lv : pend_v);
         const bool coin = coin_on && w.z < g.coin_thr;
         const uint32_t r = uniform32(w.x, w.y, cur);
         const bool hit = !coin && r < L;
         const bool done = active && (coin || hit);
-        uint32_t v = 0;
         if constexpr (kTable) {
-            if (active && coin) v = F.fresh(w.w, g);   // a table read only for a pick
+            if (active && coin) pend_v = F.fresh(w.w, g);   // a table read only for a pick
         } else {
-            v = F.fresh(w.w, g);
+            pend_v = F.fresh(w.w, g);
         }
-        if (active && hit) v = __ldg(Ap + r);
-        pend_v = done ? v : pend_v;
+        if (active && hit) lv = __ldg(Ap + r);
+        pend_load = hit;
         pend_k = done ? item : pend_k;
         pend = done;
         cur = (active && !done) ? r : cur;
@@ -422,19 +423,24 @@ __device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip
 }
 
 // The same link with sigma(cur) carried in from the previous link (the
-// side-0 value of a link is sigma of the edge the chain moves to, so each
-// link computes one sigma instead of two), n_b a power of two, and the seed
+// side-0 value of a link is sigma of the edge the chain moves to, so a link
+// of a continuing chain computes one sigma instead of two), n_b a power of
+// two, and the seed
 // clique's edges read from a table in the workspace (stab[e] = a | b << 16;
 // every lane reads entry 0 unless it hit a seed slot, so the load is a
 // broadcast from L1)
 // instead of a branch: straight-line code apart from nothing.
-__device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, uint32_t q,
+__device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, bool& fresh, uint32_t q,
                                             const QRecip& c, const PbaGeom& g,
                                             const uint32_t* __restrict__ stab, uint32_t& v)
 {
+    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
+    // a newly claimed entry's sigma, computed after the draw so that the
+    // load of the target's reciprocal has the draw's time to land
+    if (fresh) sig = sigma32(cur, c);
+    fresh = false;
     const uint32_t nb = (uint32_t)g.n_b;
     const uint32_t before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
-    const uint4 w = philox(make_uint4(cur, 0u, q, 2u), g.key);
     const uint32_t e0 = (uint32_t)g.e0;
     const uint32_t X = e0 + before;
     const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
@@ -686,21 +692,21 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
         CurT* item_all = &ws.item[0][0];
         const uint16_t* qs_all = &ws.qs[0][0];
         uint32_t gk = lane, next = 32, q = 0, cur = 0, sig = 0, k = 0;
-        bool active = false;
+        bool active = false, fresh = false;
         QRecip c{0, 0, 0, 0};
         auto take = [&](uint32_t pos) {
             k = pos % (2 * kEmitRun);
             q = qs_all[k];
             cur = (uint32_t)item_all[k];
             c = recip[q];
-            if constexpr (kMode == 2) sig = sigma32(cur, c);
+            fresh = true;
         };
         // one link for every lane; a lane whose chain ended stores its value
         // and takes the next unclaimed entry (below `limit`)
         auto trip = [&](uint32_t limit) {
             uint32_t v;
             bool fin;
-            if constexpr (kMode == 2) fin = t_link_lean(cur, sig, q, c, g, stab, v);
+            if constexpr (kMode == 2) fin = t_link_lean(cur, sig, fresh, q, c, g, stab, v);
             else fin = t_link32(cur, q, c, g, v);
             const bool done = fin && active;
             if (done) item_all[k] = v;
