@@ -323,14 +323,17 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
             const uint32_t cnt_d = (d + 1 < nb ? loff[d + 1] : n) - loff[d];
             if (tile != withhold) st[d] = tag | kInc | (excl + cnt_d);
         }
-        tbase[d] = dstart[d] + excl;
+        // where the tile's run of d starts in the output, less its start in
+        // the sorted tile (never negative: the tile's counts of the lower
+        // digits, loff[d], are at most their totals, which dstart[d] sums)
+        tbase[d] = dstart[d] + excl - loff[d];
     }
     __syncthreads();
-    // write runs: sorted position p goes to tbase[d] + (p - loff[d])
+    // write runs: sorted position p goes to tbase[d] + p (one table read per pair)
     for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
         const P v = buf[p];
         const uint32_t d = digit_of(v, field, shift, mask);
-        out[tbase[d] + (p - loff[d])] = v;
+        out[tbase[d] + p] = v;
     }
 }
 

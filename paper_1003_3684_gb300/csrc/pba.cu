@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
 // x*C/2^64 = x*n_b/R + x*d/2^64 with 0 <= d < 1, and x/2^64 < 1/R because
 // R^2 < 2^64; the fractional part of x*n_b/R is a multiple of 1/R below 1, so
 // adding less than 1/R never carries: floor(x*C/2^64) = sigma(x) exactly.
-struct QRecip {
+struct __align__(16) QRecip {
     uint32_t R, C2, C1, C0;
 };
 
