@@ -64,11 +64,15 @@ __device__ __forceinline__ uint64_t load_streaming(const uint64_t* p)
     return __ldcs(reinterpret_cast<const unsigned long long*>(p));
 }
 
-// One BFS level: each warp takes frontier vertices in turn and its lanes
-// walk the vertex's row. A neighbour whose bit in the visited bitmap (N bits,
-// small enough to stay in L2) is clear is claimed by an atomic OR of that bit;
-// the claimer writes its distance and appends it to the next frontier.
-// scanned += the degrees of the frontier.
+// One BFS level. Each warp takes 32 frontier vertices at a time and walks
+// their rows as one concatenated range, 32 adjacency entries per step: lane
+// k of a step finds the vertex owning entry base + k by a binary search over
+// the 32 rows' starts (a warp scan of their degrees, kept in shared memory),
+// so short rows (most rows of a power-law graph) do not leave lanes idle and
+// a hub row is walked by the whole warp. A neighbour whose bit in the visited
+// bitmap (N bits, small enough to stay in L2) is clear is claimed by an atomic
+// OR of that bit; the claimer writes its distance and appends it to the next
+// frontier. scanned += the degrees of the frontier.
 template <typename Id>
 __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_t* __restrict__ row_ptr,
                                                         const Id* __restrict__ col,
@@ -84,21 +88,48 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
     // so the shared counter of the next frontier takes one atomic per 32
     // claims (the frontier's order is not part of the result)
     __shared__ uint32_t wbuf[kBfsWarps][64];
+    __shared__ uint64_t wstart[kBfsWarps][32];   // the 32 rows' starts in the concatenation
+    __shared__ uint64_t wrow[kBfsWarps][32];     // and in col
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     uint32_t* buf = wbuf[wid];
+    uint64_t* st = wstart[wid];
+    uint64_t* rw = wrow[wid];
     uint32_t held = 0;   // warp-uniform, < 32 between chunks
     unsigned long long seen = 0;
-    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < fsize; i += warps) {
-        const uint32_t v = frontier[i];
-        const uint64_t a = row_ptr[v], b = row_ptr[v + 1];
-        seen += b - a;
-        for (uint64_t base = a; base < b; base += 32) {
-            const uint64_t e = base + lane;
+    const uint64_t first = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    for (uint64_t c = first; c < fsize; c += warps * 32) {
+        uint64_t a = 0, d = 0;
+        if (c + lane < fsize) {
+            const uint32_t v = frontier[c + lane];
+            a = row_ptr[v];
+            d = row_ptr[v + 1] - a;
+        }
+        // inclusive scan of the degrees over the warp
+        uint64_t incl = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint64_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        st[lane] = incl - d;
+        rw[lane] = a;
+        __syncwarp();
+        seen += total;
+        for (uint64_t base = 0; base < total; base += 32) {
+            const uint64_t k = base + lane;
             bool claim = false;
             uint32_t u = 0;
-            if (e < b) {
+            if (k < total) {
+                // the last row whose start is at or below k owns entry k (an
+                // empty row starts where the next one does)
+                uint32_t o = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (st[o + step] <= k) o += step;
+                const uint64_t e = rw[o] + (k - st[o]);
                 const uint64_t u64 = load_streaming(col + e);
                 if (u64 < N) {
                     u = (uint32_t)u64;
@@ -127,6 +158,7 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
                 held = rest;
             }
         }
+        __syncwarp();   // the next chunk rewrites the row tables
     }
     __syncwarp();
     if (held) {
@@ -226,7 +258,7 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
     TraceScope trace("bfs", s);
     while (fsize > 0) {
         if (cudaMemsetAsync(nsize, 0, 4, s) != cudaSuccess) return PG_ECUDA;
-        const int grid = grid_cap((uint64_t)fsize * 32);
+        const int grid = grid_cap(fsize);
         if (w == PG_ID64)
             bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(d_row_ptr, (const uint64_t*)d_col,
                                                             fr[cur], fsize, fr[cur ^ 1], nsize,
