@@ -369,6 +369,41 @@ pg_status pg_csr_check(const void* d_ws, uint64_t n_edges, uint64_t n_vertices, 
  * Process-wide, read at each call; cannot fail. */
 void pg_csr_test_wait_hook(uint32_t spin_limit, uint32_t withhold_tile);
 
+/* ------------------------------------------------------------------------
+ * Checked build (a debugging aid, not part of the method). The same sources
+ * compiled with -DPGEN_CHECKED give libpgen_checked.so, with the same entry
+ * points. There every kernel access whose index comes from data -- a random
+ * draw, a block id read from the phase-1 lists, a vertex id, a position from
+ * a scan -- and every store of a result element is compared with the bound
+ * of its buffer first. A failed comparison skips the access (a skipped load
+ * reads as 0) and is counted in a device record of the kernel's source file;
+ * nothing traps, so the CUDA context stays usable.
+ * ---------------------------------------------------------------------- */
+
+/* 1 in the checked build, 0 in the default one. */
+int pg_checked_build(void);
+
+/* Waits for `stream`, then reports the failed bounds comparisons since the
+ * last reset on the current device: *count their number (saturating at
+ * 2^32 - 1); *unit the source file of the first one found, in the order
+ * 1 Kronecker, 2 PBA, 3 CSR, 4 batch, 5 graph checks (0 when count is 0);
+ * *line its source line, *index and *bound the compared values. Files are
+ * read in that order, so with failures in several files the lowest number
+ * is reported. reset != 0 zeroes every record after reading it. Any output
+ * pointer may be NULL. The default build has no checks: it reports count 0
+ * and returns PG_OK. PG_ECUDA when a copy or the synchronisation fails. */
+pg_status pg_check_read(int reset, uint32_t* count, uint32_t* unit, uint32_t* line,
+                        uint64_t* index, uint64_t* bound, void* stream);
+
+/* Test hook of the checked build: from the next launch on, every bound that
+ * a store of a result element (an edge, a col entry) is compared with is
+ * taken as bound >> shift (0 restores the real bounds). The shortened bound
+ * lies inside the real buffer, so the stores it skips were in bounds: a test
+ * sees real kernels report and skip stores without any access outside a
+ * buffer. Stream-ordered on `stream`, and waits for it. PG_EINVAL for
+ * shift > 63 or in the default build. */
+pg_status pg_check_test_out_shift(uint32_t shift, void* stream);
+
 /* Random graph G(N, M) with replacement, for the exclusive-or randomisation
  * of PK graphs (Sec. 3, PK method): edge e (e < n_edges) is the cell
  * (row, col) = (floor((w1:w0) * N / 2^64), floor((w3:w2) * N / 2^64)) of the

@@ -21,6 +21,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+from typing import NamedTuple
 
 import numpy as np
 
@@ -37,6 +38,8 @@ __all__ = [
     "pg_kron_edge_count", "gen_kronecker",
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
     "pg_csr_wait_error_offset", "csr_wait_error", "pg_csr_check", "pg_csr_test_wait_hook",
+    "pg_checked_build", "pg_check_read", "pg_check_test_out_shift", "CheckReport",
+    "empty_device", "set_fail_alloc_at",
 ]
 
 PG_OK, PG_EINVAL, PG_ENOSPC, PG_ECUDA, PG_ETIMEOUT, PG_ENOMEM = range(6)
@@ -44,7 +47,13 @@ PG_ID32, PG_ID64 = 0, 1
 PG_KRON_STOCHASTIC, PG_KRON_DETERMINISTIC = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libpgen.so")
+# PGEN_LIBRARY=checked loads the bounds-checked build (same entry points);
+# anything else, or unset, the default build
+_LIB_NAMES = {"default": "libpgen.so", "checked": "libpgen_checked.so"}
+_LIB_VARIANT = os.environ.get("PGEN_LIBRARY", "default")
+if _LIB_VARIANT not in _LIB_NAMES:
+    raise RuntimeError(f"PGEN_LIBRARY={_LIB_VARIANT!r}: expected one of {sorted(_LIB_NAMES)}")
+_LIB_PATH = os.path.join(_HERE, _LIB_NAMES[_LIB_VARIANT])
 _lock = threading.Lock()
 _lib = None
 
@@ -119,9 +128,40 @@ def _ptr(t):
     return vp(t.data_ptr()) if t is not None and t.numel() > 0 else vp(None)
 
 
-def _empty(nbytes_or_shape, dtype, device):
+# Allocation-failure injection (a testing aid, not part of the method). The
+# library itself allocates no device memory: every buffer it writes is made
+# here, by empty_device. With PGEN_FAIL_ALLOC_AT=k in the environment, or
+# after set_fail_alloc_at(k), the k-th of those allocations from then on
+# (k >= 1) raises torch.cuda.OutOfMemoryError instead, as an exhausted device
+# would, once; 0 turns the injection off.
+_alloc_lock = threading.Lock()
+try:
+    _fail_at = [int(os.environ.get("PGEN_FAIL_ALLOC_AT", "0") or 0), 0]   # [k, counted]
+except ValueError:
+    raise RuntimeError("PGEN_FAIL_ALLOC_AT must be an integer") from None
+
+
+def set_fail_alloc_at(k: int) -> None:
+    """Make the k-th device allocation of the binding from now on fail (0: never)."""
+    with _alloc_lock:
+        _fail_at[0], _fail_at[1] = int(k), 0
+
+
+def empty_device(shape, dtype, device):
+    """An uninitialised buffer for the library to write: every device buffer
+    the binding (and the serving loop) allocates comes from here."""
     import torch
-    return torch.empty(nbytes_or_shape, dtype=dtype, device=device)
+    with _alloc_lock:
+        if _fail_at[0] > 0:
+            _fail_at[1] += 1
+            if _fail_at[1] == _fail_at[0]:
+                _fail_at[0] = 0
+                raise torch.cuda.OutOfMemoryError(
+                    f"injected allocation failure (shape {shape}, {dtype})")
+    return torch.empty(shape, dtype=dtype, device=device)
+
+
+_empty = empty_device
 
 
 # --------------------------------------------------------------------------
@@ -565,6 +605,53 @@ def pg_csr_test_wait_hook(spin_limit: int = 0, withhold_tile: int = 0xFFFFFFFF) 
     L.pg_csr_test_wait_hook.argtypes = [u32, u32]
     L.pg_csr_test_wait_hook.restype = None
     L.pg_csr_test_wait_hook(spin_limit, withhold_tile)
+
+
+class CheckReport(NamedTuple):
+    """What the checked build's bounds comparisons found (pg_check_read)."""
+    count: int    # failed comparisons
+    unit: int     # source file of the first one: 1 Kronecker, 2 PBA, 3 CSR, 4 batch, 5 checks
+    line: int     # its source line
+    index: int    # the compared index and bound
+    bound: int
+
+
+def _check_lib():
+    L = lib()
+    if not getattr(L, "_bounds_ready", False):
+        L.pg_checked_build.argtypes = []
+        L.pg_checked_build.restype = i32
+        L.pg_check_read.argtypes = [i32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32),
+                                    C.POINTER(u64), C.POINTER(u64), vp]
+        L.pg_check_read.restype = i32
+        L.pg_check_test_out_shift.argtypes = [u32, vp]
+        L.pg_check_test_out_shift.restype = i32
+        L._bounds_ready = True
+    return L
+
+
+def pg_checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(_check_lib().pg_checked_build())
+
+
+def pg_check_read(reset: bool = True, stream=None) -> CheckReport:
+    """Wait for `stream` and return the failed bounds comparisons since the
+    last reset (always count 0 in the default build); reset zeroes them."""
+    L = _check_lib()
+    c, u, ln = u32(), u32(), u32()
+    ix, bd = u64(), u64()
+    _check("pg_check_read", L.pg_check_read(1 if reset else 0, C.byref(c), C.byref(u),
+                                            C.byref(ln), C.byref(ix), C.byref(bd),
+                                            _stream(stream)))
+    return CheckReport(c.value, u.value, ln.value, ix.value, bd.value)
+
+
+def pg_check_test_out_shift(shift: int, stream=None) -> None:
+    """Test hook of the checked build: result stores are compared with
+    bound >> shift (0 restores the real bounds)."""
+    _check("pg_check_test_out_shift",
+           _check_lib().pg_check_test_out_shift(shift, _stream(stream)))
 
 
 CSR_SYMMETRIZE, CSR_DEDUP, CSR_NO_LOOPS, CSR_ODD = 1, 2, 4, 8

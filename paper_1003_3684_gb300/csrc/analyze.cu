@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
     const uint64_t first = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     for (uint64_t c = first; c < fsize; c += warps * 32) {
         uint64_t a = 0, d = 0;
-        if (c + lane < fsize) {
+        if (c + lane < fsize && PG_CHECK(frontier[c + lane], N)) {
             const uint32_t v = frontier[c + lane];
             a = row_ptr[v];
             d = row_ptr[v + 1] - a;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
                 uint32_t at = 0;
                 if (lane == 0) at = atomicAdd(nsize, 32u);
                 at = __shfl_sync(0xFFFFFFFFu, at, 0);
-                next[at + lane] = buf[lane];
+                if (PG_CHECK(at + lane, N)) next[at + lane] = buf[lane];
                 const uint32_t rest = held - 32;
                 const uint32_t x = lane < rest ? buf[32 + lane] : 0;
                 __syncwarp();
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
         uint32_t at = 0;
         if (lane == 0) at = atomicAdd(nsize, held);
         at = __shfl_sync(0xFFFFFFFFu, at, 0);
-        if (lane < held) next[at + lane] = buf[lane];
+        if (lane < held && PG_CHECK(at + lane, N)) next[at + lane] = buf[lane];
     }
     if (lane == 0 && seen) atomicAdd(scanned, seen);
 }
@@ -187,6 +187,9 @@ int grid_cap(uint64_t items)
 }
 
 }  // namespace
+
+PG_CHECK_UNIT(analyze)
+
 }  // namespace pgen
 
 using namespace pgen;

@@ -591,6 +591,63 @@ void pg_csr_test_wait_hook(uint32_t spin_limit, uint32_t withhold_tile)
     set_csr_wait_hook(spin_limit, withhold_tile);
 }
 
+int pg_checked_build(void) { return kChecked ? 1 : 0; }
+
+#ifdef PGEN_CHECKED
+namespace {
+using CheckAccess = cudaError_t (*)(CheckRecord*, int, uint32_t, cudaStream_t);
+// indexed by CheckUnit
+constexpr CheckAccess kCheckUnits[] = {nullptr, check_access_kron, check_access_pba,
+                                       check_access_csr, check_access_batch,
+                                       check_access_analyze};
+constexpr uint32_t kNumCheckUnits = sizeof(kCheckUnits) / sizeof(kCheckUnits[0]);
+}  // namespace
+#endif
+
+pg_status pg_check_read(int reset, uint32_t* count, uint32_t* unit, uint32_t* line,
+                        uint64_t* index, uint64_t* bound, void* stream)
+{
+    uint64_t total = 0;
+    uint32_t first_unit = 0;
+    CheckRecord first{0, 0, 0, 0};
+#ifdef PGEN_CHECKED
+    for (uint32_t u = 1; u < kNumCheckUnits; ++u) {
+        CheckRecord r{0, 0, 0, 0};
+        if (kCheckUnits[u](&r, reset, 0xFFFFFFFFu, (cudaStream_t)stream) != cudaSuccess)
+            return PG_ECUDA;
+        if (r.count && !first_unit) {
+            first_unit = u;
+            first = r;
+        }
+        total += r.count;
+    }
+#else
+    (void)reset;
+    (void)stream;
+#endif
+    if (count) *count = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
+    if (unit) *unit = first_unit;
+    if (line) *line = first.line;
+    if (index) *index = first.index;
+    if (bound) *bound = first.bound;
+    return PG_OK;
+}
+
+pg_status pg_check_test_out_shift(uint32_t shift, void* stream)
+{
+#ifdef PGEN_CHECKED
+    if (shift > 63) return PG_EINVAL;
+    for (uint32_t u = 1; u < kNumCheckUnits; ++u)
+        if (kCheckUnits[u](nullptr, 0, shift, (cudaStream_t)stream) != cudaSuccess)
+            return PG_ECUDA;
+    return PG_OK;
+#else
+    (void)shift;
+    (void)stream;
+    return PG_EINVAL;
+#endif
+}
+
 size_t pg_csr_workspace_size(uint64_t n_edges, uint64_t n_vertices)
 {
     return csr_workspace_bytes(n_edges, n_vertices);

@@ -58,17 +58,20 @@ size_t plan_bytes(uint32_t n_jobs, uint32_t n_pool)
            a16((size_t)(n_jobs + 1) * 4) + a16((size_t)n_pool * 4);
 }
 
+// Edge e (and e + 1) of an arena of `cap` edges.
 template <typename Id>
-__device__ __forceinline__ void put_pair(Id* out, uint64_t e, uint64_t s, uint64_t d)
+__device__ __forceinline__ void put_pair(Id* out, uint64_t cap, uint64_t e, uint64_t s, uint64_t d)
 {
+    if (!PG_CHECK_OUT(e, cap)) return;
     out[2 * e] = (Id)s;
     out[2 * e + 1] = (Id)d;
 }
 
 template <typename Id>
-__device__ __forceinline__ void put_two(Id* out, uint64_t e, uint64_t s0, uint64_t d0, uint64_t s1,
-                                        uint64_t d1)
+__device__ __forceinline__ void put_two(Id* out, uint64_t cap, uint64_t e, uint64_t s0,
+                                        uint64_t d0, uint64_t s1, uint64_t d1)
 {
+    if (!PG_CHECK_OUT(e + 1, cap)) return;
     if constexpr (sizeof(Id) == 4) {
         *reinterpret_cast<uint4*>(out + 2 * e) =
             make_uint4((uint32_t)s0, (uint32_t)d0, (uint32_t)s1, (uint32_t)d1);
@@ -155,8 +158,8 @@ __device__ __forceinline__ void kron_edge_full32(const Key& key, uint32_t k, uin
 }
 
 __device__ __forceinline__ void kron_edge(const BatchJob& J, const Key& key,
-                                          const uint32_t* pool, uint64_t e, uint64_t& row,
-                                          uint64_t& col)
+                                          const uint32_t* pool, uint32_t n_pool, uint64_t e,
+                                          uint64_t& row, uint64_t& col)
 {
     row = 0;
     col = 0;
@@ -182,6 +185,7 @@ __device__ __forceinline__ void kron_edge(const BatchJob& J, const Key& key,
         }
         return;
     }
+    if (J.n_u > 0 && !PG_CHECK((uint64_t)J.u_off + J.n_u - 1, n_pool)) return;
     const uint32_t* u = pool + J.u_off;
     uint4 w = make_uint4(0, 0, 0, 0);
     for (uint32_t l = 0; l < J.k; ++l) {
@@ -203,7 +207,8 @@ __device__ __forceinline__ void kron_edge(const BatchJob& J, const Key& key,
 template <typename Id>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned char* __restrict__ plan,
                                                               Id* __restrict__ arena,
-                                                              unsigned long long* __restrict__ counter)
+                                                              unsigned long long* __restrict__ counter,
+                                                              uint64_t cap, uint32_t n_jobs_smem)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const PlanHeader& H = *reinterpret_cast<const PlanHeader*>(plan);
@@ -212,6 +217,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
     const uint32_t* pool = reinterpret_cast<const uint32_t*>(plan + H.off_pool);
     const uint32_t n_jobs = H.n_jobs;
     const uint64_t n_items = H.n_items;
+    // the first-item table in smem was sized for n_jobs_smem jobs (uniform exit)
+    if (!PG_CHECK(n_jobs, n_jobs_smem + 1)) return;
 
     Id* sDst = reinterpret_cast<Id*>(smem);                                    // kMaxTile ids
     uint32_t* first = reinterpret_cast<uint32_t*>(smem + kMaxTile * sizeof(Id));   // n_jobs + 1
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
         if (J.kind == PG_JOB_BA) {
             if (t0 == 0)
                 for (uint64_t e = threadIdx.x; e < J.e0; e += blockDim.x)
-                    put_pair(arena, J.out_edge + e, seed_endpoint(e, 0, J.n0),
+                    put_pair(arena, cap, J.out_edge + e, seed_endpoint(e, 0, J.n0),
                              seed_endpoint(e, 1, J.n0));
             // warps take runs of the tile; lanes pool their chains
             const uint32_t per = (n + kBatchWarps - 1) / kBatchWarps;
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
                 if (active) {
                     uint32_t v;
                     done = ba_link(cur, J, key, ph, v);
-                    if (done) sDst[r0 + item] = (Id)v;
+                    if (done && PG_CHECK(r0 + item, kMaxTile)) sDst[r0 + item] = (Id)v;
                 }
                 const uint32_t dm = __ballot_sync(0xFFFFFFFFu, done);
                 if (done) {
@@ -279,14 +286,14 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
             const uint64_t e_first = J.out_edge + J.e0 + t0;
             const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
             if (head && threadIdx.x == 0)
-                put_pair(arena, e_first, J.n0 + fdiv32((uint32_t)t0, J.div_m), (uint64_t)sDst[0]);
+                put_pair(arena, cap, e_first, J.n0 + fdiv32((uint32_t)t0, J.div_m), (uint64_t)sDst[0]);
             for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
                 const uint64_t s0 = J.n0 + fdiv32((uint32_t)(t0 + t2), J.div_m);
                 if (t2 + 1 < n)
-                    put_two(arena, e_first + t2, s0, (uint64_t)sDst[t2],
+                    put_two(arena, cap, e_first + t2, s0, (uint64_t)sDst[t2],
                             J.n0 + fdiv32((uint32_t)(t0 + t2 + 1), J.div_m), (uint64_t)sDst[t2 + 1]);
                 else
-                    put_pair(arena, e_first + t2, s0, (uint64_t)sDst[t2]);
+                    put_pair(arena, cap, e_first + t2, s0, (uint64_t)sDst[t2]);
             }
         } else if (J.n0 == 2 && J.n_zero == 0 && J.n_u == 3 && J.k <= 32 &&
                    J.n_units <= 0xFFFFFFFFull) {
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
             if (head && threadIdx.x == 0) {
                 uint32_t r, c;
                 kron_edge_full32(key, k, u0, u1, u2, (uint32_t)t0, r, c);
-                put_pair(arena, e_first, r, c);
+                put_pair(arena, cap, e_first, r, c);
             }
             for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
                 uint32_t r0, c0;
@@ -305,9 +312,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
                 if (t2 + 1 < n) {
                     uint32_t r1, c1;
                     kron_edge_full32(key, k, u0, u1, u2, (uint32_t)(t0 + t2 + 1), r1, c1);
-                    put_two(arena, e_first + t2, r0, c0, r1, c1);
+                    put_two(arena, cap, e_first + t2, r0, c0, r1, c1);
                 } else {
-                    put_pair(arena, e_first + t2, r0, c0);
+                    put_pair(arena, cap, e_first + t2, r0, c0);
                 }
             }
         } else {
@@ -315,23 +322,29 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
             const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
             if (head && threadIdx.x == 0) {
                 uint64_t r, c;
-                kron_edge(J, key, pool, t0, r, c);
-                put_pair(arena, e_first, r, c);
+                kron_edge(J, key, pool, H.n_pool, t0, r, c);
+                put_pair(arena, cap, e_first, r, c);
             }
             for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
                 uint64_t r0, c0;
-                kron_edge(J, key, pool, t0 + t2, r0, c0);
+                kron_edge(J, key, pool, H.n_pool, t0 + t2, r0, c0);
                 if (t2 + 1 < n) {
                     uint64_t r1, c1;
-                    kron_edge(J, key, pool, t0 + t2 + 1, r1, c1);
-                    put_two(arena, e_first + t2, r0, c0, r1, c1);
+                    kron_edge(J, key, pool, H.n_pool, t0 + t2 + 1, r1, c1);
+                    put_two(arena, cap, e_first + t2, r0, c0, r1, c1);
                 } else {
-                    put_pair(arena, e_first + t2, r0, c0);
+                    put_pair(arena, cap, e_first + t2, r0, c0);
                 }
             }
         }
     }
 }
+
+}  // namespace
+
+PG_CHECK_UNIT(batch)
+
+namespace {
 
 bool kron_thresholds_host(const double* P, uint32_t n0, uint64_t* T)
 {
@@ -488,10 +501,12 @@ pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_a
     TraceScope trace("batch_persistent", s);
     if (w == PG_ID64)
         batch_kernel<uint64_t><<<grid, kBatchThreads, smem, s>>>(
-            (const unsigned char*)d_plan, (uint64_t*)d_arena, (unsigned long long*)d_ws);
+            (const unsigned char*)d_plan, (uint64_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
+            n_jobs);
     else
         batch_kernel<uint32_t><<<grid, kBatchThreads, smem, s>>>(
-            (const unsigned char*)d_plan, (uint32_t*)d_arena, (unsigned long long*)d_ws);
+            (const unsigned char*)d_plan, (uint32_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
+            n_jobs);
     return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
 }
 

@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
         if (t < n) {
             const uint32_t d = digit_of(e[r], field, shift, mask);
             const uint32_t rank = (rk[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
-            buf[loff[d] + wcnt[wid][d] + rank] = e[r];
+            const uint32_t at = loff[d] + wcnt[wid][d] + rank;
+            if (PG_CHECK(at, n)) buf[at] = e[r];
         }
     }
     // look back through up to kLookWindow earlier tiles per round trip
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
         const P v = buf[p];
         const uint32_t d = digit_of(v, field, shift, mask);
-        out[tbase[d] + p] = v;
+        if (PG_CHECK(tbase[d] + p, M)) out[tbase[d] + p] = v;
     }
 }
 
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(256) csr_grouped_kernel(const typename PairOf<
             const uint64_t dj = s[j].y;
             rank += (dj < d) || (dj == d && j < i);
         }
-        col[a + rank] = (Id)d;
+        if (PG_CHECK_OUT(a + rank, M)) col[a + rank] = (Id)d;
         mark_row_end(s, M, N, i, row_ptr);
     }
 }
@@ -605,7 +606,7 @@ __global__ void __launch_bounds__(256) csr_finish_kernel(const typename PairOf<I
         for (int u = 0; u < kU; ++u) {
             const uint64_t i = i0 + u * stride;
             if (i < M) {
-                col[i] = (Id)e[u].y;
+                if (PG_CHECK_OUT(i, M)) col[i] = (Id)e[u].y;
                 const uint64_t v = e[u].x;
                 if (v < N && nx[u] != v) row_ptr[v + 1] = i + 1;
             }
@@ -709,10 +710,17 @@ __global__ void __launch_bounds__(256) csr_keep_apply_kernel(const typename Pair
         const uint64_t i = base + t;
         if (i >= M) break;
         const uint64_t v = s[i].x;
-        if (keep & (1u << t)) col[e++] = (Id)s[i].y;
+        if ((keep & (1u << t)) && PG_CHECK_OUT(e, M)) col[e] = (Id)s[i].y;
+        if (keep & (1u << t)) ++e;
         if (v < N && (i + 1 == M || (uint64_t)s[i + 1].x != v)) row_ptr[v + 1] = e;
     }
 }
+
+}  // namespace
+
+PG_CHECK_UNIT(csr)
+
+namespace {
 
 int bit_length(uint64_t x)
 {

@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(256) kron2_kernel(const __grid_constant__ Kron
         if (e + 1 < n_edges) {
             T r1, c1;
             edge(e_begin + e + 1, r1, c1);
-            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+            if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
-            Pair2<Id>::store1(out, e, r0, c0);
+            if (PG_CHECK_OUT(e, n_edges)) Pair2<Id>::store1(out, e, r0, c0);
         }
     }
 }
@@ -195,9 +195,9 @@ __global__ void __launch_bounds__(256) kron2_kernel32(const __grid_constant__ Kr
         if (e + 1 < n_edges) {
             uint32_t r1, c1;
             kron2_edge32<kFull>(p, e_begin + e + 1, u0, u1, u2, r1, c1);
-            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+            if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
-            Pair2<Id>::store1(out, e, r0, c0);
+            if (PG_CHECK_OUT(e, n_edges)) Pair2<Id>::store1(out, e, r0, c0);
         }
     }
 }
@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(256) kron_generic_kernel(const __grid_constant
         if (e + 1 < n_edges) {
             uint64_t r1, c1;
             kron_edge_generic(p, u, n_u, e_begin + e + 1, r1, c1);
-            Pair2<Id>::store(out, e, r0, c0, r1, c1);
+            if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
-            Pair2<Id>::store1(out, e, r0, c0);
+            if (PG_CHECK_OUT(e, n_edges)) Pair2<Id>::store1(out, e, r0, c0);
         }
     }
 }
@@ -262,7 +262,7 @@ __device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint
         const uint64_t q = fdiv(e, p.div_e0);
         const uint32_t d = (uint32_t)(e - q * p.e0);
         e = q;
-        const uint32_t v = ab[d];
+        const uint32_t v = PG_CHECK(d, p.e0) ? ab[d] : 0u;
         row += (v & 0xFFu) * mul;
         col += (v >> 8) * mul;
         mul *= p.n0;
@@ -313,10 +313,11 @@ __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ K
             kron_det_edge(p, ab, e_begin + e, r0, c0);
             if (two) kron_det_edge(p, ab, e_begin + e + 1, r1, c1);
         }
-        if (two)
-            Pair2<Id>::store(out, e, r0, c0, r1, c1);
-        else
-            Pair2<Id>::store1(out, e, r0, c0);
+        if (two) {
+            if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
+        } else {
+            if (PG_CHECK_OUT(e, n_edges)) Pair2<Id>::store1(out, e, r0, c0);
+        }
     }
 }
 
@@ -335,10 +336,12 @@ __global__ void __launch_bounds__(256) random_cells_kernel(const Key key, uint64
         const uint4 a = draw(e_begin + e, 0, 4, key);
         if (e + 1 < n_edges) {
             const uint4 b = draw(e_begin + e + 1, 0, 4, key);
-            Pair2<Id>::store(out, e, uniform64(a.x, a.y, N), uniform64(a.z, a.w, N),
-                             uniform64(b.x, b.y, N), uniform64(b.z, b.w, N));
+            if (PG_CHECK_OUT(e + 1, n_edges))
+                Pair2<Id>::store(out, e, uniform64(a.x, a.y, N), uniform64(a.z, a.w, N),
+                                 uniform64(b.x, b.y, N), uniform64(b.z, b.w, N));
         } else {
-            Pair2<Id>::store1(out, e, uniform64(a.x, a.y, N), uniform64(a.z, a.w, N));
+            if (PG_CHECK_OUT(e, n_edges))
+                Pair2<Id>::store1(out, e, uniform64(a.x, a.y, N), uniform64(a.z, a.w, N));
         }
     }
 }
@@ -357,6 +360,8 @@ int grid_for(K kernel, uint64_t work_items, int threads)
 }
 
 }  // namespace
+
+PG_CHECK_UNIT(kron)
 
 cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, uint64_t e_begin,
                                    uint64_t n_edges, cudaStream_t s)

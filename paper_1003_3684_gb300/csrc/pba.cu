@@ -104,13 +104,17 @@ struct Faction {
     }
     __device__ __forceinline__ uint32_t member(uint32_t t) const
     {
-        if constexpr (kTable) return rec[kFacHeader + t];
+        if constexpr (kTable) return PG_CHECK(t, kFacSlots) ? rec[kFacHeader + t] : 0u;
         else return phi + t;
     }
     __device__ __forceinline__ uint32_t fresh(uint32_t w3, const PbaGeom& g) const
     {
-        if constexpr (kTable) return rec[kFacHeader + kFacSlots + __umulhi(w3, n_out)];
-        else return fresh_block(w3, g.B, g.W, phi);
+        if constexpr (kTable) {
+            const uint32_t x = __umulhi(w3, n_out);
+            return PG_CHECK(x, kFacSlots) ? rec[kFacHeader + kFacSlots + x] : 0u;
+        } else {
+            return fresh_block(w3, g.B, g.W, phi);
+        }
     }
 };
 
@@ -118,6 +122,7 @@ struct Faction {
 __device__ __forceinline__ void flush_counts(const uint32_t* hist, uint32_t* cnt,
                                              const PbaGeom& g, uint32_t p, uint32_t sgm)
 {
+    if (!PG_CHECK(sgm, g.S)) return;
     uint32_t* row = cnt + ((uint64_t)p * g.S + sgm) * g.B;
     for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x)
         if (hist[t]) atomicAdd(&row[t], hist[t]);
@@ -171,7 +176,8 @@ __global__ void __launch_bounds__(kPrefixThreads) pba_prefix_kernel(
         const uint32_t b = (uint32_t)((a + g.seg_len < P) ? a + g.seg_len : P);
         for (uint32_t t = threadIdx.x; t < g.B; t += blockDim.x) hist[t] = 0;
         __syncthreads();
-        for (uint32_t t = a + threadIdx.x; t < b; t += blockDim.x) atomicAdd(&hist[sA[t]], 1u);
+        for (uint32_t t = a + threadIdx.x; t < b; t += blockDim.x)
+            if (PG_CHECK(sA[t], g.B)) atomicAdd(&hist[sA[t]], 1u);
         __syncthreads();
         flush_counts(hist, cnt, g, p, sgm);
         __syncthreads();
@@ -251,15 +257,16 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
     for (uint32_t t = lane; t < n_items; t += 32) {
         const uint32_t v = my[t];
         if (v == p) ++own;
-        else atomicAdd(&hist[v], 1u);
+        else if (PG_CHECK(v, g.B)) atomicAdd(&hist[v], 1u);
     }
     // the run back to A: 16-byte stores when the run is whole (run is a
     // multiple of 8 entries and rows are 16-byte aligned)
-    if (n_items == kPassRun) {
+    const bool in_row = n_items == 0 || PG_CHECK(run + n_items - 1, g.N_e);
+    if (in_row && n_items == kPassRun) {
         const uint4* src = reinterpret_cast<const uint4*>(my);
         uint4* dst = reinterpret_cast<uint4*>(Ap + run);
         for (uint32_t t = lane; t < kPassRun / 8; t += 32) dst[t] = src[t];
-    } else {
+    } else if (in_row) {
         for (uint32_t t = lane; t < n_items; t += 32) Ap[run + t] = my[t];
     }
     if (own) atomicAdd(&hist[p], own);
@@ -449,7 +456,8 @@ __device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, bool& 
     const uint32_t e2 = e - e0;
     const uint32_t sig2 = sigma32(e2, c);
     const bool seed = e < e0;
-    const uint32_t ab = __ldg(stab + (seed ? e : 0));
+    const uint32_t ti = seed ? e : 0u;
+    const uint32_t ab = PG_CHECK(ti, kSeedTab) ? __ldg(stab + ti) : 0u;
     const uint32_t vs = side ? (ab >> 16) : (ab & 0xFFFFu);
     v = seed ? vs : g.n0 + sig2;
     const bool fin = seed || side == 0;
@@ -522,18 +530,20 @@ __device__ __forceinline__ void store_two(Id* out, uint64_t e, uint64_t s0, uint
     }
 }
 
-// Writes n consecutive edges starting at global edge index e_first; edge t
-// comes from edge_at(t, src, dst). Pairs of edges whose first index is even
-// go out as one 16-byte (uint32 ids) or two 16-byte (uint64 ids) stores; an
-// odd first index is written alone first so that the rest stay aligned.
+// Writes n consecutive edges starting at global edge index e_first of an
+// output of `cap` edges; edge t comes from edge_at(t, src, dst). Pairs of
+// edges whose first index is even go out as one 16-byte (uint32 ids) or two
+// 16-byte (uint64 ids) stores; an odd first index is written alone first so
+// that the rest stay aligned.
 template <typename Id, typename F>
-__device__ __forceinline__ void emit_tile(Id* out, uint64_t e_first, uint32_t n, F&& edge_at)
+__device__ __forceinline__ void emit_tile(Id* out, uint64_t cap, uint64_t e_first, uint32_t n,
+                                          F&& edge_at)
 {
     const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
     if (head && threadIdx.x == 0) {
         uint64_t s0, d0;
         edge_at(0, s0, d0);
-        store_pair(out, e_first, s0, d0);
+        if (PG_CHECK_OUT(e_first, cap)) store_pair(out, e_first, s0, d0);
     }
     for (uint32_t t2 = head + 2 * threadIdx.x; t2 < n; t2 += 2 * blockDim.x) {
         uint64_t s0, d0;
@@ -541,33 +551,35 @@ __device__ __forceinline__ void emit_tile(Id* out, uint64_t e_first, uint32_t n,
         if (t2 + 1 < n) {
             uint64_t s1, d1;
             edge_at(t2 + 1, s1, d1);
-            store_two(out, e_first + t2, s0, d0, s1, d1);
+            if (PG_CHECK_OUT(e_first + t2 + 1, cap)) store_two(out, e_first + t2, s0, d0, s1, d1);
         } else {
-            store_pair(out, e_first + t2, s0, d0);
+            if (PG_CHECK_OUT(e_first + t2, cap)) store_pair(out, e_first + t2, s0, d0);
         }
     }
 }
 
 // Seed clique of one block (e0 edges, lexicographic) at out[e_first...].
 template <typename Id>
-__device__ void write_seed_edges(Id* out, uint64_t e_first, uint64_t base, uint32_t n0)
+__device__ void write_seed_edges(Id* out, uint64_t cap, uint64_t e_first, uint64_t base,
+                                 uint32_t n0)
 {
     const uint64_t e0 = (uint64_t)n0 * (n0 - 1) / 2;
     for (uint64_t e = threadIdx.x; e < e0; e += blockDim.x)
-        store_pair(out, e_first + e, base + seed_endpoint(e, 0, n0),
-                   base + seed_endpoint(e, 1, n0));
+        if (PG_CHECK_OUT(e_first + e, cap))
+            store_pair(out, e_first + e, base + seed_endpoint(e, 0, n0),
+                       base + seed_endpoint(e, 1, n0));
 }
 
 // Warp-scoped version of emit_tile: lanes of one warp write n edges.
 template <typename Id, typename F>
-__device__ __forceinline__ void emit_run(Id* out, uint64_t e_first, uint32_t n, uint32_t lane,
-                                         F&& edge_at)
+__device__ __forceinline__ void emit_run(Id* out, uint64_t cap, uint64_t e_first, uint32_t n,
+                                         uint32_t lane, F&& edge_at)
 {
     const uint32_t head = (uint32_t)(e_first & 1) < n ? (uint32_t)(e_first & 1) : n;
     if (head && lane == 0) {
         uint64_t s0, d0;
         edge_at(0, s0, d0);
-        store_pair(out, e_first, s0, d0);
+        if (PG_CHECK_OUT(e_first, cap)) store_pair(out, e_first, s0, d0);
     }
     for (uint32_t t2 = head + 2 * lane; t2 < n; t2 += 64) {
         uint64_t s0, d0;
@@ -575,9 +587,9 @@ __device__ __forceinline__ void emit_run(Id* out, uint64_t e_first, uint32_t n, 
         if (t2 + 1 < n) {
             uint64_t s1, d1;
             edge_at(t2 + 1, s1, d1);
-            store_two(out, e_first + t2, s0, d0, s1, d1);
+            if (PG_CHECK_OUT(e_first + t2 + 1, cap)) store_two(out, e_first + t2, s0, d0, s1, d1);
         } else {
-            store_pair(out, e_first + t2, s0, d0);
+            if (PG_CHECK_OUT(e_first + t2, cap)) store_pair(out, e_first + t2, s0, d0);
         }
     }
 }
@@ -612,7 +624,7 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     const uint64_t* __restrict__ off, const uint64_t* __restrict__ R,
     const FastDiv* __restrict__ divR, const QRecip* __restrict__ recip,
     const uint32_t* __restrict__ wide_flag, const uint32_t* __restrict__ stab,
-    Id* __restrict__ out, uint32_t block_off, uint32_t out_block0)
+    Id* __restrict__ out, uint32_t block_off, uint32_t out_block0, uint64_t out_cap)
 {
     constexpr bool kFast = kMode != 0;
     using CurT = typename std::conditional<kFast, uint32_t, uint64_t>::type;
@@ -636,8 +648,9 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
     if (sw == 0) {
         const uint64_t e0 = g.e0, base_id = (uint64_t)p * g.span;
         for (uint64_t e = lane; e < e0; e += 32)
-            store_pair(out, out_block + e, base_id + seed_endpoint(e, 0, g.n0),
-                       base_id + seed_endpoint(e, 1, g.n0));
+            if (PG_CHECK_OUT(out_block + e, out_cap))
+                store_pair(out, out_block + e, base_id + seed_endpoint(e, 0, g.n0),
+                           base_id + seed_endpoint(e, 1, g.n0));
     }
     __syncwarp();
 
@@ -656,9 +669,10 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             const uint32_t q = qv[r];
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, q);
             CurT prev = 0;
-            if (q != 0xFFFFu) prev = ws.cur[q];
+            const bool named = q != 0xFFFFu && PG_CHECK(q, B);
+            if (named) prev = ws.cur[q];
             __syncwarp();
-            if (q != 0xFFFFu && (peers & lt) == 0) ws.cur[q] = prev + __popc(peers);
+            if (named && (peers & lt) == 0) ws.cur[q] = prev + __popc(peers);
             __syncwarp();
             item[r * 32 + lane] = prev + __popc(peers & lt);
             qs[r * 32 + lane] = (uint16_t)q;
@@ -670,8 +684,9 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
         auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
             s_ = src_base + fdiv32((uint32_t)(base + t2), g.div_m32);
             d_ = (uint64_t)qs[t2] * g.span + (uint32_t)item[t2];
+            (void)PG_CHECK(item[t2], g.span);   // a local id of block qs[t2]
         };
-        emit_run(out, out_block + g.e0 + base, n, lane, edge_at);
+        emit_run(out, out_cap, out_block + g.e0 + base, n, lane, edge_at);
         __syncwarp();
     };
 
@@ -698,7 +713,7 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
             k = pos % (2 * kEmitRun);
             q = qs_all[k];
             cur = (uint32_t)item_all[k];
-            c = recip[q];
+            c = PG_CHECK(q, B) ? recip[q] : QRecip{0, 0, 0, 0};
             fresh = true;
         };
         // one link for every lane; a lane whose chain ended stores its value
@@ -760,7 +775,7 @@ __global__ void __launch_bounds__(kEmitThreads) pba_emit_kernel(
                 if (active && fresh) {
                     q = ws.qs[0][k];
                     cur = ws.item[0][k];
-                    if (q != 0xFFFFu) {
+                    if (q != 0xFFFFu && PG_CHECK(q, B)) {
                         qd.R = R[q];
                         qd.d = divR[q];
                     }
@@ -800,7 +815,8 @@ __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ 
 {
     constexpr uint32_t kBaRun = BaShape<Id>::run, kBaTile = BaShape<Id>::tile;
     __shared__ __align__(16) Id sDst[kBaTile];
-    if (blockIdx.x == 0) write_seed_edges(out, 0, 0, g.n0);
+    const uint64_t cap = g.e0 + g.N_e;   // edges of the output
+    if (blockIdx.x == 0) write_seed_edges(out, cap, 0, 0, g.n0);
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t N = g.N_e;
@@ -840,8 +856,9 @@ __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ 
         auto edge_at = [&](uint32_t t2, uint64_t& s_, uint64_t& d_) {
             s_ = g.n0 + (kFast ? fdiv32((uint32_t)(base + t2), g.div_m32) : fdiv(base + t2, g.div_m));
             d_ = (uint64_t)sDst[t2];
+            (void)PG_CHECK(d_, g.span);   // an id below the graph's vertex count
         };
-        emit_tile(out, g.e0 + base, n, edge_at);
+        emit_tile(out, cap, g.e0 + base, n, edge_at);
         __syncthreads();
     }
 }
@@ -849,6 +866,8 @@ __global__ void __launch_bounds__(kBaThreads) ba_kernel(const __grid_constant__ 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
+
+PG_CHECK_UNIT(pba)
 
 uint32_t pba_prefix_len(uint64_t N_e) { return (uint32_t)(N_e < kPrefixMax ? N_e : kPrefixMax); }
 
@@ -1060,6 +1079,7 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
     const uint32_t chunks = hc ? hc->chunks : 1;
     const uint32_t per = (nblk + chunks - 1) / chunks;
     const uint64_t edges_per_block = g.e0 + g.N_e;
+    const uint64_t out_cap = (uint64_t)nblk * edges_per_block;   // edges at d_out
     const size_t pair = id64 ? 16 : 8;
     for (uint32_t b0 = b_begin, c = 0; b0 < b_end; b0 += per, ++c) {
         const uint32_t nb = (b_end - b0 < per) ? b_end - b0 : per;
@@ -1069,23 +1089,29 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
             if (id64) {
                 if (lean)
                     pba_emit_kernel<uint64_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin);
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin,
+                        out_cap);
                 else
                     pba_emit_kernel<uint64_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin);
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin,
+                        out_cap);
                 if (!surely_fast)
                     pba_emit_kernel<uint64_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin);
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin,
+                        out_cap);
             } else {
                 if (lean)
                     pba_emit_kernel<uint32_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin);
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin,
+                        out_cap);
                 else
                     pba_emit_kernel<uint32_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin);
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin,
+                        out_cap);
                 if (!surely_fast)
                     pba_emit_kernel<uint32_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
-                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin);
+                        g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin,
+                        out_cap);
             }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

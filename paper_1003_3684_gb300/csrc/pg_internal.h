@@ -9,6 +9,7 @@
 #include <mutex>
 #include <cuda_runtime.h>
 
+#include "pg_check.cuh"
 #include "pg_common.cuh"
 
 namespace pgen {
@@ -155,5 +156,14 @@ cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertice
                        cudaStream_t s);
 
 int device_sm_count();
+
+#ifdef PGEN_CHECKED
+// Per-unit bounds-check records of the checked build (pg_check.cuh).
+cudaError_t check_access_kron(CheckRecord* out, int reset, uint32_t shift, cudaStream_t s);
+cudaError_t check_access_pba(CheckRecord* out, int reset, uint32_t shift, cudaStream_t s);
+cudaError_t check_access_csr(CheckRecord* out, int reset, uint32_t shift, cudaStream_t s);
+cudaError_t check_access_batch(CheckRecord* out, int reset, uint32_t shift, cudaStream_t s);
+cudaError_t check_access_analyze(CheckRecord* out, int reset, uint32_t shift, cudaStream_t s);
+#endif
 
 }  // namespace pgen

@@ -240,61 +240,82 @@ class Server:
             batch.append(r)
         return batch
 
+    def _fail(self, batch, why: str):
+        """Requests of a batch whose launch failed: failed, budget returned."""
+        for r in batch:
+            r.row_ptr = r.col = None
+            if r.held:
+                self._give_back(r, r.held)
+            r.state, r.error = "failed", why
+            self.failed.append(r)
+
     def _launch(self, now):
         if not self._cuda:
             self._init_cuda()
-        torch, pg = self.torch, self.pg
         for i, b in self.busy.items():
             if b is not None or not self.admitted:
                 continue
             batch = self._next_batch()
-            s = self.streams[i]
-            with torch.cuda.stream(s):
-                if self.per_graph:
-                    offs = np.cumsum([0] + [job_edges(r.job) + (job_edges(r.job) & 1)
-                                            for r in batch])
-                    arena = torch.empty((max(int(offs[-1]), 1), 2), dtype=torch.int32,
-                                        device=self.device)
-                    for k, r in enumerate(batch):
-                        j, a = r.job, int(offs[k])
-                        sl = arena[a:a + job_edges(j)]
-                        if j["kind"] == "pba":
-                            pg.gen_pba(j["n"], j["m"], 1, j["n0"], 1, 0.0, j["seed"], out=sl,
-                                       stream=s)
-                        else:
-                            pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"],
-                                             out=sl, stream=s)
-                        self.launches += 1
-                    plan = None
-                    offsets = [int(x) for x in offs]
-                else:
-                    plan = pg.BatchPlan([r.job for r in batch], tile_edges=self.tile_edges,
-                                        device=self.device)
-                    arena = torch.empty((max(plan.total_edges, 1), 2), dtype=torch.int32,
-                                        device=self.device)
-                    pg.gen_batch(plan, arena=arena, workspace=self.batch_ws[i], stream=s)
-                    self.launches += 1
-                    offsets = [int(x) for x in plan.offsets]
-                # one CSR workspace for the batch, sized for its largest
-                # request (each request's share is counted in its bytes)
-                need = max(pg.pg_csr_workspace_size(job_edges(r.job), job_vertices(r.job))
-                           for r in batch)
-                ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
-                status = torch.zeros(len(batch), dtype=torch.int32, pin_memory=True)
+            try:
+                self.busy[i] = self._start(i, batch, now)
+            except (RuntimeError, MemoryError) as exc:
+                # a device allocation that failed, or a library call that
+                # refused: this batch fails, the server goes on. Work already
+                # queued on the stream only touches buffers allocated on that
+                # stream, which the allocator hands out again only to later
+                # work on the same stream.
+                self._fail(batch, f"launch failed: {exc}")
+
+    def _start(self, i, batch, now) -> _Batch:
+        """Queue one batch on stream i: generation, then a CSR per request."""
+        torch, pg = self.torch, self.pg
+        s = self.streams[i]
+        with torch.cuda.stream(s):
+            if self.per_graph:
+                offs = np.cumsum([0] + [job_edges(r.job) + (job_edges(r.job) & 1)
+                                        for r in batch])
+                arena = pg.empty_device((max(int(offs[-1]), 1), 2), torch.int32,
+                                        self.device)
                 for k, r in enumerate(batch):
-                    a = offsets[k]
-                    z = a + job_edges(r.job)
-                    E, N = job_edges(r.job), job_vertices(r.job)
-                    r.row_ptr, r.col = pg.edges_to_csr(arena[a:z], N, workspace=ws, stream=s)
-                    off = pg.pg_csr_wait_error_offset(E, N)
-                    if off is not None:   # the call's wait word, to pinned memory
-                        status[k:k + 1].copy_(ws[off:off + 4].view(torch.int32), non_blocking=True)
-                    r.launched = now
-                    r.state = "running"
+                    j, a = r.job, int(offs[k])
+                    sl = arena[a:a + job_edges(j)]
+                    if j["kind"] == "pba":
+                        pg.gen_pba(j["n"], j["m"], 1, j["n0"], 1, 0.0, j["seed"], out=sl,
+                                   stream=s)
+                    else:
+                        pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"],
+                                         out=sl, stream=s)
                     self.launches += 1
-                ev = torch.cuda.Event()
-                ev.record(s)
-            self.busy[i] = _Batch(batch, s, ev, keep=[plan, arena, ws], status=status)
+                plan = None
+                offsets = [int(x) for x in offs]
+            else:
+                plan = pg.BatchPlan([r.job for r in batch], tile_edges=self.tile_edges,
+                                    device=self.device)
+                arena = pg.empty_device((max(plan.total_edges, 1), 2), torch.int32,
+                                        self.device)
+                pg.gen_batch(plan, arena=arena, workspace=self.batch_ws[i], stream=s)
+                self.launches += 1
+                offsets = [int(x) for x in plan.offsets]
+            # one CSR workspace for the batch, sized for its largest
+            # request (each request's share is counted in its bytes)
+            need = max(pg.pg_csr_workspace_size(job_edges(r.job), job_vertices(r.job))
+                       for r in batch)
+            ws = pg.empty_device(max(need, 256), torch.uint8, self.device)
+            status = torch.zeros(len(batch), dtype=torch.int32, pin_memory=True)
+            for k, r in enumerate(batch):
+                a = offsets[k]
+                z = a + job_edges(r.job)
+                E, N = job_edges(r.job), job_vertices(r.job)
+                r.row_ptr, r.col = pg.edges_to_csr(arena[a:z], N, workspace=ws, stream=s)
+                off = pg.pg_csr_wait_error_offset(E, N)
+                if off is not None:   # the call's wait word, to pinned memory
+                    status[k:k + 1].copy_(ws[off:off + 4].view(torch.int32), non_blocking=True)
+                r.launched = now
+                r.state = "running"
+                self.launches += 1
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return _Batch(batch, s, ev, keep=[plan, arena, ws], status=status)
 
     def step(self, now: float | None = None) -> int:
         """One scheduling step; returns the number of requests completed."""

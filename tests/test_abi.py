@@ -3,6 +3,8 @@ rejects bad arguments on the host before any launch (no GPU needed)."""
 import ctypes as C
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -234,3 +236,49 @@ def test_csr_check_arguments_on_host(L):
     assert L.pg_csr_check(None, 0, 10, 0, 0, None) == 0
     assert L.pg_csr_check(None, 10, 1, 0, 0, None) == 0
     assert L.pg_csr_check(None, 10, 10, 0, 0, None) == 1     # a sorting call needs its workspace
+
+
+@pytest.fixture(scope="module")
+def LC(L):
+    """The bounds-checked build, loaded by path beside the default one."""
+    return C.CDLL(os.path.join(ROOT, "paper_1003_3684_gb300", "libpgen_checked.so"))
+
+
+def test_checked_library_exports_every_declared_symbol(LC):
+    for name in declared_functions():
+        assert hasattr(LC, name), name
+
+
+def test_checked_build_flag_and_host_side_checks(L, LC):
+    for lib in (L, LC):
+        lib.pg_checked_build.restype = C.c_int
+        lib.pg_check_test_out_shift.argtypes = [C.c_uint32, C.c_void_p]
+        lib.pg_check_test_out_shift.restype = C.c_int
+        lib.pg_check_read.restype = C.c_int
+    assert L.pg_checked_build() == 0 and LC.pg_checked_build() == 1
+    # the default build has no checks: the hook is refused, the record is empty
+    assert L.pg_check_test_out_shift(1, None) == 1
+    count, unit = C.c_uint32(7), C.c_uint32(7)
+    assert L.pg_check_read(1, C.byref(count), C.byref(unit), None, None, None, None) == 0
+    assert count.value == 0 and unit.value == 0
+    # the checked build refuses a shift past 63 before touching the device
+    assert LC.pg_check_test_out_shift(64, None) == 1
+
+
+@pytest.mark.parametrize("variant,expect", [("default", "False libpgen.so"),
+                                            ("checked", "True libpgen_checked.so")])
+def test_binding_loads_the_library_named_by_the_environment(L, variant, expect):
+    code = ("import os, paper_1003_3684_gb300 as pg; "
+            "print(pg.pg_checked_build(), os.path.basename(pg.library_path()))")
+    env = dict(os.environ, PGEN_LIBRARY=variant)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == expect
+
+
+def test_binding_rejects_an_unknown_library_variant():
+    env = dict(os.environ, PGEN_LIBRARY="fast")
+    r = subprocess.run([sys.executable, "-c", "import paper_1003_3684_gb300"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "PGEN_LIBRARY" in r.stderr

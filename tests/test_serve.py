@@ -16,23 +16,26 @@ class FakeEvent:
 
 class FakeServer(serve.Server):
     """Server whose 'device' finishes a batch 1 ms per million edges later.
-    `fail` holds request ids whose CSR sort reports a wait that gave up."""
+    `fail` holds request ids whose CSR sort reports a wait that gave up;
+    a batch holding a request id of `refuse` fails to launch, as when a
+    device allocation fails."""
 
     fail = ()
+    refuse = ()
 
-    def _launch(self, now):
-        for i, b in self.busy.items():
-            if b is not None or not self.admitted:
-                continue
-            batch = self._next_batch()
-            for r in batch:
-                r.launched = now
-                r.state = "running"
-            cost = sum(serve.job_edges(r.job) for r in batch) / 1e9
-            status = np.array([1 if r.rid in self.fail else 0 for r in batch], np.int32)
-            self.busy[i] = serve._Batch(batch, None, FakeEvent(self.clock, now + cost),
-                                        status=status)
-            self.launches += 1
+    def _init_cuda(self):
+        self._cuda = True
+
+    def _start(self, i, batch, now):
+        if any(r.rid in self.refuse for r in batch):
+            raise MemoryError("fake device: out of memory")
+        for r in batch:
+            r.launched = now
+            r.state = "running"
+        cost = sum(serve.job_edges(r.job) for r in batch) / 1e9
+        status = np.array([1 if r.rid in self.fail else 0 for r in batch], np.int32)
+        self.launches += 1
+        return serve._Batch(batch, None, FakeEvent(self.clock, now + cost), status=status)
 
 
 def fake_clock():
@@ -146,6 +149,46 @@ def test_failed_csr_wait_is_reported_not_completed():
     assert srv.in_use == 0 and len(reqs) == 6
 
 
+def test_failed_launch_fails_its_batch_and_the_server_goes_on():
+    clock, advance = fake_clock()
+    jobs = [serve.job_for_edges("kron", 2**14, seed=i) for i in range(8)]
+    srv = FakeServer(budget_bytes=1 << 40, n_streams=1, max_batch_jobs=2, clock=clock)
+    srv.refuse = {2}
+    reqs = [srv.submit(j, now=0.0) for j in jobs]
+    run_until_idle(srv, advance)
+    assert sorted(r.rid for r in srv.failed) == [2, 3]          # the batch [2, 3]
+    assert all(r.state == "failed" and "out of memory" in r.error and r.held == 0
+               and r.launched is None for r in srv.failed)
+    assert sorted(r.rid for r in srv.completed) == [0, 1, 4, 5, 6, 7]
+    assert srv.in_use == 0 and len(reqs) == 8
+
+
+def test_allocation_failure_injection_on_the_host():
+    import subprocess
+    import sys
+
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    pg.set_fail_alloc_at(3)
+    try:
+        pg.empty_device(4, torch.int32, "cpu")
+        pg.empty_device((2, 2), torch.int64, "cpu")
+        with pytest.raises(torch.cuda.OutOfMemoryError, match="injected"):
+            pg.empty_device(8, torch.uint8, "cpu")
+        pg.empty_device(8, torch.uint8, "cpu")                 # once only
+    finally:
+        pg.set_fail_alloc_at(0)
+    code = ("import torch, paper_1003_3684_gb300 as pg\n"
+            "try:\n    pg.empty_device(2, torch.int32, 'cpu')\n"
+            "except torch.cuda.OutOfMemoryError:\n    print('refused')\n")
+    import os
+    from conftest import ROOT
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       env=dict(os.environ, PGEN_FAIL_ALLOC_AT="1"), timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "refused", r.stderr
+
+
 def test_request_bytes_count_the_csr_workspace():
     import paper_1003_3684_gb300 as pg
     for kind, E in (("pba", 2**12), ("kron", 2**20)):
@@ -217,3 +260,39 @@ def test_open_loop_short_run():
     assert len(done) == len(arr)
     lat = np.array([r.latency for r in done])
     assert (lat > 0).all()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_injected_allocation_failure_fails_one_batch(k):
+    # the first batch (requests 0 and 1) allocates its arena (1), the CSR
+    # workspace (2), then row_ptr and col of request 0 (3, 4) and of
+    # request 1 (5, 6): k = 1 fails before any kernel, 2 after the batch
+    # kernel, 5 after request 0's CSR was queued
+    import torch
+
+    import oracle as o
+    import paper_1003_3684_gb300 as pg
+    jobs = [serve.job_for_edges("pba" if i % 2 else "kron", 2**13 + 512 * i, seed=i)
+            for i in range(6)]
+    srv = serve.Server(budget_bytes=8 << 30, n_streams=1, max_batch_jobs=2)
+    reqs = [srv.submit(j) for j in jobs]
+    srv._init_cuda()
+    pg.set_fail_alloc_at(k)
+    try:
+        srv.drain()
+    finally:
+        pg.set_fail_alloc_at(0)
+    torch.cuda.synchronize()
+    assert [r.rid for r in srv.failed] == [0, 1]
+    assert all("injected allocation failure" in r.error and r.held == 0 for r in srv.failed)
+    assert [r.rid for r in srv.completed] == [2, 3, 4, 5]
+    for r in reqs[2:]:
+        j = r.job
+        e = (o.ba(j["n"], j["m"], j["n0"], j["seed"]) if j["kind"] == "pba"
+             else o.kron(j["initiator"], j["k"], j["n_edges"], j["seed"]))
+        ref_rp, ref_col = o.csr(e, serve.job_vertices(j))
+        assert np.array_equal(r.row_ptr.cpu().numpy().view(np.uint64), ref_rp)
+        assert np.array_equal(r.col.cpu().numpy().view(np.uint32).astype(np.uint64), ref_col)
+        srv.release(r)
+    assert srv.in_use == sum(w.numel() for w in srv.batch_ws)
