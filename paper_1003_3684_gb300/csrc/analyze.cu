@@ -64,15 +64,78 @@ __device__ __forceinline__ uint64_t load_streaming(const uint64_t* p)
     return __ldcs(reinterpret_cast<const unsigned long long*>(p));
 }
 
-// One BFS level. Each warp takes 32 frontier vertices at a time and walks
-// their rows as one concatenated range, 32 adjacency entries per step: lane
-// k of a step finds the vertex owning entry base + k by a binary search over
-// the 32 rows' starts (a warp scan of their degrees, kept in shared memory),
-// so short rows (most rows of a power-law graph) do not leave lanes idle and
-// a hub row is walked by the whole warp. A neighbour whose bit in the visited
-// bitmap (N bits, small enough to stay in L2) is clear is claimed by an atomic
-// OR of that bit; the claimer writes its distance and appends it to the next
-// frontier. scanned += the degrees of the frontier.
+// Claims for one step of 32 adjacency entries: lane l holds neighbour u when
+// `have`. A neighbour whose bit in the visited bitmap (N bits, small enough
+// to stay in L2) is clear is claimed by an atomic OR of that bit; the claimer
+// writes its distance. Claimed vertices collect in the warp's buffer (64
+// slots, fewer than 32 held between steps) and leave for the next frontier
+// 32 at a time, so the frontier's counter takes one atomic per 32 claims (the
+// frontier's order is not part of the result).
+struct BfsQueue {
+    uint32_t* buf;       // this warp's 64 shared-memory slots
+    uint32_t held;       // warp-uniform, < 32 between steps
+    uint32_t* next;
+    uint32_t* nsize;
+    uint32_t* dist;
+    uint32_t* vis;
+    uint32_t level;
+    uint64_t N;
+
+    __device__ __forceinline__ void step(bool have, uint32_t u, uint32_t lane, uint32_t lt)
+    {
+        bool claim = false;
+        if (have) {
+            const uint32_t bit = 1u << (u & 31);
+            // a stale cached word only costs an atomic that finds the bit set
+            if ((vis[u >> 5] & bit) == 0) claim = (atomicOr(&vis[u >> 5], bit) & bit) == 0;
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, claim);
+        if (claim) {
+            dist[u] = level + 1;
+            buf[held + __popc(m & lt)] = u;
+        }
+        held += __popc(m);
+        if (held >= 32) {
+            __syncwarp();
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(nsize, 32u);
+            at = __shfl_sync(0xFFFFFFFFu, at, 0);
+            if (PG_CHECK(at + lane, N)) next[at + lane] = buf[lane];
+            const uint32_t rest = held - 32;
+            const uint32_t x = lane < rest ? buf[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) buf[lane] = x;
+            __syncwarp();
+            held = rest;
+        }
+    }
+
+    __device__ __forceinline__ void flush(uint32_t lane)
+    {
+        __syncwarp();
+        if (held) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(nsize, held);
+            at = __shfl_sync(0xFFFFFFFFu, at, 0);
+            if (lane < held && PG_CHECK(at + lane, N)) next[at + lane] = buf[lane];
+        }
+    }
+};
+
+// Rows of kLongRow or more entries leave the level kernel for the slice
+// kernel, which cuts them into slices of kSlice entries spread over all warps.
+constexpr uint64_t kLongRow = 64;
+constexpr uint32_t kSlice = 512;
+
+// One BFS level, short rows. Each warp takes 32 frontier vertices at a time
+// and walks their short rows as one concatenated range, 32 adjacency entries
+// per step: lane k of a step finds the vertex owning entry base + k by a
+// binary search over the 32 rows' starts (a warp scan of their degrees, kept
+// in shared memory), so short rows (most rows of a power-law graph) do not
+// leave lanes idle. A long row is appended to the long-row list instead:
+// one 64-bit atomic on long_ctr adds 1 to the row count (high word) and its
+// slice count to the slice total (low word), so the slice bases of the list
+// ascend with its index. scanned += the short rows' lengths.
 template <typename Id>
 __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_t* __restrict__ row_ptr,
                                                         const Id* __restrict__ col,
@@ -82,21 +145,20 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
                                                         uint32_t* __restrict__ dist,
                                                         uint32_t* __restrict__ vis, uint32_t level,
                                                         uint64_t N,
-                                                        unsigned long long* __restrict__ scanned)
+                                                        unsigned long long* __restrict__ scanned,
+                                                        unsigned long long* __restrict__ long_ctr,
+                                                        uint32_t* __restrict__ long_v,
+                                                        uint32_t* __restrict__ long_base)
 {
-    // claimed vertices collect in a per-warp buffer and leave 32 at a time,
-    // so the shared counter of the next frontier takes one atomic per 32
-    // claims (the frontier's order is not part of the result)
     __shared__ uint32_t wbuf[kBfsWarps][64];
     __shared__ uint64_t wstart[kBfsWarps][32];   // the 32 rows' starts in the concatenation
     __shared__ uint64_t wrow[kBfsWarps][32];     // and in col
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    uint32_t* buf = wbuf[wid];
+    BfsQueue Q{wbuf[wid], 0, next, nsize, dist, vis, level, N};
     uint64_t* st = wstart[wid];
     uint64_t* rw = wrow[wid];
-    uint32_t held = 0;   // warp-uniform, < 32 between chunks
     unsigned long long seen = 0;
     const uint64_t first = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     for (uint64_t c = first; c < fsize; c += warps * 32) {
@@ -105,8 +167,18 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
             const uint32_t v = frontier[c + lane];
             a = row_ptr[v];
             d = row_ptr[v + 1] - a;
+            if (d >= kLongRow) {
+                const uint64_t ns = (d + kSlice - 1) / kSlice;
+                const unsigned long long old = atomicAdd(long_ctr, (1ull << 32) | ns);
+                const uint32_t r = (uint32_t)(old >> 32);
+                if (PG_CHECK(r, N)) {
+                    long_v[r] = v;
+                    long_base[r] = (uint32_t)old;
+                }
+                d = 0;
+            }
         }
-        // inclusive scan of the degrees over the warp
+        // inclusive scan of the short rows' lengths over the warp
         uint64_t incl = d;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -120,7 +192,7 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
         seen += total;
         for (uint64_t base = 0; base < total; base += 32) {
             const uint64_t k = base + lane;
-            bool claim = false;
+            bool have = false;
             uint32_t u = 0;
             if (k < total) {
                 // the last row whose start is at or below k owns entry k (an
@@ -129,44 +201,77 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
 #pragma unroll
                 for (uint32_t step = 16; step > 0; step >>= 1)
                     if (st[o + step] <= k) o += step;
-                const uint64_t e = rw[o] + (k - st[o]);
-                const uint64_t u64 = load_streaming(col + e);
-                if (u64 < N) {
-                    u = (uint32_t)u64;
-                    const uint32_t bit = 1u << (u & 31);
-                    // a stale cached word only costs an atomic that finds the bit set
-                    if ((vis[u >> 5] & bit) == 0) claim = (atomicOr(&vis[u >> 5], bit) & bit) == 0;
-                }
+                const uint64_t u64 = load_streaming(col + rw[o] + (k - st[o]));
+                have = u64 < N;
+                u = (uint32_t)u64;
             }
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, claim);
-            if (claim) {
-                dist[u] = level + 1;
-                buf[held + __popc(m & lt)] = u;
-            }
-            held += __popc(m);
-            if (held >= 32) {
-                __syncwarp();
-                uint32_t at = 0;
-                if (lane == 0) at = atomicAdd(nsize, 32u);
-                at = __shfl_sync(0xFFFFFFFFu, at, 0);
-                if (PG_CHECK(at + lane, N)) next[at + lane] = buf[lane];
-                const uint32_t rest = held - 32;
-                const uint32_t x = lane < rest ? buf[32 + lane] : 0;
-                __syncwarp();
-                if (lane < rest) buf[lane] = x;
-                __syncwarp();
-                held = rest;
-            }
+            Q.step(have, u, lane, lt);
         }
         __syncwarp();   // the next chunk rewrites the row tables
     }
-    __syncwarp();
-    if (held) {
-        uint32_t at = 0;
-        if (lane == 0) at = atomicAdd(nsize, held);
-        at = __shfl_sync(0xFFFFFFFFu, at, 0);
-        if (lane < held && PG_CHECK(at + lane, N)) next[at + lane] = buf[lane];
+    Q.flush(lane);
+    if (lane == 0 && seen) atomicAdd(scanned, seen);
+}
+
+// One BFS level, long rows: slice t of the level's long rows is entries
+// [t - long_base[r]) * kSlice, ...) of row r, the last row whose base is at
+// or below t. Warps take slices t = warp, warp + warps, ...; a warp finds r
+// by a 32-way search (each round the lanes test 32 evenly spaced bases and
+// a ballot keeps the interval below the first base above t), then walks the
+// slice 32 entries per step with the same claims as the level kernel.
+template <typename Id>
+__global__ void __launch_bounds__(kBfsWarps * 32) bfs_long_kernel(const uint64_t* __restrict__ row_ptr,
+                                                       const Id* __restrict__ col,
+                                                       uint32_t* __restrict__ next,
+                                                       uint32_t* __restrict__ nsize,
+                                                       uint32_t* __restrict__ dist,
+                                                       uint32_t* __restrict__ vis, uint32_t level,
+                                                       uint64_t N,
+                                                       unsigned long long* __restrict__ scanned,
+                                                       const unsigned long long* __restrict__ long_ctr,
+                                                       const uint32_t* __restrict__ long_v,
+                                                       const uint32_t* __restrict__ long_base)
+{
+    __shared__ uint32_t wbuf[kBfsWarps][64];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const unsigned long long ctr = *long_ctr;   // written by the level kernel before
+    const uint32_t rows = (uint32_t)(ctr >> 32), slices = (uint32_t)ctr;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    BfsQueue Q{wbuf[wid], 0, next, nsize, dist, vis, level, N};
+    unsigned long long seen = 0;
+    for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + wid; t < slices; t += warps) {
+        uint32_t lo = 0, n = rows;   // r lies in [lo, lo + n); long_base[lo] <= t
+        while (n > 1) {
+            const uint32_t step = (n + 31) / 32;
+            const uint32_t off = lane * step;
+            const bool le = off < n && PG_CHECK(lo + off, rows) && long_base[lo + off] <= t;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, le);   // lane 0 always set
+            const uint32_t k = 31 - __clz(m);
+            lo += k * step;
+            n = (n - k * step < step) ? n - k * step : step;
+        }
+        uint64_t e0 = 0, e1 = 0;
+        if (PG_CHECK(lo, rows) && PG_CHECK(long_v[lo], N)) {
+            const uint32_t v = long_v[lo];
+            const uint64_t a = row_ptr[v], end = row_ptr[v + 1];
+            e0 = a + (uint64_t)(t - long_base[lo]) * kSlice;
+            e1 = (e0 + kSlice < end) ? e0 + kSlice : end;
+            if (e0 > e1) e0 = e1;
+        }
+        seen += e1 - e0;
+        for (uint64_t e = e0; e < e1; e += 32) {
+            bool have = false;
+            uint32_t u = 0;
+            if (e + lane < e1) {
+                const uint64_t u64 = load_streaming(col + e + lane);
+                have = u64 < N;
+                u = (uint32_t)u64;
+            }
+            Q.step(have, u, lane, lt);
+        }
     }
+    Q.flush(lane);
     if (lane == 0 && seen) atomicAdd(scanned, seen);
 }
 
@@ -232,8 +337,9 @@ pg_status pg_degree_histogram(const uint64_t* d_deg, uint64_t n_vertices, uint32
 
 size_t pg_bfs_workspace_size(uint64_t n_vertices)
 {
-    // two frontiers of n_vertices uint32, the counters, the visited bitmap
-    return 2 * (((size_t)n_vertices * 4 + 255) & ~(size_t)255) + 256 +
+    // two frontiers of n_vertices uint32, the counters, the visited bitmap,
+    // and the long-row list (a vertex and a slice base per row)
+    return 4 * (((size_t)n_vertices * 4 + 255) & ~(size_t)255) + 256 +
            ((((size_t)n_vertices + 31) / 32 * 4 + 255) & ~(size_t)255);
 }
 
@@ -249,27 +355,42 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
     const size_t fbytes = ((size_t)n_vertices * 4 + 255) & ~(size_t)255;
     unsigned char* ws = (unsigned char*)d_ws;
     uint32_t* fr[2] = {(uint32_t*)ws, (uint32_t*)(ws + fbytes)};
+    // counters: the next frontier's size and the long-row list's counts,
+    // zeroed every level, then the scanned total
     uint32_t* nsize = (uint32_t*)(ws + 2 * fbytes);
-    unsigned long long* scanned = (unsigned long long*)(ws + 2 * fbytes + 8);
+    unsigned long long* long_ctr = (unsigned long long*)(ws + 2 * fbytes + 8);
+    unsigned long long* scanned = (unsigned long long*)(ws + 2 * fbytes + 16);
     uint32_t* vis = (uint32_t*)(ws + 2 * fbytes + 256);
     const size_t vbytes = ((size_t)n_vertices + 31) / 32 * 4;
+    unsigned char* lists = ws + 2 * fbytes + 256 + ((vbytes + 255) & ~(size_t)255);
+    uint32_t* long_v = (uint32_t*)lists;
+    uint32_t* long_base = (uint32_t*)(lists + fbytes);
     if (cudaMemsetAsync(d_dist, 0xFF, n_vertices * 4, s) != cudaSuccess) return PG_ECUDA;
     if (cudaMemsetAsync(ws + 2 * fbytes, 0, 256, s) != cudaSuccess) return PG_ECUDA;
     if (cudaMemsetAsync(vis, 0, vbytes, s) != cudaSuccess) return PG_ECUDA;
     bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, vis, fr[0], (uint32_t)source);
     uint32_t fsize = 1, level = 0, cur = 0;
     TraceScope trace("bfs", s);
+    // the slice kernel's grid: every warp of a full wave takes slices
+    const int long_grid = device_sm_count() * 8;
     while (fsize > 0) {
-        if (cudaMemsetAsync(nsize, 0, 4, s) != cudaSuccess) return PG_ECUDA;
+        if (cudaMemsetAsync(nsize, 0, 16, s) != cudaSuccess) return PG_ECUDA;
         const int grid = grid_cap(fsize);
-        if (w == PG_ID64)
-            bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(d_row_ptr, (const uint64_t*)d_col,
-                                                            fr[cur], fsize, fr[cur ^ 1], nsize,
-                                                            d_dist, vis, level, n_vertices, scanned);
-        else
-            bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(d_row_ptr, (const uint32_t*)d_col,
-                                                            fr[cur], fsize, fr[cur ^ 1], nsize,
-                                                            d_dist, vis, level, n_vertices, scanned);
+        if (w == PG_ID64) {
+            bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                d_row_ptr, (const uint64_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist, vis,
+                level, n_vertices, scanned, long_ctr, long_v, long_base);
+            bfs_long_kernel<uint64_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
+                d_row_ptr, (const uint64_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
+                n_vertices, scanned, long_ctr, long_v, long_base);
+        } else {
+            bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                d_row_ptr, (const uint32_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist, vis,
+                level, n_vertices, scanned, long_ctr, long_v, long_base);
+            bfs_long_kernel<uint32_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
+                d_row_ptr, (const uint32_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
+                n_vertices, scanned, long_ctr, long_v, long_base);
+        }
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
         // the next frontier's size decides whether another level runs
         if (cudaMemcpyAsync(&fsize, nsize, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -594,10 +594,19 @@ def _bfs_case(name):
         return e, n, o.CSR_SYMMETRIZE, [0, 1500]
     if name == "single":
         return np.zeros((0, 2), np.uint64), 1, 0, [0]
+    if name == "hubs":
+        # vertex 0 joined to 1..4999 (a row of ten 512-entry slices); each of
+        # 1..1500 joined to 70 vertices of its own (1500 rows of 71 entries:
+        # more than 32^2 long rows in one level)
+        hub = np.stack([np.zeros(4999, np.uint64), np.arange(1, 5000, dtype=np.uint64)], 1)
+        owner = np.repeat(np.arange(1, 1501, dtype=np.uint64), 70)
+        leaf = 5000 + np.arange(1500 * 70, dtype=np.uint64)
+        e = np.concatenate([hub, np.stack([owner, leaf], 1)])
+        return e, 5000 + 1500 * 70, o.CSR_SYMMETRIZE, [0, 1, 7000]
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["pba_undirected", "kron_directed", "path", "single"])
+@pytest.mark.parametrize("name", ["pba_undirected", "kron_directed", "path", "single", "hubs"])
 @pytest.mark.parametrize("id64", [False, True])
 def test_bfs_matches_oracle(name, id64):
     e, N, flags, sources = _bfs_case(name)
