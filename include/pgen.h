@@ -448,30 +448,54 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
 /* ------------------------------------------------------------------------
  * Batched generation: many independent graphs in one persistent launch. The
  * batching is not in the paper; each job is one of its generators (Sec. 3,
- * the O(1) preferential attachment of the PBA method with one block, or the
- * stochastic Kronecker model that the PK method cites in Sec. 2).
+ * the O(1) preferential attachment of the PBA method, or the stochastic
+ * Kronecker model that the PK method cites in Sec. 2).
  *
- * A job is a serial BA graph (gen_pba with blocks = 1: n new vertices, m
- * edges each, seed clique K_{n0}) or a stochastic Kronecker graph (as
- * gen_kronecker with PG_KRON_STOCHASTIC). Job i's edges are exactly those the
- * single-graph call with the same arguments writes, placed at
- * h_edge_offsets[i] in one shared output arena.
+ * A job is a BA graph (as gen_pba: n new vertices, m edges each, seed
+ * clique K_{n0}; blocks <= 1 is the serial model, blocks > 1 the two-phase
+ * PBA method with inter_frac and faction_width as in gen_pba) or a
+ * stochastic Kronecker graph (as gen_kronecker with PG_KRON_STOCHASTIC).
+ * Job i's edges are exactly those the single-graph call with the same
+ * arguments writes, placed at h_edge_offsets[i] in one shared output arena.
+ * Jobs follow one another in the arena, except that with PG_ID32 a
+ * two-phase job starts at an even edge, so one unused arena edge may
+ * precede it.
  *
  * pg_batch_plan (host only) validates the jobs and writes a plan of
  * pg_batch_plan_size() bytes into h_plan: per-job records (parameters,
- * Philox round keys, thresholds, arena offset) and a work-item table that
- * cuts every job into tiles of tile_edges edges (64 <= tile_edges <= 8192,
- * a multiple of 64). h_edge_offsets (n_jobs + 1 entries, may be NULL)
- * receives each job's first edge and the total; h_n_items the number of
- * work items. 32-bit chain arithmetic is used, so BA jobs need
+ * Philox round keys, thresholds, arena offset), a work-item table that cuts
+ * every serial-BA and Kronecker job into tiles of tile_edges edges (64 <=
+ * tile_edges <= 8192, a multiple of 64), and the launch geometry of the
+ * two-phase jobs. h_edge_offsets (n_jobs + 1 entries, may be NULL) receives
+ * each job's first edge and the arena length; h_n_items the number of work
+ * items. 32-bit chain arithmetic is used, so serial BA jobs need
  * n*m + e0 < 2^32. At most 8192 jobs.
  *
  * gen_batch launches one persistent kernel over a copy of the plan in
  * device memory (d_plan, 16-byte aligned): resident CTAs claim work items
- * from a counter in d_ws (pg_batch_workspace_size() bytes, reset by the
- * call) until none are left. grid_ctas = 0 picks one wave of resident CTAs.
- * The call is stream-ordered with no host synchronisation and can be
- * captured in a CUDA graph; a replay regenerates the same edges.
+ * from a counter in d_ws until none are left. grid_ctas = 0 picks one wave
+ * of resident CTAs. Then each two-phase job runs the single-graph PBA
+ * kernels (phase 1, the count exchange, the emission) in d_ws after the
+ * counter. h_plan is the host plan d_plan was copied from (its two-phase
+ * geometry is read there). d_ws: pg_batch_workspace_size(h_plan) bytes,
+ * 256-byte aligned. The call is stream-ordered with no host
+ * synchronisation and can be captured in a CUDA graph; a replay regenerates
+ * the same edges.
+ *
+ * gen_batch_csr builds, after gen_batch on the same stream, the CSR (as
+ * edges_to_csr) of every job with want_csr: job i's row_ptr (its vertex
+ * count + 1 entries, starting at 0) at d_row_ptr[row_offset_i], and its
+ * col entries (its edge count) at d_col[col_offset_i], the offsets given
+ * by pg_batch_csr_layout (UINT64_MAX for a job without want_csr). All of
+ * them come from one CSR of the jobs' union graph, in a fixed number of
+ * launches whatever the number of jobs: each job's sources are shifted by
+ * the vertices of the CSR jobs before it, the union is sorted once, and
+ * every job's row_ptr is rebased to 0. With PG_ID32 the CSR jobs' vertices
+ * together must be at most 2^32. d_ws: pg_batch_csr_workspace_size(h_plan)
+ * bytes, 256-byte aligned; its wait word (see pg_csr_wait_error_offset) is
+ * at pg_batch_csr_wait_error_offset(h_plan) (SIZE_MAX when the call sorts
+ * nothing). PG_ENOSPC when cap_row_ptr or cap_col is smaller than the
+ * totals of pg_batch_csr_layout.
  * ---------------------------------------------------------------------- */
 typedef enum { PG_JOB_BA = 0, PG_JOB_KRON = 1 } pg_job_kind;
 
@@ -483,16 +507,28 @@ typedef struct {
     uint64_t n;               /* BA: new vertices; KRON: edge count */
     uint64_t seed;            /* Philox key */
     const double* initiator;  /* KRON: host, n0*n0 doubles, row-major */
+    uint32_t blocks;          /* BA: vertex blocks (0 or 1: serial BA) */
+    uint32_t faction_width;   /* BA with blocks > 1: faction width (0: 1) */
+    double inter_frac;        /* BA with blocks > 1: inter-block fraction */
+    uint32_t want_csr;        /* 1: gen_batch_csr builds this job's CSR */
+    uint32_t reserved;        /* 0 */
 } pg_job;
 
 size_t pg_batch_plan_size(const pg_job* jobs, uint32_t n_jobs);
-size_t pg_batch_workspace_size(void);
+size_t pg_batch_workspace_size(const void* h_plan);
 pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges, pg_idwidth w,
                         void* h_plan, size_t plan_size, uint64_t* h_edge_offsets,
                         uint64_t* h_n_items);
-pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_arena,
-                    uint64_t cap_edges, uint64_t total_edges, uint32_t grid_ctas, void* d_ws,
-                    size_t ws_bytes, void* stream);
+pg_status gen_batch(const void* h_plan, const void* d_plan, uint32_t n_jobs, pg_idwidth w,
+                    void* d_arena, uint64_t cap_edges, uint64_t total_edges, uint32_t grid_ctas,
+                    void* d_ws, size_t ws_bytes, void* stream);
+pg_status pg_batch_csr_layout(const void* h_plan, uint32_t n_jobs, uint64_t* h_row_offsets,
+                              uint64_t* h_col_offsets, uint64_t* rows_total, uint64_t* cols_total);
+size_t pg_batch_csr_workspace_size(const void* h_plan);
+size_t pg_batch_csr_wait_error_offset(const void* h_plan);
+pg_status gen_batch_csr(const void* h_plan, const void* d_plan, uint32_t n_jobs, pg_idwidth w,
+                        const void* d_arena, uint64_t* d_row_ptr, uint64_t cap_row_ptr,
+                        void* d_col, uint64_t cap_col, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * Kernel timing trace (profiling aid, not part of the method).

@@ -39,7 +39,8 @@ __all__ = [
     "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
     "pg_csr_wait_error_offset", "csr_wait_error", "pg_csr_check", "pg_csr_test_wait_hook",
     "pg_checked_build", "pg_check_read", "pg_check_test_out_shift", "CheckReport",
-    "empty_device", "set_fail_alloc_at",
+    "empty_device", "set_fail_alloc_at", "BatchPlan", "gen_batch", "pg_batch_workspace_size",
+    "gen_batch_csr", "pg_batch_csr_workspace_size", "pg_batch_csr_wait_error_offset",
 ]
 
 PG_OK, PG_EINVAL, PG_ENOSPC, PG_ECUDA, PG_ETIMEOUT, PG_ENOMEM = range(6)
@@ -782,7 +783,8 @@ PG_JOB_BA, PG_JOB_KRON = 0, 1
 
 class _PgJob(C.Structure):
     _fields_ = [("kind", u32), ("m", u32), ("n0", u32), ("k", u32), ("n", u64), ("seed", u64),
-                ("initiator", vp)]
+                ("initiator", vp), ("blocks", u32), ("faction_width", u32), ("inter_frac", dbl),
+                ("want_csr", u32), ("reserved", u32)]
 
 
 def _batch_lib():
@@ -790,23 +792,52 @@ def _batch_lib():
     if not getattr(L, "_batch_ready", False):
         L.pg_batch_plan_size.argtypes = [vp, u32]
         L.pg_batch_plan_size.restype = sz
-        L.pg_batch_workspace_size.argtypes = []
+        L.pg_batch_workspace_size.argtypes = [vp]
         L.pg_batch_workspace_size.restype = sz
         L.pg_batch_plan.argtypes = [vp, u32, u32, i32, vp, sz, vp, vp]
         L.pg_batch_plan.restype = i32
-        L.gen_batch.argtypes = [vp, u32, i32, vp, u64, u64, u32, vp, sz, vp]
+        L.gen_batch.argtypes = [vp, vp, u32, i32, vp, u64, u64, u32, vp, sz, vp]
         L.gen_batch.restype = i32
+        L.pg_batch_csr_layout.argtypes = [vp, u32, vp, vp, C.POINTER(u64), C.POINTER(u64)]
+        L.pg_batch_csr_layout.restype = i32
+        L.pg_batch_csr_workspace_size.argtypes = [vp]
+        L.pg_batch_csr_workspace_size.restype = sz
+        L.pg_batch_csr_wait_error_offset.argtypes = [vp]
+        L.pg_batch_csr_wait_error_offset.restype = sz
+        L.gen_batch_csr.argtypes = [vp, vp, u32, i32, vp, vp, u64, vp, u64, vp, sz, vp]
+        L.gen_batch_csr.restype = i32
         L._batch_ready = True
     return L
+
+
+def _job_struct(j, keep):
+    """One pg_job from a job dict (see BatchPlan)."""
+    want = 1 if j.get("want_csr") else 0
+    if j["kind"] == "pba":
+        blocks = int(j.get("blocks", 1) or 1)
+        return _PgJob(PG_JOB_BA, j["m"], j.get("n0") or j["m"] + 1, 0, j["n"], j["seed"], None,
+                      blocks, int(j.get("faction_width", 1) or 1), float(j.get("inter_frac", 0.0)),
+                      want, 0)
+    if j["kind"] == "kron":
+        P = _initiator(j["initiator"])
+        keep.append(P)
+        return _PgJob(PG_JOB_KRON, 0, P.shape[0], j["k"], j["n_edges"], j["seed"],
+                      P.ctypes.data_as(vp), 0, 0, 0.0, want, 0)
+    raise ValueError(f"unknown job kind {j['kind']!r}")
 
 
 class BatchPlan:
     """Host-built plan of a batch of jobs, copied to the device.
 
     ``jobs`` is a list of dicts: ``dict(kind="pba", n=..., m=..., n0=..., seed=...)``
-    (serial BA, i.e. gen_pba with blocks = 1) or ``dict(kind="kron",
-    initiator=..., k=..., n_edges=..., seed=...)`` (stochastic Kronecker).
-    ``offsets[i]`` is job i's first edge in the arena, ``offsets[-1]`` the total.
+    (BA: serial with the default blocks = 1, or two-phase PBA with
+    ``blocks=B, inter_frac=f`` and optionally ``faction_width``), or
+    ``dict(kind="kron", initiator=..., k=..., n_edges=..., seed=...)`` (stochastic
+    Kronecker). ``want_csr=True`` on a job asks gen_batch_csr for its CSR.
+    ``offsets[i]`` is job i's first edge in the arena, ``offsets[-1]`` the arena
+    length, ``counts[i]`` its number of edges (with 32-bit ids one unused arena
+    edge may precede a two-phase job). ``csr_rows[i]`` / ``csr_cols[i]`` are where
+    gen_batch_csr puts job i's row_ptr and col entries (-1: no CSR).
     """
 
     def __init__(self, jobs, tile_edges: int = 4096, id64: bool = False, device="cuda"):
@@ -817,18 +848,7 @@ class BatchPlan:
         arr = (_PgJob * max(n, 1))()
         self._keep = []
         for i, j in enumerate(jobs):
-            if j["kind"] == "pba":
-                if j.get("blocks", 1) != 1:
-                    raise ValueError("batched PBA jobs are serial BA (blocks = 1)")
-                arr[i] = _PgJob(PG_JOB_BA, j["m"], j.get("n0") or j["m"] + 1, 0, j["n"], j["seed"],
-                                None)
-            elif j["kind"] == "kron":
-                P = _initiator(j["initiator"])
-                self._keep.append(P)
-                arr[i] = _PgJob(PG_JOB_KRON, 0, P.shape[0], j["k"], j["n_edges"], j["seed"],
-                                P.ctypes.data_as(vp))
-            else:
-                raise ValueError(f"unknown job kind {j['kind']!r}")
+            arr[i] = _job_struct(j, self._keep)
         size = int(L.pg_batch_plan_size(C.cast(arr, vp), n))
         host = np.zeros(max(size, 16), dtype=np.uint8)
         offsets = np.zeros(n + 1, dtype=np.uint64)
@@ -837,31 +857,115 @@ class BatchPlan:
                              host.ctypes.data_as(vp), host.size, offsets.ctypes.data_as(vp),
                              C.byref(n_items))
         _check("pg_batch_plan", st)
+        rows = np.zeros(max(n, 1), dtype=np.uint64)
+        cols = np.zeros(max(n, 1), dtype=np.uint64)
+        rt, ct = u64(0), u64(0)
+        _check("pg_batch_csr_layout", L.pg_batch_csr_layout(
+            host.ctypes.data_as(vp), n, rows.ctypes.data_as(vp), cols.ctypes.data_as(vp),
+            C.byref(rt), C.byref(ct)))
+        self.jobs = list(jobs)
         self.n_jobs = n
         self.tile_edges = tile_edges
         self.id64 = id64
+        self.host = host
         self.offsets = offsets
+        self.counts = [int(pg_pba_edge_count(j["n"], j["m"], int(j.get("blocks", 1) or 1),
+                                             j.get("n0") or j["m"] + 1))
+                       if j["kind"] == "pba" else int(j["n_edges"]) for j in jobs]
         self.total_edges = int(offsets[-1])
         self.n_items = int(n_items.value)
+        none = np.uint64(0xFFFFFFFFFFFFFFFF)
+        self.csr_rows = [int(r) if r != none else -1 for r in rows[:n]]
+        self.csr_cols = [int(c) if c != none else -1 for c in cols[:n]]
+        self.csr_rows_total = int(rt.value)
+        self.csr_cols_total = int(ct.value)
         self.d_plan = torch.from_numpy(host).to(device)
         self.device = self.d_plan.device
 
+    def edges_of(self, arena, i: int):
+        """Job i's (count, 2) slice of a gen_batch arena."""
+        a = int(self.offsets[i])
+        return arena[a:a + self.counts[i]]
 
-def pg_batch_workspace_size() -> int:
-    return int(_batch_lib().pg_batch_workspace_size())
+    def csr_of(self, row_ptr, col, i: int):
+        """Job i's (row_ptr, col) views into gen_batch_csr's output."""
+        if self.csr_rows[i] < 0:
+            raise ValueError(f"job {i} has no CSR (want_csr not set)")
+        r, c = self.csr_rows[i], self.csr_cols[i]
+        nv = _job_vertices(self.jobs[i])
+        return row_ptr[r:r + nv + 1], col[c:c + self.counts[i]]
+
+
+def _job_vertices(j) -> int:
+    """Vertex ids of a batch job's graph (0 .. count - 1)."""
+    if j["kind"] == "pba":    # a seed clique per block, then the new vertices
+        return int(j.get("blocks", 1) or 1) * (j.get("n0") or j["m"] + 1) + j["n"]
+    return len(j["initiator"]) ** j["k"]
+
+
+def pg_batch_workspace_size(plan: "BatchPlan | None" = None) -> int:
+    """Workspace bytes of gen_batch for `plan` (None: a plan without
+    two-phase jobs)."""
+    return int(_batch_lib().pg_batch_workspace_size(
+        plan.host.ctypes.data_as(vp) if plan is not None else None))
 
 
 def gen_batch(plan: "BatchPlan", arena=None, workspace=None, grid_ctas: int = 0, stream=None):
-    """Run a BatchPlan in one persistent launch; returns the (total, 2) arena."""
+    """Run a BatchPlan: one persistent launch for the serial-BA and Kronecker
+    jobs, then the two-phase PBA jobs; returns the (total, 2) arena."""
     import torch
     L = _batch_lib()
     dtype = torch.int64 if plan.id64 else torch.int32
     if arena is None:
         arena = _empty((max(plan.total_edges, 1), 2), dtype, plan.device)
     if workspace is None:
-        workspace = _empty(pg_batch_workspace_size(), torch.uint8, plan.device)
-    st = L.gen_batch(_ptr(plan.d_plan), plan.n_jobs, PG_ID64 if plan.id64 else PG_ID32,
-                     _ptr(arena), arena.shape[0], plan.total_edges, grid_ctas, _ptr(workspace),
-                     workspace.numel(), _stream(stream))
+        workspace = _empty(pg_batch_workspace_size(plan), torch.uint8, plan.device)
+    st = L.gen_batch(plan.host.ctypes.data_as(vp), _ptr(plan.d_plan), plan.n_jobs,
+                     PG_ID64 if plan.id64 else PG_ID32, _ptr(arena), arena.shape[0],
+                     plan.total_edges, grid_ctas, _ptr(workspace), workspace.numel(),
+                     _stream(stream))
     _check("gen_batch", st)
     return arena[:plan.total_edges]
+
+
+def pg_batch_csr_workspace_size(plan: "BatchPlan") -> int:
+    return int(_batch_lib().pg_batch_csr_workspace_size(plan.host.ctypes.data_as(vp)))
+
+
+def pg_batch_csr_wait_error_offset(plan: "BatchPlan"):
+    """Byte offset of gen_batch_csr's wait word in its workspace, or None."""
+    off = int(_batch_lib().pg_batch_csr_wait_error_offset(plan.host.ctypes.data_as(vp)))
+    return None if off == C.c_size_t(-1).value else off
+
+
+def gen_batch_csr(plan: "BatchPlan", arena, row_ptr=None, col=None, workspace=None, stream=None,
+                  check: bool = False):
+    """CSR of every want_csr job of a gen_batch arena, from one sort of their
+    union graph; returns (row_ptr, col) arenas (plan.csr_of gives a job's
+    views). check=True waits and raises PG_ETIMEOUT if a bounded wait of the
+    sort gave up."""
+    import torch
+    L = _batch_lib()
+    dev = arena.device
+    dtype = torch.int64 if plan.id64 else torch.int32
+    if row_ptr is None:
+        row_ptr = _empty(max(plan.csr_rows_total, 1), torch.int64, dev)
+    if col is None:
+        col = _empty(max(plan.csr_cols_total, 1), dtype, dev)
+    if workspace is None:
+        workspace = _empty(max(pg_batch_csr_workspace_size(plan), 256), torch.uint8, dev)
+    st = L.gen_batch_csr(plan.host.ctypes.data_as(vp), _ptr(plan.d_plan), plan.n_jobs,
+                         PG_ID64 if plan.id64 else PG_ID32, _ptr(arena), _ptr(row_ptr),
+                         row_ptr.numel(), _ptr(col), col.numel(), _ptr(workspace),
+                         workspace.numel(), _stream(stream))
+    _check("gen_batch_csr", st)
+    if check:
+        off = pg_batch_csr_wait_error_offset(plan)
+        if off is not None:
+            if stream is not None:
+                stream.synchronize()
+            else:
+                torch.cuda.current_stream(dev).synchronize()
+            if int(workspace[off:off + 4].view(torch.int32).item()) != 0:
+                raise PgenError("gen_batch_csr", PG_ETIMEOUT)
+    return row_ptr, col

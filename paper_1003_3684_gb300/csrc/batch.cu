@@ -13,6 +13,7 @@
 // + kernel) is stream-ordered and contains no host synchronisation, so it can
 // be captured in a CUDA graph and replayed.
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 
 #include "../../include/pgen.h"
@@ -27,6 +28,11 @@ constexpr uint32_t kBatchWarps = kBatchThreads / 32;
 constexpr uint32_t kMaxTile = 8192;        // staging limit (edges per work item)
 constexpr uint32_t kMaxBatchJobs = 8192;   // first-item table held in smem
 
+// A job's kind in the plan: PG_JOB_BA (serial BA, tiles of the persistent
+// kernel), PG_JOB_KRON, or a two-phase PBA job (blocks > 1), which has no
+// work items: gen_batch runs it with the single-graph PBA kernels.
+constexpr uint32_t kKindTwoPhase = 2;
+
 struct BatchJob {              // 256 bytes, one per job
     uint32_t kind, m, n0, k;
     uint64_t n_units;          // BA: n*m generated edges; KRON: edges
@@ -37,25 +43,50 @@ struct BatchJob {              // 256 bytes, one per job
     uint32_t u_off;            // KRON: offset of u[] in the threshold pool (n0 > 2)
     uint32_t u0, u1, u2, pad;  // KRON n0 = 2 thresholds
     FastDiv32 div_m;
-    uint32_t pad2;
+    uint32_t want_csr;         // 0: no CSR; 1 + g: gen_batch_csr builds it in group g
     Key key;                   // 80 bytes
-    uint8_t reserved[256 - 80 - 88];
+    uint64_t n_vertices;       // ids of the job's graph: 0 .. n_vertices - 1
+    uint64_t vbase;            // want_csr: first row of the job in its group's union graph
+    uint64_t csr_edge;         // want_csr: first col entry of the job (and its union slot)
+    uint64_t rbase;            // want_csr: first row_ptr entry of the job
+    uint64_t edges;            // the job's edges: [out_edge, out_edge + edges) of the arena
+    uint8_t reserved[256 - 80 - 88 - 40];
 };
 static_assert(sizeof(BatchJob) == 256, "job record is 256 bytes");
+
+// A two-phase PBA job's launch geometry, read by the host in gen_batch.
+struct TwoPhaseJob {
+    uint32_t job, pad;
+    uint64_t ws_bytes;         // its PBA workspace
+    PbaGeom g;
+};
 
 struct PlanHeader {
     uint32_t n_jobs, n_pool;
     uint64_t n_items, total_edges;
     uint64_t off_jobs, off_first, off_pool;
-    uint64_t pad;
+    uint64_t off_starts;       // n_jobs + 1 uint64: every job's first edge, then the total
+    uint64_t off_rstart[2];    // per CSR group g: csr_jobs[g] + 1 uint64, each CSR job's
+                               // first row_ptr entry, then the group's end
+    uint64_t off_two;          // n_two TwoPhaseJob records (host only)
+    uint32_t n_two, id64;
+    uint64_t two_ws;           // the largest two-phase job's workspace
+    // The CSR jobs form two groups, each with its own union graph: 0, the BA
+    // jobs (their lists are grouped by source, so their union needs no
+    // sort), and 1, the Kronecker jobs. Group 0's row_ptr and col entries
+    // come first in the output arenas.
+    uint64_t csr_jobs[2], csr_vertices[2], csr_edges[2];
+    uint64_t csr_max_vertices[2];   // the largest job of the group: bounds its col ids
 };
 
 size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-size_t plan_bytes(uint32_t n_jobs, uint32_t n_pool)
+size_t plan_bytes(uint32_t n_jobs, uint32_t n_pool, uint32_t n_two, uint32_t n_csr)
 {
     return a16(sizeof(PlanHeader)) + a16((size_t)n_jobs * sizeof(BatchJob)) +
-           a16((size_t)(n_jobs + 1) * 4) + a16((size_t)n_pool * 4);
+           a16((size_t)(n_jobs + 1) * 4) + a16((size_t)n_pool * 4) +
+           a16((size_t)(n_jobs + 1) * 8) + 2 * a16((size_t)(n_csr + 1) * 8) +
+           a16((size_t)n_two * sizeof(TwoPhaseJob));
 }
 
 // Edge e (and e + 1) of an arena of `cap` edges.
@@ -340,6 +371,85 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const unsigned cha
     }
 }
 
+// Rewrites the edges of every want_csr job into its group's union list of
+// (vbase + src, dst) pairs, at the job's csr_edge: the union graph of the
+// group, whose CSR is its jobs' CSRs one after another (rows of job t are
+// vbase_t .. vbase_t + n_vertices_t - 1, and its col entries keep their
+// local ids). One pair per thread, moved as one vector load and store; lane
+// 0 of a warp finds the job of the warp's first edge by a binary search over
+// the job starts, and each lane steps from there to its own.
+template <typename Id>
+__global__ void __launch_bounds__(256) batch_union_kernel(const unsigned char* __restrict__ plan,
+                                                          const Id* __restrict__ arena,
+                                                          Id* __restrict__ uni)
+{
+    using P = typename std::conditional<sizeof(Id) == 4, uint2, ulonglong2>::type;
+    const PlanHeader& H = *reinterpret_cast<const PlanHeader*>(plan);
+    const BatchJob* jobs = reinterpret_cast<const BatchJob*>(plan + H.off_jobs);
+    const uint64_t* starts = reinterpret_cast<const uint64_t*>(plan + H.off_starts);
+    const uint32_t n_jobs = H.n_jobs;
+    const uint64_t E = H.total_edges;
+    const P* in = reinterpret_cast<const P*>(arena);
+    P* out = reinterpret_cast<P*>(uni);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
+         base += warps * 32) {
+        uint32_t job = 0;
+        if (lane == 0) {
+            uint32_t lo = 0, hi = n_jobs;   // the last job starting at or before base
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (starts[mid] <= base) lo = mid;
+                else hi = mid;
+            }
+            job = lo;
+        }
+        job = __shfl_sync(0xFFFFFFFFu, job, 0);
+        const uint64_t e = base + lane;
+        if (e >= E) continue;
+        while (job + 1 < n_jobs && starts[job + 1] <= e) ++job;
+        const BatchJob& J = jobs[job];
+        const uint64_t local = e - J.out_edge;   // past the job's edges: an alignment gap
+        if (!J.want_csr || local >= J.edges) continue;
+        const uint64_t at = J.csr_edge + local;
+        if (PG_CHECK(at, H.csr_edges[0] + H.csr_edges[1])) {
+            P p = in[e];
+            p.x += (decltype(p.x))J.vbase;
+            out[at] = p;
+        }
+    }
+}
+
+// Row pointers of the CSR jobs of one group from its union's (rp_u,
+// vertices + 1 entries): job t of the group owns output entries rstart[t] ..
+// rstart[t] + n_vertices_t, and entry v there is rp_u[vbase_t + v] -
+// rp_u[vbase_t], with vbase_t = rstart[t] - rstart[0] - t.
+__global__ void __launch_bounds__(256) batch_rebase_kernel(const uint64_t* __restrict__ rstart,
+                                                           uint64_t jobs, uint64_t vertices,
+                                                           const uint64_t* __restrict__ rp_u,
+                                                           uint64_t* __restrict__ out)
+{
+    const uint64_t r0 = rstart[0], R = rstart[jobs] - r0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
+        uint64_t lo = 0, hi = jobs;   // the last job whose entries start at or before r
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (rstart[mid] - r0 <= r) lo = mid;
+            else hi = mid;
+        }
+        const uint64_t vbase = rstart[lo] - r0 - lo;
+        const uint64_t v = vbase + (r - (rstart[lo] - r0));
+        if (PG_CHECK(v, vertices + 1)) out[r0 + r] = rp_u[v] - rp_u[vbase];
+    }
+}
+
+__global__ void or_word_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src)
+{
+    *dst |= *src;
+}
+
 }  // namespace
 
 PG_CHECK_UNIT(batch)
@@ -374,13 +484,24 @@ extern "C" {
 size_t pg_batch_plan_size(const pg_job* jobs, uint32_t n_jobs)
 {
     uint64_t pool = 0;
-    for (uint32_t i = 0; jobs && i < n_jobs; ++i)
+    uint32_t two = 0, csr = 0;
+    for (uint32_t i = 0; jobs && i < n_jobs; ++i) {
         if (jobs[i].kind == PG_JOB_KRON && jobs[i].n0 > 2 && jobs[i].n0 <= 16)
             pool += (uint64_t)jobs[i].n0 * jobs[i].n0;
-    return plan_bytes(n_jobs, (uint32_t)pool);
+        if (jobs[i].kind == PG_JOB_BA && jobs[i].blocks > 1) ++two;
+        if (jobs[i].want_csr) ++csr;
+    }
+    return plan_bytes(n_jobs, (uint32_t)pool, two, csr);
 }
 
-size_t pg_batch_workspace_size(void) { return 256; }
+size_t pg_batch_workspace_size(const void* h_plan)
+{
+    // the persistent kernel's work counter, then the two-phase jobs' PBA
+    // workspace (they run one after another, so one region serves all)
+    if (!h_plan) return 256;
+    const PlanHeader& H = *(const PlanHeader*)h_plan;
+    return 256 + (H.n_two ? ((H.two_ws + 255) & ~(uint64_t)255) : 0);
+}
 
 pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges, pg_idwidth w,
                         void* h_plan, size_t plan_size, uint64_t* h_edge_offsets,
@@ -391,15 +512,31 @@ pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges
     if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
     if (plan_size < pg_batch_plan_size(jobs, n_jobs)) return PG_ENOMEM;
     std::memset(h_plan, 0, plan_size);
+    uint32_t n_two = 0, n_csr = 0;
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        if (jobs[i].kind == PG_JOB_BA && jobs[i].blocks > 1) ++n_two;
+        if (jobs[i].want_csr) ++n_csr;
+    }
     unsigned char* base = (unsigned char*)h_plan;
     PlanHeader& H = *(PlanHeader*)base;
     H.n_jobs = n_jobs;
+    H.id64 = w == PG_ID64;
     H.off_jobs = a16(sizeof(PlanHeader));
     H.off_first = H.off_jobs + a16((size_t)n_jobs * sizeof(BatchJob));
     H.off_pool = H.off_first + a16((size_t)(n_jobs + 1) * 4);
     BatchJob* J = (BatchJob*)(base + H.off_jobs);
     uint32_t* first = (uint32_t*)(base + H.off_first);
     uint32_t* pool = (uint32_t*)(base + H.off_pool);
+    uint32_t pool_entries = 0;
+    for (uint32_t i = 0; i < n_jobs; ++i)
+        if (jobs[i].kind == PG_JOB_KRON && jobs[i].n0 > 2 && jobs[i].n0 <= 16)
+            pool_entries += jobs[i].n0 * jobs[i].n0;
+    H.off_starts = H.off_pool + a16((size_t)pool_entries * 4);
+    H.off_rstart[0] = H.off_starts + a16((size_t)(n_jobs + 1) * 8);
+    H.off_rstart[1] = H.off_rstart[0] + a16((size_t)(n_csr + 1) * 8);
+    H.off_two = H.off_rstart[1] + a16((size_t)(n_csr + 1) * 8);
+    uint64_t* starts = (uint64_t*)(base + H.off_starts);
+    TwoPhaseJob* two = (TwoPhaseJob*)(base + H.off_two);
     uint64_t edges = 0, items = 0;
     uint32_t n_pool = 0;
     const uint64_t id_limit = w == PG_ID32 ? ((uint64_t)1 << 32) : ~(uint64_t)0;
@@ -409,8 +546,26 @@ pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges
         b.kind = q.kind;
         b.tile = tile_edges;
         b.key = make_key(q.seed);
-        b.out_edge = edges;
-        if (q.kind == PG_JOB_BA) {
+        uint64_t job_items = 0;
+        if (q.kind == PG_JOB_BA && q.blocks > 1) {
+            // two-phase PBA: the single-graph kernels write it, from an even
+            // edge so that their 16-byte stores stay aligned
+            TwoPhaseJob& tp = two[H.n_two];
+            uint64_t ne = 0;
+            const int st = pba_setup(q.n, q.m, q.blocks, q.n0, q.faction_width ? q.faction_width : 1,
+                                     q.inter_frac, q.seed, w == PG_ID64, &tp.g, &ne);
+            if (st != PG_OK) return (pg_status)st;
+            if (w == PG_ID32) edges += edges & 1;
+            tp.job = i;
+            tp.ws_bytes = pba_workspace_layout(tp.g.A_stride, tp.g.B, tp.g.S).total;
+            if (tp.ws_bytes > H.two_ws) H.two_ws = tp.ws_bytes;
+            ++H.n_two;
+            b.kind = kKindTwoPhase;
+            b.m = q.m;
+            b.n0 = q.n0;
+            b.edges = ne;
+            b.n_vertices = (uint64_t)tp.g.B * tp.g.span;
+        } else if (q.kind == PG_JOB_BA) {
             if (q.m < 1 || q.n0 < 2 || q.n0 > 65536) return PG_EINVAL;
             const unsigned __int128 ne = (unsigned __int128)q.n * q.m;
             b.e0 = (uint64_t)q.n0 * (q.n0 - 1) / 2;
@@ -420,7 +575,10 @@ pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges
             b.n0 = q.n0;
             b.n_units = (uint64_t)ne;
             b.div_m = make_fastdiv32(q.m);
-            edges += b.e0 + b.n_units;
+            b.edges = b.e0 + b.n_units;
+            b.n_vertices = (uint64_t)q.n0 + q.n;
+            job_items = (b.n_units + tile_edges - 1) / tile_edges;
+            if (job_items == 0) job_items = 1;   // its seed clique
         } else if (q.kind == PG_JOB_KRON) {
             if (!q.initiator || q.n0 < 1 || q.n0 > 16 || q.k < 1 || q.k > 64) return PG_EINVAL;
             unsigned __int128 nv = 1;
@@ -447,18 +605,51 @@ pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges
                 b.u_off = n_pool;
                 for (uint32_t t = 0; t < nu; ++t) pool[n_pool++] = u[t];
             }
-            edges += b.n_units;
+            b.edges = b.n_units;
+            b.n_vertices = (uint64_t)nv;
+            job_items = (b.n_units + tile_edges - 1) / tile_edges;
         } else {
             return PG_EINVAL;
         }
+        b.out_edge = edges;
+        starts[i] = edges;
+        edges += b.edges;
+        if (q.want_csr) b.want_csr = 1 + (q.kind == PG_JOB_KRON ? 1u : 0u);
         first[i] = (uint32_t)items;
-        uint64_t job_items = (b.n_units + tile_edges - 1) / tile_edges;
-        if (job_items == 0 && q.kind == PG_JOB_BA) job_items = 1;   // its seed clique
         items += job_items;
         if (items >= 0xFFFFFFFFull) return PG_EINVAL;
         if (h_edge_offsets) h_edge_offsets[i] = b.out_edge;
     }
     first[n_jobs] = (uint32_t)items;
+    starts[n_jobs] = edges;
+    // the CSR groups: each job's rows in its group's union graph, then its
+    // places in the output arenas (group 0's jobs first, in job order)
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        if (!J[i].want_csr) continue;
+        const uint32_t g = J[i].want_csr - 1;
+        J[i].vbase = H.csr_vertices[g];
+        H.csr_vertices[g] += J[i].n_vertices;
+        H.csr_edges[g] += J[i].edges;
+        ++H.csr_jobs[g];
+        if (J[i].n_vertices > H.csr_max_vertices[g]) H.csr_max_vertices[g] = J[i].n_vertices;
+        if (H.csr_vertices[g] > id_limit || H.csr_vertices[g] >= ((uint64_t)1 << 62))
+            return PG_EINVAL;   // the union's row ids must fit the id width
+    }
+    const uint64_t row_base[2] = {0, H.csr_vertices[0] + H.csr_jobs[0]};
+    const uint64_t col_base[2] = {0, H.csr_edges[0]};
+    uint64_t t_g[2] = {0, 0}, e_g[2] = {0, 0};
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        if (!J[i].want_csr) continue;
+        const uint32_t g = J[i].want_csr - 1;
+        uint64_t* rstart = (uint64_t*)(base + H.off_rstart[g]);
+        J[i].csr_edge = col_base[g] + e_g[g];
+        J[i].rbase = row_base[g] + J[i].vbase + t_g[g];
+        rstart[t_g[g]++] = J[i].rbase;
+        e_g[g] += J[i].edges;
+    }
+    for (uint32_t g = 0; g < 2; ++g)
+        ((uint64_t*)(base + H.off_rstart[g]))[H.csr_jobs[g]] =
+            row_base[g] + H.csr_vertices[g] + H.csr_jobs[g];
     H.n_items = items;
     H.total_edges = edges;
     H.n_pool = n_pool;
@@ -467,15 +658,29 @@ pg_status pg_batch_plan(const pg_job* jobs, uint32_t n_jobs, uint32_t tile_edges
     return PG_OK;
 }
 
-pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_arena,
-                    uint64_t cap_edges, uint64_t total_edges, uint32_t grid_ctas, void* d_ws,
-                    size_t ws_bytes, void* stream)
+namespace {
+// The host plan's header, if it describes a plan of n_jobs jobs of width w.
+const PlanHeader* plan_header(const void* h_plan, uint32_t n_jobs, pg_idwidth w)
+{
+    if (!h_plan) return nullptr;
+    const PlanHeader* H = (const PlanHeader*)h_plan;
+    if (H->n_jobs != n_jobs || H->id64 != (w == PG_ID64 ? 1u : 0u)) return nullptr;
+    return H;
+}
+}  // namespace
+
+pg_status gen_batch(const void* h_plan, const void* d_plan, uint32_t n_jobs, pg_idwidth w,
+                    void* d_arena, uint64_t cap_edges, uint64_t total_edges, uint32_t grid_ctas,
+                    void* d_ws, size_t ws_bytes, void* stream)
 {
     if (!d_plan || n_jobs == 0 || n_jobs > kMaxBatchJobs) return PG_EINVAL;
     if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    const PlanHeader* HP = plan_header(h_plan, n_jobs, w);
+    if (!HP || HP->total_edges != total_edges) return PG_EINVAL;
     if (cap_edges < total_edges) return PG_ENOSPC;
     if (total_edges > 0 && (!d_arena || ((uintptr_t)d_arena & 15))) return PG_EINVAL;
-    if (!d_ws || ws_bytes < pg_batch_workspace_size() || ((uintptr_t)d_ws & 255)) return PG_ENOMEM;
+    if (!d_ws || ws_bytes < pg_batch_workspace_size(h_plan) || ((uintptr_t)d_ws & 255))
+        return PG_ENOMEM;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t id_bytes = w == PG_ID64 ? 8 : 4;
     const size_t smem = kMaxTile * id_bytes + (size_t)(n_jobs + 1) * 4;
@@ -489,25 +694,160 @@ pg_status gen_batch(const void* d_plan, uint32_t n_jobs, pg_idwidth w, void* d_a
                                  (int)(kMaxTile * 8 + (kMaxBatchJobs + 1) * 4))});
     });
     if (ae != cudaSuccess) return PG_ECUDA;
-    int per_sm = 0;
-    if (w == PG_ID64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint64_t>, kBatchThreads, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint32_t>, kBatchThreads, smem);
-    if (per_sm < 1) per_sm = 1;
-    const uint32_t full = (uint32_t)(device_sm_count() * per_sm);
-    const uint32_t grid = grid_ctas == 0 || grid_ctas > full ? full : grid_ctas;
-    if (cudaMemsetAsync(d_ws, 0, 8, s) != cudaSuccess) return PG_ECUDA;
-    TraceScope trace("batch_persistent", s);
-    if (w == PG_ID64)
-        batch_kernel<uint64_t><<<grid, kBatchThreads, smem, s>>>(
-            (const unsigned char*)d_plan, (uint64_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
-            n_jobs);
-    else
-        batch_kernel<uint32_t><<<grid, kBatchThreads, smem, s>>>(
-            (const unsigned char*)d_plan, (uint32_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
-            n_jobs);
-    return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
+    if (HP->n_items > 0) {
+        int per_sm = 0;
+        if (w == PG_ID64)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint64_t>, kBatchThreads, smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<uint32_t>, kBatchThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+        const uint32_t full = (uint32_t)(device_sm_count() * per_sm);
+        const uint32_t grid = grid_ctas == 0 || grid_ctas > full ? full : grid_ctas;
+        if (cudaMemsetAsync(d_ws, 0, 8, s) != cudaSuccess) return PG_ECUDA;
+        TraceScope trace("batch_persistent", s);
+        if (w == PG_ID64)
+            batch_kernel<uint64_t><<<grid, kBatchThreads, smem, s>>>(
+                (const unsigned char*)d_plan, (uint64_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
+                n_jobs);
+        else
+            batch_kernel<uint32_t><<<grid, kBatchThreads, smem, s>>>(
+                (const unsigned char*)d_plan, (uint32_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
+                n_jobs);
+        if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
+    }
+    // two-phase PBA jobs: phase 1, the count exchange and the emission of
+    // each, in the shared workspace region after the counter
+    const TwoPhaseJob* two = (const TwoPhaseJob*)((const unsigned char*)h_plan + HP->off_two);
+    const BatchJob* J = (const BatchJob*)((const unsigned char*)h_plan + HP->off_jobs);
+    for (uint32_t t = 0; t < HP->n_two; ++t) {
+        const uint64_t at = J[two[t].job].out_edge;
+        if (launch_pba(two[t].g, w == PG_ID64, (unsigned char*)d_arena + at * 2 * id_bytes,
+                       (unsigned char*)d_ws + 256, s) != cudaSuccess)
+            return PG_ECUDA;
+    }
+    return PG_OK;
+}
+
+pg_status pg_batch_csr_layout(const void* h_plan, uint32_t n_jobs, uint64_t* h_row_offsets,
+                              uint64_t* h_col_offsets, uint64_t* rows_total, uint64_t* cols_total)
+{
+    if (!h_plan || ((const PlanHeader*)h_plan)->n_jobs != n_jobs) return PG_EINVAL;
+    const PlanHeader& H = *(const PlanHeader*)h_plan;
+    const BatchJob* J = (const BatchJob*)((const unsigned char*)h_plan + H.off_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        if (h_row_offsets) h_row_offsets[i] = J[i].want_csr ? J[i].rbase : UINT64_MAX;
+        if (h_col_offsets) h_col_offsets[i] = J[i].want_csr ? J[i].csr_edge : UINT64_MAX;
+    }
+    if (rows_total)
+        *rows_total = H.csr_vertices[0] + H.csr_jobs[0] + H.csr_vertices[1] + H.csr_jobs[1];
+    if (cols_total) *cols_total = H.csr_edges[0] + H.csr_edges[1];
+    return PG_OK;
+}
+
+namespace {
+// gen_batch_csr's workspace: the union lists of both groups, each group's
+// union row pointers, the call's wait word, then one CSR workspace that the
+// two groups' CSR calls use in turn.
+struct BatchCsrLayout {
+    size_t off_rp[2], off_wait, off_csr, total;
+};
+BatchCsrLayout batch_csr_layout(const PlanHeader& H)
+{
+    BatchCsrLayout L;
+    const size_t pair = H.id64 ? 16 : 8;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = up((size_t)(H.csr_edges[0] + H.csr_edges[1]) * pair);
+    size_t ws = 0;
+    for (int g = 0; g < 2; ++g) {
+        L.off_rp[g] = o;
+        o += up(((size_t)H.csr_vertices[g] + 1) * 8);
+        if (H.csr_jobs[g]) {
+            const size_t w = csr_workspace_bytes(H.csr_edges[g], H.csr_vertices[g],
+                                                 H.csr_max_vertices[g]);
+            ws = w > ws ? w : ws;
+        }
+    }
+    L.off_wait = o;
+    o += 256;
+    L.off_csr = o;
+    L.total = o + ws;
+    return L;
+}
+bool csr_jobs_any(const PlanHeader& H) { return H.csr_jobs[0] + H.csr_jobs[1] > 0; }
+}  // namespace
+
+size_t pg_batch_csr_workspace_size(const void* h_plan)
+{
+    if (!h_plan) return 0;
+    const PlanHeader& H = *(const PlanHeader*)h_plan;
+    return csr_jobs_any(H) ? batch_csr_layout(H).total : 0;
+}
+
+size_t pg_batch_csr_wait_error_offset(const void* h_plan)
+{
+    if (!h_plan) return SIZE_MAX;
+    const PlanHeader& H = *(const PlanHeader*)h_plan;
+    return csr_jobs_any(H) ? batch_csr_layout(H).off_wait : SIZE_MAX;
+}
+
+pg_status gen_batch_csr(const void* h_plan, const void* d_plan, uint32_t n_jobs, pg_idwidth w,
+                        const void* d_arena, uint64_t* d_row_ptr, uint64_t cap_row_ptr,
+                        void* d_col, uint64_t cap_col, void* d_ws, size_t ws_bytes, void* stream)
+{
+    if (!d_plan || n_jobs == 0 || n_jobs > kMaxBatchJobs) return PG_EINVAL;
+    if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    const PlanHeader* HP = plan_header(h_plan, n_jobs, w);
+    if (!HP) return PG_EINVAL;
+    const PlanHeader& H = *HP;
+    if (!csr_jobs_any(H)) return PG_OK;
+    uint64_t rows = 0, cols = 0;
+    pg_batch_csr_layout(h_plan, n_jobs, nullptr, nullptr, &rows, &cols);
+    if (cap_row_ptr < rows || cap_col < cols) return PG_ENOSPC;
+    if (!d_row_ptr || ((uintptr_t)d_row_ptr & 7)) return PG_EINVAL;
+    if (cols > 0 && (!d_arena || !d_col || ((uintptr_t)d_arena & 15))) return PG_EINVAL;
+    const BatchCsrLayout L = batch_csr_layout(H);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return PG_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* ws = (unsigned char*)d_ws;
+    const size_t pair = H.id64 ? 16 : 8, id_bytes = pair / 2;
+    uint32_t* wait = (uint32_t*)(ws + L.off_wait);
+    if (cudaMemsetAsync(wait, 0, 4, s) != cudaSuccess) return PG_ECUDA;
+    if (cols > 0) {
+        TraceScope trace("batch_csr_union", s);
+        const uint64_t warps = (H.total_edges + 31) / 32;
+        const uint64_t full = (uint64_t)device_sm_count() * 8;
+        const int grid = (int)(warps / 8 + 1 < full ? warps / 8 + 1 : full);
+        if (w == PG_ID64)
+            batch_union_kernel<uint64_t><<<grid, 256, 0, s>>>(
+                (const unsigned char*)d_plan, (const uint64_t*)d_arena, (uint64_t*)ws);
+        else
+            batch_union_kernel<uint32_t><<<grid, 256, 0, s>>>(
+                (const unsigned char*)d_plan, (const uint32_t*)d_arena, (uint32_t*)ws);
+        if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
+    }
+    const uint64_t col_base[2] = {0, H.csr_edges[0]};
+    for (int g = 0; g < 2; ++g) {
+        if (!H.csr_jobs[g]) continue;
+        const uint64_t E = H.csr_edges[g], V = H.csr_vertices[g], nd = H.csr_max_vertices[g];
+        uint64_t* rp_u = (uint64_t*)(ws + L.off_rp[g]);
+        if (launch_csr(ws + col_base[g] * pair, E, V, (int)H.id64, rp_u,
+                       (unsigned char*)d_col + col_base[g] * id_bytes, ws + L.off_csr,
+                       L.total - L.off_csr, s, nd) != cudaSuccess)
+            return PG_ECUDA;
+        if (E > 0 && V >= 2)   // the group's sort had a wait word: fold it into the call's
+            or_word_kernel<<<1, 1, 0, s>>>(
+                wait, (const uint32_t*)(ws + L.off_csr + csr_wait_error_offset(E, V, 0, (int)H.id64,
+                                                                               nd)));
+        TraceScope trace("batch_csr_rebase", s);
+        const uint64_t R = V + H.csr_jobs[g];
+        const uint64_t full = (uint64_t)device_sm_count() * 8;
+        const int grid = (int)(R / 256 + 1 < full ? R / 256 + 1 : full);
+        batch_rebase_kernel<<<grid, 256, 0, s>>>(
+            (const uint64_t*)((const unsigned char*)d_plan + H.off_rstart[g]), H.csr_jobs[g], V,
+            rp_u, d_row_ptr);
+        if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
+    }
+    return PG_OK;
 }
 
 }  // extern "C"

@@ -740,12 +740,38 @@ struct CsrLayout {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes)
+// The LSD passes that sort pairs by (src, dst): the digits of dst (the bits
+// of n_dst - 1), then those of src (the bits of n_src - 1), each field cut
+// into equal digits of at most kMaxDigitBits.
+PassList make_passes(uint64_t n_src, uint64_t n_dst)
+{
+    PassList pl;
+    std::memset(&pl, 0, sizeof(pl));
+    for (int field = 0; field < 2; ++field) {
+        const uint64_t n = field ? n_src : n_dst;
+        const int bits = bit_length(n > 0 ? n - 1 : 0);
+        const int per_field = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+        const int width = per_field ? (bits + per_field - 1) / per_field : 0;
+        int shift = 0;
+        for (int ps = 0; ps < per_field; ++ps) {
+            const int b = bits - shift < width ? bits - shift : width;
+            if (b <= 0) break;
+            pl.field[pl.n] = field;
+            pl.shift[pl.n] = shift;
+            pl.bits[pl.n] = b;
+            ++pl.n;
+            shift += b;
+        }
+    }
+    return pl;
+}
+
+CsrLayout csr_layout(uint64_t M, uint64_t N, size_t pair_bytes, uint64_t N_dst = 0)
 {
     CsrLayout L;
-    const int bits = bit_length(N > 0 ? N - 1 : 0);
-    const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
-    const int dbits = passes ? (bits + passes - 1) / passes : 0;
+    const PassList pl = make_passes(N, N_dst ? N_dst : N);
+    int dbits = 0;
+    for (uint32_t k = 0; k < pl.n; ++k) dbits = pl.bits[k] > dbits ? pl.bits[k] : dbits;
     const uint32_t tile = pair_bytes == 8 ? SortShape<uint32_t>::tile : SortShape<uint64_t>::tile;
     L.max_nb = 1u << dbits;
     L.n_tiles = (uint32_t)((M + tile - 1) / tile);
@@ -791,9 +817,10 @@ cudaError_t set_csr_attributes()
 int sort_grid(uint64_t work);
 
 template <typename Id>
-cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t N, const CsrLayout& L,
-                         unsigned char* ws, const uint32_t* sort_needed, cudaStream_t s,
-                         const typename PairOf<Id>::T** sorted, typename PairOf<Id>::T** spare)
+cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t N, uint64_t N_dst,
+                         const CsrLayout& L, unsigned char* ws, const uint32_t* sort_needed,
+                         cudaStream_t s, const typename PairOf<Id>::T** sorted,
+                         typename PairOf<Id>::T** spare)
 {
     using P = typename PairOf<Id>::T;
     P* buf[2] = {(P*)(ws + L.off_a), (P*)(ws + L.off_b)};
@@ -803,24 +830,7 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
     uint32_t* tickets = (uint32_t*)(ws + L.off_flag + 64);
     uint32_t* err = (uint32_t*)(ws + L.off_flag + 128);
     // the passes: dst digits, then src digits, at most kMaxDigitBits each
-    const int bits = bit_length(N > 0 ? N - 1 : 0);
-    const int per_field = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
-    PassList pl;
-    std::memset(&pl, 0, sizeof(pl));
-    for (int field = 0; field < 2; ++field) {
-        int shift = 0;
-        for (int ps = 0; ps < per_field; ++ps) {
-            const int b = (bits - shift < (bits + per_field - 1) / per_field)
-                              ? bits - shift
-                              : (bits + per_field - 1) / per_field;
-            if (b <= 0) break;
-            pl.field[pl.n] = field;
-            pl.shift[pl.n] = shift;
-            pl.bits[pl.n] = b;
-            ++pl.n;
-            shift += b;
-        }
-    }
+    const PassList pl = make_passes(N, N_dst);
     const P* cur = in;
     int which = 0;
     cudaError_t err_c;
@@ -879,11 +889,11 @@ int sort_grid(uint64_t work)
 }
 
 template <typename Id>
-cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_row_ptr, void* d_col,
-                     void* d_ws, cudaStream_t s)
+cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t N_dst,
+                     uint64_t* d_row_ptr, void* d_col, void* d_ws, cudaStream_t s)
 {
     using P = typename PairOf<Id>::T;
-    const CsrLayout L = csr_layout(M, N, sizeof(P));
+    const CsrLayout L = csr_layout(M, N, sizeof(P), N_dst);
     cudaError_t err;
     if ((err = set_csr_attributes<Id>()) != cudaSuccess) return err;
     unsigned char* ws = (unsigned char*)d_ws;
@@ -900,8 +910,8 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t* d_ro
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const P* cur;
     P* spare;
-    if ((err = radix_passes<Id>((const P*)d_edges, M, N, L, ws, sort_needed, s, &cur, &spare)) !=
-        cudaSuccess)
+    if ((err = radix_passes<Id>((const P*)d_edges, M, N, N_dst, L, ws, sort_needed, s, &cur,
+                                &spare)) != cudaSuccess)
         return err;
     TraceScope trace("csr_finish", s);
     csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed);
@@ -955,7 +965,8 @@ cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t 
     }
     const P* cur;
     P* spare;
-    if ((err = radix_passes<Id>(in, M2, N, O.L, ws, sort_needed, s, &cur, &spare)) != cudaSuccess)
+    if ((err = radix_passes<Id>(in, M2, N, N, O.L, ws, sort_needed, s, &cur, &spare)) !=
+        cudaSuccess)
         return err;
     TraceScope trace("csr_compact", s);
     if (M2 > 0) {
@@ -984,11 +995,11 @@ void set_csr_wait_hook(uint32_t spin_limit, uint32_t withhold_tile)
     g_hook_withhold.store(withhold_tile);
 }
 
-size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices)
+size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint64_t n_dst)
 {
     // one size that fits either id width
-    const size_t a = csr_layout(n_edges, n_vertices, 16).total;
-    const size_t b = csr_layout(n_edges, n_vertices, 8).total;
+    const size_t a = csr_layout(n_edges, n_vertices, 16, n_dst).total;
+    const size_t b = csr_layout(n_edges, n_vertices, 8, n_dst).total;
     return a > b ? a : b;
 }
 
@@ -1001,11 +1012,12 @@ size_t csr_opts_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint32_t 
 
 // Byte offset of the look-back error word in the workspace of a call with
 // these arguments (the layout the call itself uses).
-size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64)
+size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64,
+                             uint64_t n_dst)
 {
     const size_t pair_bytes = id64 ? 16 : 8;
     const CsrLayout L = flags ? opts_layout(n_edges, n_vertices, flags, pair_bytes).L
-                              : csr_layout(n_edges, n_vertices, pair_bytes);
+                              : csr_layout(n_edges, n_vertices, pair_bytes, n_dst);
     return L.off_flag + 128;
 }
 
@@ -1021,11 +1033,12 @@ cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_ve
 
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                        uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,
-                       cudaStream_t s)
+                       cudaStream_t s, uint64_t n_dst)
 {
     (void)ws_bytes;
-    return id64 ? csr_impl<uint64_t>(d_edges, n_edges, n_vertices, d_row_ptr, d_col, d_ws, s)
-                : csr_impl<uint32_t>(d_edges, n_edges, n_vertices, d_row_ptr, d_col, d_ws, s);
+    const uint64_t nd = n_dst ? n_dst : n_vertices;
+    return id64 ? csr_impl<uint64_t>(d_edges, n_edges, n_vertices, nd, d_row_ptr, d_col, d_ws, s)
+                : csr_impl<uint32_t>(d_edges, n_edges, n_vertices, nd, d_row_ptr, d_col, d_ws, s);
 }
 
 }  // namespace pgen

@@ -148,12 +148,17 @@ size_t csr_opts_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint32_t 
 cudaError_t launch_csr_opts(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                             uint32_t flags, uint64_t* d_row_ptr, void* d_col, void* d_ws,
                             cudaStream_t s);
-size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices);
-size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64);
+// n_dst (0: n_vertices) bounds the destination ids: the sort orders them on
+// the bits of n_dst - 1 only (a CSR whose rows hold local ids of smaller
+// graphs, as the batch CSR's union). The workspace and wait-word offset of
+// a call depend on it.
+size_t csr_workspace_bytes(uint64_t n_edges, uint64_t n_vertices, uint64_t n_dst = 0);
+size_t csr_wait_error_offset(uint64_t n_edges, uint64_t n_vertices, uint32_t flags, int id64,
+                             uint64_t n_dst = 0);
 void set_csr_wait_hook(uint32_t spin_limit, uint32_t withhold_tile);
 cudaError_t launch_csr(const void* d_edges, uint64_t n_edges, uint64_t n_vertices, int id64,
                        uint64_t* d_row_ptr, void* d_col, void* d_ws, size_t ws_bytes,
-                       cudaStream_t s);
+                       cudaStream_t s, uint64_t n_dst = 0);
 
 int device_sm_count();
 

@@ -8,21 +8,26 @@ memory. At every scheduling step it
   2. drops waiting requests whose deadline has passed, then admits waiting
      requests, in arrival order, while their bytes fit the remaining budget,
   3. launches the admitted requests as one batch on a free stream: one
-     persistent generation launch for all of them (gen_batch), then each
-     request's CSR (edges_to_csr) on the same stream, then an event.
+     persistent generation launch for all of them (gen_batch), then on the
+     same stream the CSRs -- of the small requests from one sort of their
+     union graph (gen_batch_csr), of each large one by its own call
+     (edges_to_csr), where the launches cost nothing next to the sort --
+     then an event.
 Batches on different streams overlap on the GPU, so requests that arrive
 while others are running are admitted and started as soon as a stream and
 memory free up -- continuous batching rather than a queue drained in rounds.
 Results stay on the device until the client releases them.
 
-A request's bytes are its edge list, its CSR and the CSR call's workspace;
-the edge list and the workspace are given back when its batch retires, the
-CSR when the client releases it. A request can be cancelled at any time (a
-running one still finishes on the device, and its results are dropped when
-its batch retires) and can carry a deadline, the latest time it may start:
-a request still waiting at its deadline expires without running. Each CSR
-call's bounded-wait status is copied to pinned host memory on the batch's
-stream; a request whose sort gave up waiting is reported failed, not done.
+A request's bytes are its edge list, its CSR and its share of the batch
+CSR's workspace; the edge list and the workspace are given back when its
+batch retires. The CSRs of a batch share one allocation, so a request's CSR
+bytes are given back when the last request of its batch is released. A
+request can be cancelled at any time (a running one still finishes on the
+device, and its results are dropped when its batch retires) and can carry a
+deadline, the latest time it may start: a request still waiting at its
+deadline expires without running. The batch CSR's bounded-wait status is
+copied to pinned host memory on the batch's stream; if its sort gave up
+waiting, the batch's requests are reported failed, not done.
 
 The server never synchronises the device except through event queries; the
 only host work per request is planning and launching.
@@ -67,10 +72,12 @@ def job_csr_bytes(job) -> int:
 
 def job_transient_bytes(job) -> int:
     """Device bytes a request needs only until its batch retires: the edge
-    list (8 B/edge) and the workspace of its CSR call."""
+    list (8 B/edge), and its share of the batch CSR's workspace: the sort's
+    workspace for its edges, its edges again in the union list (8 B/edge) and
+    its rows in the union's row pointers (8 B/vertex)."""
     import paper_1003_3684_gb300 as pg
-    E = job_edges(job)
-    return E * 8 + pg.pg_csr_workspace_size(E, job_vertices(job))
+    E, N = job_edges(job), job_vertices(job)
+    return E * 8 + pg.pg_csr_workspace_size(E, N) + E * 8 + (N + 1) * 8
 
 
 def job_bytes(job) -> int:
@@ -93,10 +100,19 @@ class Request:
     row_ptr: object = None
     col: object = None
     held: int = 0          # budget bytes this request holds right now
+    csr_share: object = None   # the batch's shared CSR allocation, while results are held
 
     @property
     def latency(self):
         return None if self.done is None else self.done - self.arrival
+
+
+@dataclass
+class _CsrShare:
+    """The CSR allocation shared by a batch's requests: the budget bytes of
+    released requests stay counted until the last one is released."""
+    live: int
+    parked: int = 0
 
 
 @dataclass
@@ -105,16 +121,21 @@ class _Batch:
     stream: object
     event: object
     keep: list = field(default_factory=list)
-    status: object = None   # per request: the CSR call's wait word (pinned host memory)
+    status: object = None   # per request: its own CSR call's wait word (pinned host memory)
+    batch_status: object = None   # the batch CSR's wait word, for the requests it built
 
 
 class Server:
     def __init__(self, budget_bytes: int = 64 << 30, n_streams: int = 2, max_batch_jobs: int = 256,
                  max_batch_edges: int = 1 << 28, tile_edges: int = 4096, device="cuda",
-                 clock=time.perf_counter, per_graph: bool = False):
+                 clock=time.perf_counter, per_graph: bool = False,
+                 batch_csr_edges: int = 1 << 17):
         """per_graph=True replaces the batched launch by one gen_pba /
-        gen_kronecker call per request (the baseline a batching server beats)."""
+        gen_kronecker call per request (the baseline a batching server beats).
+        Requests with fewer than batch_csr_edges edges get their CSR from the
+        batch's one sort; larger ones from a call of their own."""
         self.per_graph = per_graph
+        self.batch_csr_edges = batch_csr_edges
         self.budget = budget_bytes
         self.in_use = 0
         self.peak_in_use = 0
@@ -180,9 +201,19 @@ class Server:
         return True
 
     def release(self, r: Request):
-        """Client is done with a result: free its device memory and budget."""
+        """Client is done with a result: free its device memory and budget
+        (a batch's CSR bytes come back when its last request is released)."""
         r.row_ptr = r.col = None
-        self._give_back(r, r.held)
+        share, r.csr_share = r.csr_share, None
+        if share is None:
+            self._give_back(r, r.held)
+            return
+        share.parked += r.held      # still allocated in the shared CSR arenas
+        r.held = 0
+        share.live -= 1
+        if share.live == 0:
+            self.in_use -= share.parked
+            share.parked = 0
 
     def pending(self) -> int:
         return len(self.waiting) + len(self.admitted) + sum(b is not None for b in self.busy.values())
@@ -203,7 +234,10 @@ class Server:
                     self.release(r)
                     continue
                 r.done = now
-                if b.status is not None and int(b.status[k]) != 0:
+                own = b.status is not None and int(b.status[k]) != 0
+                shared = (r.csr_share is not None and b.batch_status is not None and
+                          int(b.batch_status[0]) != 0)
+                if own or shared:
                     r.state, r.error = "failed", "CSR sort: a bounded wait gave up (PG_ETIMEOUT)"
                     self.release(r)
                     self.failed.append(r)
@@ -267,35 +301,29 @@ class Server:
                 self._fail(batch, f"launch failed: {exc}")
 
     def _start(self, i, batch, now) -> _Batch:
-        """Queue one batch on stream i: generation, then a CSR per request."""
+        """Queue one batch on stream i."""
+        if self.per_graph:
+            return self._start_per_graph(i, batch, now)
+        return self._start_batched(i, batch, now)
+
+    def _start_per_graph(self, i, batch, now) -> _Batch:
+        """The per-graph baseline: a generation call and a CSR call per request."""
         torch, pg = self.torch, self.pg
         s = self.streams[i]
         with torch.cuda.stream(s):
-            if self.per_graph:
-                offs = np.cumsum([0] + [job_edges(r.job) + (job_edges(r.job) & 1)
-                                        for r in batch])
-                arena = pg.empty_device((max(int(offs[-1]), 1), 2), torch.int32,
-                                        self.device)
-                for k, r in enumerate(batch):
-                    j, a = r.job, int(offs[k])
-                    sl = arena[a:a + job_edges(j)]
-                    if j["kind"] == "pba":
-                        pg.gen_pba(j["n"], j["m"], 1, j["n0"], 1, 0.0, j["seed"], out=sl,
-                                   stream=s)
-                    else:
-                        pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"],
-                                         out=sl, stream=s)
-                    self.launches += 1
-                plan = None
-                offsets = [int(x) for x in offs]
-            else:
-                plan = pg.BatchPlan([r.job for r in batch], tile_edges=self.tile_edges,
-                                    device=self.device)
-                arena = pg.empty_device((max(plan.total_edges, 1), 2), torch.int32,
-                                        self.device)
-                pg.gen_batch(plan, arena=arena, workspace=self.batch_ws[i], stream=s)
+            offs = np.cumsum([0] + [job_edges(r.job) + (job_edges(r.job) & 1) for r in batch])
+            arena = pg.empty_device((max(int(offs[-1]), 1), 2), torch.int32, self.device)
+            for k, r in enumerate(batch):
+                j, a = r.job, int(offs[k])
+                sl = arena[a:a + job_edges(j)]
+                if j["kind"] == "pba":
+                    pg.gen_pba(j["n"], j["m"], 1, j["n0"], 1, 0.0, j["seed"], out=sl, stream=s)
+                else:
+                    pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"], out=sl,
+                                     stream=s)
                 self.launches += 1
-                offsets = [int(x) for x in plan.offsets]
+            plan = None
+            offsets = [int(x) for x in offs]
             # one CSR workspace for the batch, sized for its largest
             # request (each request's share is counted in its bytes)
             need = max(pg.pg_csr_workspace_size(job_edges(r.job), job_vertices(r.job))
@@ -316,6 +344,60 @@ class Server:
             ev = torch.cuda.Event()
             ev.record(s)
         return _Batch(batch, s, ev, keep=[plan, arena, ws], status=status)
+
+    def _start_batched(self, i, batch, now) -> _Batch:
+        """One persistent generation launch for the batch; then the CSRs of
+        its small requests from one sort of their union (gen_batch_csr), and
+        of each large one from its own edges_to_csr call."""
+        torch, pg = self.torch, self.pg
+        s = self.streams[i]
+        small = [job_edges(r.job) < self.batch_csr_edges for r in batch]
+        with torch.cuda.stream(s):
+            plan = pg.BatchPlan([dict(r.job, want_csr=sm) for r, sm in zip(batch, small)],
+                                tile_edges=self.tile_edges, device=self.device)
+            arena = pg.empty_device((max(plan.total_edges, 1), 2), torch.int32, self.device)
+            pg.gen_batch(plan, arena=arena, workspace=self.batch_ws[i], stream=s)
+            self.launches += 1
+            keep = [plan, arena]
+            batch_status = None
+            if any(small):
+                ws = pg.empty_device(max(pg.pg_batch_csr_workspace_size(plan), 256), torch.uint8,
+                                     self.device)
+                rp_all = pg.empty_device(max(plan.csr_rows_total, 1), torch.int64, self.device)
+                col_all = pg.empty_device(max(plan.csr_cols_total, 1), torch.int32, self.device)
+                pg.gen_batch_csr(plan, arena, row_ptr=rp_all, col=col_all, workspace=ws, stream=s)
+                self.launches += 1
+                keep.append(ws)
+                batch_status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+                off = pg.pg_batch_csr_wait_error_offset(plan)
+                if off is not None:   # the sort's wait word, to pinned memory
+                    batch_status.copy_(ws[off:off + 4].view(torch.int32), non_blocking=True)
+                share = _CsrShare(live=sum(small))
+            status = None
+            if not all(small):
+                need = max(pg.pg_csr_workspace_size(job_edges(r.job), job_vertices(r.job))
+                           for r, sm in zip(batch, small) if not sm)
+                ws_big = pg.empty_device(max(need, 256), torch.uint8, self.device)
+                keep.append(ws_big)
+                status = torch.zeros(len(batch), dtype=torch.int32, pin_memory=True)
+            for k, r in enumerate(batch):
+                if small[k]:
+                    r.row_ptr, r.col = plan.csr_of(rp_all, col_all, k)
+                    r.csr_share = share
+                else:
+                    E, N = job_edges(r.job), job_vertices(r.job)
+                    r.row_ptr, r.col = pg.edges_to_csr(plan.edges_of(arena, k), N,
+                                                       workspace=ws_big, stream=s)
+                    off = pg.pg_csr_wait_error_offset(E, N)
+                    if off is not None:   # the call's wait word, to pinned memory
+                        status[k:k + 1].copy_(ws_big[off:off + 4].view(torch.int32),
+                                              non_blocking=True)
+                    self.launches += 1
+                r.launched = now
+                r.state = "running"
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return _Batch(batch, s, ev, keep=keep, status=status, batch_status=batch_status)
 
     def step(self, now: float | None = None) -> int:
         """One scheduling step; returns the number of requests completed."""

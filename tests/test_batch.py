@@ -36,7 +36,7 @@ def oracle_job(j):
     return o.kron(j["initiator"], j["k"], j["n_edges"], j["seed"])
 
 
-def _plan_host(jobs, tile=512):
+def _plan_host(jobs, tile=512, id64=False, host_out=None):
     """Run pg_batch_plan on the host only (no device copy)."""
     import paper_1003_3684_gb300 as pg
     from paper_1003_3684_gb300 import build
@@ -45,20 +45,35 @@ def _plan_host(jobs, tile=512):
     arr = (pg._PgJob * len(jobs))()
     keep = []
     for i, j in enumerate(jobs):
-        if j["kind"] == "pba":
-            arr[i] = pg._PgJob(0, j["m"], j["n0"], 0, j["n"], j["seed"], None)
-        else:
-            P = np.ascontiguousarray(j["initiator"], dtype=np.float64)
-            keep.append(P)
-            arr[i] = pg._PgJob(1, 0, P.shape[0], j["k"], j["n_edges"], j["seed"],
-                               P.ctypes.data_as(C.c_void_p))
+        arr[i] = pg._job_struct(j, keep)
     size = L.pg_batch_plan_size(C.cast(arr, C.c_void_p), len(jobs))
     host = np.zeros(size, np.uint8)
     offs = np.zeros(len(jobs) + 1, np.uint64)
     items = C.c_uint64(0)
-    st = L.pg_batch_plan(C.cast(arr, C.c_void_p), len(jobs), tile, 0, host.ctypes.data_as(C.c_void_p),
-                         size, offs.ctypes.data_as(C.c_void_p), C.byref(items))
+    st = L.pg_batch_plan(C.cast(arr, C.c_void_p), len(jobs), tile, 1 if id64 else 0,
+                         host.ctypes.data_as(C.c_void_p), size, offs.ctypes.data_as(C.c_void_p),
+                         C.byref(items))
+    if host_out is not None:
+        host_out.append(host)
     return st, offs, items.value
+
+
+def two_phase_jobs():
+    """Two-phase PBA jobs (blocks > 1) between serial and Kronecker ones."""
+    return [dict(kind="pba", n=3001, m=3, n0=4, seed=1),                      # odd edge count
+            dict(kind="pba", n=8 * 1000, m=4, n0=5, blocks=8, inter_frac=0.1, seed=2),
+            dict(kind="kron", initiator=W.KRON_INITIATOR, k=11, n_edges=7777, seed=3),
+            dict(kind="pba", n=4 * 2048, m=3, n0=4, blocks=4, inter_frac=0.3, faction_width=2,
+                 seed=4),
+            dict(kind="pba", n=0, m=2, n0=3, seed=5),
+            dict(kind="pba", n=16 * 700, m=5, n0=6, blocks=16, inter_frac=0.0, seed=6)]
+
+
+def job_edges(j):
+    if j["kind"] == "kron":
+        return j["n_edges"]
+    e0 = j["n0"] * (j["n0"] - 1) // 2
+    return j.get("blocks", 1) * e0 + j["n"] * j["m"]
 
 
 def test_batch_plan_offsets_and_items():
@@ -84,6 +99,72 @@ def test_batch_plan_offsets_and_items():
 def test_batch_plan_rejects_bad_jobs(bad):
     st, _, _ = _plan_host([dict(kind="pba", n=10, m=2, n0=3, seed=1), bad])
     assert st == 1
+
+
+def test_batch_plan_places_two_phase_jobs_on_even_edges():
+    import paper_1003_3684_gb300 as pg
+    jobs = two_phase_jobs()
+    for id64 in (False, True):
+        st, offs, items = _plan_host(jobs, tile=512, id64=id64)
+        assert st == 0
+        prev_end = 0
+        for i, j in enumerate(jobs):
+            a = int(offs[i])
+            gap = a - prev_end
+            two = j.get("blocks", 1) > 1
+            # a two-phase job starts on an even edge with 32-bit ids, else right after
+            assert gap == ((prev_end & 1) if two and not id64 else 0), (i, gap)
+            prev_end = a + job_edges(j)
+            if j["kind"] == "pba":
+                assert job_edges(j) == pg.pg_pba_edge_count(j["n"], j["m"], j.get("blocks", 1),
+                                                            j["n0"])
+        assert int(offs[-1]) == prev_end
+        # work items: only the serial and Kronecker jobs have tiles
+        assert items == sum(max(1, -(-j["n"] * j["m"] // 512)) if j["kind"] == "pba"
+                            else -(-j["n_edges"] // 512) for j in jobs
+                            if j.get("blocks", 1) == 1)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(kind="pba", n=1001, m=3, n0=4, blocks=8, inter_frac=0.1, seed=1),   # blocks ∤ n
+    dict(kind="pba", n=800, m=3, n0=4, blocks=8, inter_frac=1.5, seed=1),    # f > 1
+    dict(kind="pba", n=800, m=3, n0=4, blocks=8, inter_frac=0.1, faction_width=3, seed=1),
+])
+def test_batch_plan_rejects_bad_two_phase_jobs(bad):
+    st, _, _ = _plan_host([dict(kind="pba", n=10, m=2, n0=3, seed=1), bad])
+    assert st == 1
+
+
+def test_batch_csr_layout_on_the_host():
+    import paper_1003_3684_gb300 as pg
+    jobs = two_phase_jobs()
+    for i, j in enumerate(jobs):
+        j["want_csr"] = i % 3 != 2
+    hosts = []
+    st, offs, _ = _plan_host(jobs, host_out=hosts)
+    assert st == 0
+    L = pg._batch_lib()
+    rows = np.zeros(len(jobs), np.uint64)
+    cols = np.zeros(len(jobs), np.uint64)
+    rt, ct = C.c_uint64(0), C.c_uint64(0)
+    assert L.pg_batch_csr_layout(hosts[0].ctypes.data_as(C.c_void_p), len(jobs),
+                                 rows.ctypes.data_as(C.c_void_p), cols.ctypes.data_as(C.c_void_p),
+                                 C.byref(rt), C.byref(ct)) == 0
+    r = c = 0
+    for i, j in enumerate(jobs):
+        if not j["want_csr"]:
+            assert rows[i] == cols[i] == np.uint64(2**64 - 1)
+            continue
+        assert (int(rows[i]), int(cols[i])) == (r, c)
+        r += pg._job_vertices(j) + 1
+        c += job_edges(j)
+    assert (rt.value, ct.value) == (r, c)
+    assert L.pg_batch_csr_workspace_size(hosts[0].ctypes.data_as(C.c_void_p)) > 0
+    # a union of more than 2^32 vertices does not fit 32-bit ids
+    big = [dict(kind="kron", initiator=W.KRON_INITIATOR, k=31, n_edges=10, seed=i,
+                want_csr=True) for i in range(3)]
+    assert _plan_host(big)[0] == 1
+    assert _plan_host(big, id64=True)[0] == 0
 
 
 def test_batch_plan_rejects_bad_tile():
@@ -139,3 +220,98 @@ def test_autotune_picks_a_candidate(tmp_path, monkeypatch):
     assert best["tile_edges"] in (512, 2048) and not best["cached"]
     again = autotune.tune_batch(jobs, reps=1, tiles=(512, 2048), fractions=(1.0,))
     assert again["cached"] and again["tile_edges"] == best["tile_edges"]
+
+
+def _single(pg, j, id64):
+    """The single-graph call a batch job must equal."""
+    if j["kind"] == "kron":
+        return pg.gen_kronecker(j["initiator"], j["k"], j["n_edges"], j["seed"], id64=id64)
+    return pg.gen_pba(j["n"], j["m"], j.get("blocks", 1), j["n0"], j.get("faction_width", 1),
+                      j.get("inter_frac", 0.0), j["seed"], id64=id64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("id64", [False, True])
+def test_batch_two_phase_jobs_equal_single_calls(id64):
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    jobs = two_phase_jobs()
+    plan = pg.BatchPlan(jobs, tile_edges=1024, id64=id64)
+    arena = pg.gen_batch(plan)
+    torch.cuda.synchronize()
+    for i, j in enumerate(jobs):
+        assert torch.equal(plan.edges_of(arena, i), _single(pg, j, id64)), (i, j)
+    # the small two-phase job against the oracle itself
+    j = jobs[1]
+    ref, _, _ = o.pba(j["n"], j["m"], j["blocks"], j["n0"], 1, j["inter_frac"], j["seed"])
+    got = plan.edges_of(arena, 1).cpu().numpy().view(np.uint64 if id64 else np.uint32)
+    assert np.array_equal(got.astype(np.uint64), ref)
+
+
+@pytest.mark.gpu
+def test_batch_with_two_phase_jobs_replays_in_a_cuda_graph():
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    plan = pg.BatchPlan(two_phase_jobs() + mixed_jobs()[:10], tile_edges=2048)
+    arena = torch.zeros((plan.total_edges, 2), dtype=torch.int32, device="cuda")
+    ws = torch.empty(pg.pg_batch_workspace_size(plan), dtype=torch.uint8, device="cuda")
+    pg.gen_batch(plan, arena=arena, workspace=ws)
+    ref = arena.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pg.gen_batch(plan, arena=arena, workspace=ws)
+    for _ in range(2):
+        arena.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(arena, ref)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("id64", [False, True])
+def test_batch_csr_equals_each_jobs_csr(id64):
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    jobs = two_phase_jobs() + mixed_jobs()[:14]
+    for i, j in enumerate(jobs):
+        j["want_csr"] = i % 4 != 1
+    plan = pg.BatchPlan(jobs, tile_edges=512, id64=id64)
+    arena = pg.gen_batch(plan)
+    row_ptr, col = pg.gen_batch_csr(plan, arena, check=True)
+    torch.cuda.synchronize()
+    idt = np.uint64 if id64 else np.uint32
+    for i, j in enumerate(jobs):
+        if not j["want_csr"]:
+            assert plan.csr_rows[i] == -1
+            continue
+        rp, cl = plan.csr_of(row_ptr, col, i)
+        e = plan.edges_of(arena, i).cpu().numpy().view(idt).astype(np.uint64)
+        ref_rp, ref_col = o.csr(e, pg._job_vertices(j))
+        assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp), (i, j)
+        assert np.array_equal(cl.cpu().numpy().view(idt).astype(np.uint64), ref_col), (i, j)
+
+
+@pytest.mark.gpu
+def test_batch_csr_of_grouped_jobs_only_and_of_none():
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    # only BA jobs: their union is grouped by source, so no sort runs
+    jobs = [dict(kind="pba", n=500 + 37 * i, m=1 + i % 4, n0=2 + i % 4, seed=i, want_csr=True)
+            for i in range(12)]
+    plan = pg.BatchPlan(jobs, tile_edges=256)
+    arena = pg.gen_batch(plan)
+    row_ptr, col = pg.gen_batch_csr(plan, arena, check=True)
+    torch.cuda.synchronize()
+    for i, j in enumerate(jobs):
+        rp, cl = plan.csr_of(row_ptr, col, i)
+        ref_rp, ref_col = o.csr(o.ba(j["n"], j["m"], j["n0"], j["seed"]), pg._job_vertices(j))
+        assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp)
+        assert np.array_equal(cl.cpu().numpy().view(np.uint32).astype(np.uint64), ref_col)
+    # no job asks for a CSR: nothing to do
+    plan = pg.BatchPlan([dict(kind="pba", n=100, m=2, n0=3, seed=1)], tile_edges=256)
+    assert plan.csr_rows_total == 0 and pg.pg_batch_csr_workspace_size(plan) == 0
+    pg.gen_batch_csr(plan, pg.gen_batch(plan))
