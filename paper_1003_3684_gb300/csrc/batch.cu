@@ -146,12 +146,12 @@ __device__ __forceinline__ void kron_level(uint32_t w, uint32_t base, uint32_t u
 
 // The same pick for a 2x2 initiator whose four cells are all positive
 // (n_zero = 0, three real thresholds u0 <= u1 <= u2): the row bit is
-// (w > u1), the column bit the parity of the three compares.
+// a = (w > u1), the column bit (w > u2) when a is set, else (w > u0).
 __device__ __forceinline__ void kron_level_full(uint32_t w, uint32_t u0, uint32_t u1, uint32_t u2,
                                                 uint64_t& row, uint64_t& col)
 {
     const uint32_t a = w > u1 ? 1u : 0u;
-    const uint32_t b = (w > u0 ? 1u : 0u) ^ a ^ (w > u2 ? 1u : 0u);
+    const uint32_t b = w > (a ? u2 : u0) ? 1u : 0u;
     row = row * 2 + a;
     col = col * 2 + b;
 }
@@ -169,7 +169,7 @@ __device__ __forceinline__ void kron_edge_full32(const Key& key, uint32_t k, uin
     uint32_t l = 0;
     auto level = [&](uint32_t w) {
         const uint32_t a = w > u1 ? 1u : 0u;
-        const uint32_t b = (w > u0 ? 1u : 0u) ^ a ^ (w > u2 ? 1u : 0u);
+        const uint32_t b = w > (a ? u2 : u0) ? 1u : 0u;
         row = row * 2 + a;
         col = col * 2 + b;
     };

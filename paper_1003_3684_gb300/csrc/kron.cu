@@ -65,14 +65,15 @@ __device__ __forceinline__ void descend2(uint32_t w, uint32_t u0, uint32_t u1, u
 
 // The same pick when cell 0 has positive weight and all three thresholds
 // are real (n_zero = 0, n_u = 3): with u0 <= u1 <= u2 the row bit of the
-// cell is (w > u1) and the column bit the parity of the three compares;
-// row = 2*row + a runs on the multiply-add pipe rather than the ALU pipe.
+// cell is a = (w > u1), and its column bit is (w > u2) when a is set (cells
+// 2, 3), else (w > u0) (cells 0, 1): two compares instead of three and a
+// parity. row = 2*row + a runs on the multiply-add pipe, not the ALU pipe.
 template <typename T>
 __device__ __forceinline__ void descend2_full(uint32_t w, uint32_t u0, uint32_t u1, uint32_t u2,
                                               T& row, T& col)
 {
     const uint32_t a = w > u1 ? 1u : 0u;
-    const uint32_t b = (w > u0 ? 1u : 0u) ^ a ^ (w > u2 ? 1u : 0u);
+    const uint32_t b = w > (a ? u2 : u0) ? 1u : 0u;
     row = row * 2 + (T)a;
     col = col * 2 + (T)b;
 }
