@@ -430,8 +430,14 @@ pg_status gen_random_cells(uint64_t n_vertices, uint64_t n_edges, uint64_t seed,
  *   bytes, 256-byte aligned. Unlike the generators, this call waits for the
  *   stream once per BFS level (to read the next frontier's size);
  *   *levels_out (host) = number of levels run (the source's eccentricity + 1
- *   within its component), *scanned_out (host) = adjacency entries examined
- *   (the sum of the reached vertices' row lengths).
+ *   within its component), *scanned_out (host) = the sum of the reached
+ *   vertices' row lengths (the adjacency entries a top-down search reads).
+ *   flags: PG_BFS_UNDIRECTED declares the CSR symmetric (every (u, v) has a
+ *   (v, u)); wide levels may then run bottom-up, each unvisited vertex
+ *   looking for a parent in the frontier (Beamer, Asanovic and Patterson,
+ *   "Direction-Optimizing Breadth-First Search", SC'12). The results are the
+ *   same either way; on a CSR that is not symmetric the flag gives wrong
+ *   distances. 0: every level top-down.
  * ---------------------------------------------------------------------- */
 #define PG_DEG_OUT 0
 #define PG_DEG_IN 1
@@ -440,9 +446,10 @@ pg_status pg_degrees(const void* d_edges, uint64_t n_edges, uint64_t n_vertices,
                      int which, uint64_t* d_deg, void* stream);
 pg_status pg_degree_histogram(const uint64_t* d_deg, uint64_t n_vertices, uint32_t max_degree,
                               uint64_t* d_hist, void* stream);
+#define PG_BFS_UNDIRECTED 1u
 size_t pg_bfs_workspace_size(uint64_t n_vertices);
 pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertices, pg_idwidth w,
-                 uint64_t source, uint32_t* d_dist, void* d_ws, size_t ws_bytes,
+                 uint64_t source, uint32_t flags, uint32_t* d_dist, void* d_ws, size_t ws_bytes,
                  uint32_t* levels_out, uint64_t* scanned_out, void* stream);
 
 /* ------------------------------------------------------------------------

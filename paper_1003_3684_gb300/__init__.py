@@ -46,6 +46,7 @@ __all__ = [
 PG_OK, PG_EINVAL, PG_ENOSPC, PG_ECUDA, PG_ETIMEOUT, PG_ENOMEM = range(6)
 PG_ID32, PG_ID64 = 0, 1
 PG_KRON_STOCHASTIC, PG_KRON_DETERMINISTIC = 0, 1
+PG_BFS_UNDIRECTED = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # PGEN_LIBRARY=checked loads the bounds-checked build (same entry points);
@@ -453,7 +454,7 @@ def _analysis_lib():
         L.pg_degree_histogram.restype = i32
         L.pg_bfs_workspace_size.argtypes = [u64]
         L.pg_bfs_workspace_size.restype = sz
-        L.pg_bfs.argtypes = [vp, vp, u64, i32, u64, vp, vp, sz, C.POINTER(u32),
+        L.pg_bfs.argtypes = [vp, vp, u64, i32, u64, u32, vp, vp, sz, C.POINTER(u32),
                              C.POINTER(u64), vp]
         L.pg_bfs.restype = i32
         L._analysis_ready = True
@@ -483,10 +484,13 @@ def degree_histogram(deg, max_degree: int, out=None, stream=None):
     return out
 
 
-def bfs(row_ptr, col, source: int, dist=None, workspace=None, stream=None):
+def bfs(row_ptr, col, source: int, dist=None, workspace=None, stream=None,
+        undirected: bool = False):
     """BFS hop distances from source (int32 view of uint32; -1 = unreached).
 
-    Returns (dist, levels, scanned). Waits for the stream once per level."""
+    Returns (dist, levels, scanned). Waits for the stream once per level.
+    undirected=True declares the CSR symmetric, so that wide levels may run
+    bottom-up (same results)."""
     import torch
     L = _analysis_lib()
     N = row_ptr.numel() - 1
@@ -496,8 +500,8 @@ def bfs(row_ptr, col, source: int, dist=None, workspace=None, stream=None):
         workspace = _empty(L.pg_bfs_workspace_size(N), torch.uint8, row_ptr.device)
     levels, scanned = u32(0), u64(0)
     st = L.pg_bfs(_ptr(row_ptr), _ptr(col), N, PG_ID64 if col.dtype == torch.int64 else PG_ID32,
-                  source, _ptr(dist), _ptr(workspace), workspace.numel(), C.byref(levels),
-                  C.byref(scanned), _stream(stream))
+                  source, PG_BFS_UNDIRECTED if undirected else 0, _ptr(dist), _ptr(workspace),
+                  workspace.numel(), C.byref(levels), C.byref(scanned), _stream(stream))
     _check("pg_bfs", st)
     return dist[:N], int(levels.value), int(scanned.value)
 

@@ -89,11 +89,15 @@ struct BfsQueue {
             // a stale cached word only costs an atomic that finds the bit set
             if ((vis[u >> 5] & bit) == 0) claim = (atomicOr(&vis[u >> 5], bit) & bit) == 0;
         }
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, claim);
-        if (claim) {
-            dist[u] = level + 1;
-            buf[held + __popc(m & lt)] = u;
-        }
+        if (claim) dist[u] = level + 1;
+        push(claim, u, lane, lt);
+    }
+
+    // appends u (where `take`) to the next frontier
+    __device__ __forceinline__ void push(bool take, uint32_t u, uint32_t lane, uint32_t lt)
+    {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, take);
+        if (take) buf[held + __popc(m & lt)] = u;
         held += __popc(m);
         if (held >= 32) {
             __syncwarp();
@@ -145,7 +149,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
                                                         uint32_t* __restrict__ dist,
                                                         uint32_t* __restrict__ vis, uint32_t level,
                                                         uint64_t N,
-                                                        unsigned long long* __restrict__ scanned,
                                                         unsigned long long* __restrict__ long_ctr,
                                                         uint32_t* __restrict__ long_v,
                                                         uint32_t* __restrict__ long_base)
@@ -159,7 +162,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
     BfsQueue Q{wbuf[wid], 0, next, nsize, dist, vis, level, N};
     uint64_t* st = wstart[wid];
     uint64_t* rw = wrow[wid];
-    unsigned long long seen = 0;
     const uint64_t first = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     for (uint64_t c = first; c < fsize; c += warps * 32) {
         uint64_t a = 0, d = 0;
@@ -189,7 +191,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
         st[lane] = incl - d;
         rw[lane] = a;
         __syncwarp();
-        seen += total;
         for (uint64_t base = 0; base < total; base += 32) {
             const uint64_t k = base + lane;
             bool have = false;
@@ -210,7 +211,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_level_kernel(const uint64_
         __syncwarp();   // the next chunk rewrites the row tables
     }
     Q.flush(lane);
-    if (lane == 0 && seen) atomicAdd(scanned, seen);
 }
 
 // One BFS level, long rows: slice t of the level's long rows is entries
@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_long_kernel(const uint64_t
                                                        uint32_t* __restrict__ dist,
                                                        uint32_t* __restrict__ vis, uint32_t level,
                                                        uint64_t N,
-                                                       unsigned long long* __restrict__ scanned,
                                                        const unsigned long long* __restrict__ long_ctr,
                                                        const uint32_t* __restrict__ long_v,
                                                        const uint32_t* __restrict__ long_base)
@@ -239,7 +238,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_long_kernel(const uint64_t
     const uint32_t rows = (uint32_t)(ctr >> 32), slices = (uint32_t)ctr;
     const uint32_t warps = gridDim.x * (blockDim.x >> 5);
     BfsQueue Q{wbuf[wid], 0, next, nsize, dist, vis, level, N};
-    unsigned long long seen = 0;
     for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + wid; t < slices; t += warps) {
         uint32_t lo = 0, n = rows;   // r lies in [lo, lo + n); long_base[lo] <= t
         while (n > 1) {
@@ -259,7 +257,6 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_long_kernel(const uint64_t
             e1 = (e0 + kSlice < end) ? e0 + kSlice : end;
             if (e0 > e1) e0 = e1;
         }
-        seen += e1 - e0;
         for (uint64_t e = e0; e < e1; e += 32) {
             bool have = false;
             uint32_t u = 0;
@@ -272,7 +269,63 @@ __global__ void __launch_bounds__(kBfsWarps * 32) bfs_long_kernel(const uint64_t
         }
     }
     Q.flush(lane);
-    if (lane == 0 && seen) atomicAdd(scanned, seen);
+}
+
+// One BFS level bottom-up (Beamer, Asanovic and Patterson, "Direction-
+// Optimizing Breadth-First Search", SC'12), for a symmetric CSR: every vertex
+// not yet visited looks through its row for a neighbour at distance `level`
+// and, at the first one, takes distance level + 1. A warp owns 32 consecutive
+// vertices, one visited word, and sets their new bits with one plain store:
+// no other warp writes that word during the level. A neighbour claimed in
+// the same level already reads level + 1, so it is never taken for a parent.
+template <typename Id>
+__global__ void __launch_bounds__(kBfsWarps * 32) bfs_bottom_up_kernel(
+    const uint64_t* __restrict__ row_ptr, const Id* __restrict__ col, uint32_t* __restrict__ next,
+    uint32_t* __restrict__ nsize, uint32_t* __restrict__ dist, uint32_t* __restrict__ vis,
+    uint32_t level, uint64_t N)
+{
+    __shared__ uint32_t wbuf[kBfsWarps][64];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    BfsQueue Q{wbuf[wid], 0, next, nsize, dist, vis, level, N};
+    for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < N;
+         base += warps * 32) {
+        const uint64_t v = base + lane;
+        const uint32_t word = vis[base >> 5];
+        bool found = false;
+        if (v < N && ((word >> lane) & 1u) == 0) {
+            const uint64_t b = row_ptr[v + 1];
+            for (uint64_t e = row_ptr[v]; e < b; ++e) {
+                const uint64_t u = load_streaming(col + e);
+                if (u < N && dist[u] == level) {
+                    found = true;
+                    break;
+                }
+            }
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, found);
+        if (found) dist[v] = level + 1;
+        if (lane == 0 && m) vis[base >> 5] = word | m;
+        Q.push(found, (uint32_t)v, lane, lt);
+    }
+    Q.flush(lane);
+}
+
+// scanned = the sum of the reached vertices' row lengths (what a top-down
+// search reads, whichever direction each level ran).
+__global__ void __launch_bounds__(256) bfs_reach_kernel(const uint64_t* __restrict__ row_ptr,
+                                                        const uint32_t* __restrict__ dist,
+                                                        uint64_t N,
+                                                        unsigned long long* __restrict__ scanned)
+{
+    unsigned long long sum = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += stride)
+        if (dist[v] != 0xFFFFFFFFu) sum += row_ptr[v + 1] - row_ptr[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(scanned, sum);
 }
 
 __global__ void bfs_seed_kernel(uint32_t* dist, uint32_t* vis, uint32_t* frontier, uint32_t source)
@@ -344,10 +397,11 @@ size_t pg_bfs_workspace_size(uint64_t n_vertices)
 }
 
 pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertices, pg_idwidth w,
-                 uint64_t source, uint32_t* d_dist, void* d_ws, size_t ws_bytes,
+                 uint64_t source, uint32_t flags, uint32_t* d_dist, void* d_ws, size_t ws_bytes,
                  uint32_t* levels_out, uint64_t* scanned_out, void* stream)
 {
     if (w != PG_ID32 && w != PG_ID64) return PG_EINVAL;
+    if (flags & ~(uint32_t)PG_BFS_UNDIRECTED) return PG_EINVAL;
     if (n_vertices == 0 || n_vertices >= 0xFFFFFFFFull || source >= n_vertices) return PG_EINVAL;
     if (!d_row_ptr || !d_col || !d_dist || !d_ws || !aligned(d_ws, 256)) return PG_EINVAL;
     if (ws_bytes < pg_bfs_workspace_size(n_vertices)) return PG_ENOMEM;
@@ -370,35 +424,61 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
     if (cudaMemsetAsync(vis, 0, vbytes, s) != cudaSuccess) return PG_ECUDA;
     bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, vis, fr[0], (uint32_t)source);
     uint32_t fsize = 1, level = 0, cur = 0;
+    uint64_t visited = 1;
+    bool bottom_up = false;
     TraceScope trace("bfs", s);
     // the slice kernel's grid: every warp of a full wave takes slices
     const int long_grid = device_sm_count() * 8;
+    const bool undirected = (flags & PG_BFS_UNDIRECTED) != 0;
     while (fsize > 0) {
+        // direction of this level (Beamer et al.'s rule with vertex counts
+        // standing in for edge counts): bottom-up once the frontier is more
+        // than 1/30 of the vertices not yet visited, top-down again once it
+        // is under 1/24 of all vertices
+        if (undirected) {
+            if (!bottom_up && (uint64_t)fsize * 30 > n_vertices - visited) bottom_up = true;
+            else if (bottom_up && (uint64_t)fsize * 24 < n_vertices) bottom_up = false;
+        }
         if (cudaMemsetAsync(nsize, 0, 16, s) != cudaSuccess) return PG_ECUDA;
-        const int grid = grid_cap(fsize);
-        if (w == PG_ID64) {
-            bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
-                d_row_ptr, (const uint64_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist, vis,
-                level, n_vertices, scanned, long_ctr, long_v, long_base);
-            bfs_long_kernel<uint64_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
-                d_row_ptr, (const uint64_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
-                n_vertices, scanned, long_ctr, long_v, long_base);
+        if (bottom_up) {
+            TraceScope bu_trace("bfs_bottom_up", s);
+            const int grid = grid_cap(n_vertices);
+            if (w == PG_ID64)
+                bfs_bottom_up_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                    d_row_ptr, (const uint64_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
+                    n_vertices);
+            else
+                bfs_bottom_up_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                    d_row_ptr, (const uint32_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
+                    n_vertices);
         } else {
-            bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
-                d_row_ptr, (const uint32_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist, vis,
-                level, n_vertices, scanned, long_ctr, long_v, long_base);
-            bfs_long_kernel<uint32_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
-                d_row_ptr, (const uint32_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
-                n_vertices, scanned, long_ctr, long_v, long_base);
+            const int grid = grid_cap(fsize);
+            if (w == PG_ID64) {
+                bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                    d_row_ptr, (const uint64_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist,
+                    vis, level, n_vertices, long_ctr, long_v, long_base);
+                bfs_long_kernel<uint64_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
+                    d_row_ptr, (const uint64_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
+                    n_vertices, long_ctr, long_v, long_base);
+            } else {
+                bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                    d_row_ptr, (const uint32_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist,
+                    vis, level, n_vertices, long_ctr, long_v, long_base);
+                bfs_long_kernel<uint32_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
+                    d_row_ptr, (const uint32_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
+                    n_vertices, long_ctr, long_v, long_base);
+            }
         }
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
         // the next frontier's size decides whether another level runs
         if (cudaMemcpyAsync(&fsize, nsize, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return PG_ECUDA;
+        visited += fsize;
         cur ^= 1;
         ++level;
     }
+    bfs_reach_kernel<<<grid_cap(n_vertices), 256, 0, s>>>(d_row_ptr, d_dist, n_vertices, scanned);
     uint64_t sc = 0;
     if (cudaMemcpyAsync(&sc, scanned, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -616,12 +616,32 @@ def test_bfs_matches_oracle(name, id64):
                            .view(np.int64 if id64 else np.int32)).cuda()
     if col.numel() == 0:
         col = torch.zeros(1, dtype=col.dtype, device="cuda")
+    # a symmetric CSR also runs with bottom-up levels allowed: the same results
+    modes = [False, True] if flags & o.CSR_SYMMETRIZE else [False]
     for s in sources:
-        dist, levels, scanned = pg.bfs(rp, col, s)
-        torch.cuda.synchronize()
         rd, rl, rs = o.bfs(ref_rp, ref_col, s)
-        assert np.array_equal(dist.cpu().numpy().view(np.uint32), rd), (name, s)
-        assert (levels, scanned) == (rl, rs), (name, s)
+        for undirected in modes:
+            dist, levels, scanned = pg.bfs(rp, col, s, undirected=undirected)
+            torch.cuda.synchronize()
+            assert np.array_equal(dist.cpu().numpy().view(np.uint32), rd), (name, s, undirected)
+            assert (levels, scanned) == (rl, rs), (name, s, undirected)
+
+
+def test_bfs_runs_bottom_up_levels_on_wide_frontiers():
+    # the PBA case's middle levels hold most of the vertices: with the graph
+    # declared undirected those levels run bottom-up (traced separately)
+    e, N, flags, _ = _bfs_case("pba_undirected")
+    ref_rp, ref_col = o.csr_opts(e, N, flags)
+    rp = torch.from_numpy(ref_rp.view(np.int64)).cuda()
+    col = torch.from_numpy(ref_col.astype(np.uint32).view(np.int32)).cuda()
+    pg.pg_trace_dump()
+    pg.pg_trace_enable(True)
+    try:
+        pg.bfs(rp, col, 0, undirected=True)
+        torch.cuda.synchronize()
+    finally:
+        pg.pg_trace_enable(False)
+    assert "bfs_bottom_up" in pg.pg_trace_dump()
 
 
 def test_throughput_probes_run():
