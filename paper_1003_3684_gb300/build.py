@@ -2,7 +2,7 @@
 
 Compiles every csrc/*.cu for sm_103a in parallel with nvcc and links them
 into paper_1003_3684_gb300/libpgen.so (CUDA runtime linked statically, so the
-library only needs the driver). The same sources compiled with -DPGEN_CHECKED
+library only needs the NVIDIA driver). The same sources compiled with -DPGEN_CHECKED
 give libpgen_checked.so, the bounds-checked build (the same entry points;
 pg_check_read reports what its checks found). Run
 ``python -m paper_1003_3684_gb300.build`` (``--force`` rebuilds everything).
