@@ -315,3 +315,42 @@ def test_batch_csr_of_grouped_jobs_only_and_of_none():
     plan = pg.BatchPlan([dict(kind="pba", n=100, m=2, n0=3, seed=1)], tile_edges=256)
     assert plan.csr_rows_total == 0 and pg.pg_batch_csr_workspace_size(plan) == 0
     pg.gen_batch_csr(plan, pg.gen_batch(plan))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("id64", [False, True])
+def test_batch_csr_of_empty_and_seed_only_jobs(id64):
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    jobs = [dict(kind="kron", initiator=W.KRON_INITIATOR, k=9, n_edges=0, seed=1, want_csr=True),
+            dict(kind="pba", n=0, m=3, n0=4, seed=2, want_csr=True),       # the seed clique only
+            dict(kind="kron", initiator=W.KRON_INITIATOR, k=6, n_edges=5, seed=3, want_csr=True),
+            dict(kind="pba", n=8 * 10, m=2, n0=3, blocks=8, inter_frac=0.5, seed=4,
+                 want_csr=True)]
+    plan = pg.BatchPlan(jobs, tile_edges=64, id64=id64)
+    arena = pg.gen_batch(plan)
+    row_ptr, col = pg.gen_batch_csr(plan, arena, check=True)
+    torch.cuda.synchronize()
+    idt = np.uint64 if id64 else np.uint32
+    for i, j in enumerate(jobs):
+        rp, cl = plan.csr_of(row_ptr, col, i)
+        e = plan.edges_of(arena, i).cpu().numpy().view(idt).astype(np.uint64).reshape(-1, 2)
+        ref_rp, ref_col = o.csr(e, pg._job_vertices(j))
+        assert np.array_equal(rp.cpu().numpy().view(np.uint64), ref_rp), (i, j)
+        assert np.array_equal(cl.cpu().numpy().view(idt).astype(np.uint64), ref_col), (i, j)
+    assert int(plan.csr_of(row_ptr, col, 0)[0].sum()) == 0
+
+
+@pytest.mark.gpu
+def test_batch_csr_with_only_an_empty_job():
+    import torch
+
+    import paper_1003_3684_gb300 as pg
+    plan = pg.BatchPlan([dict(kind="kron", initiator=W.KRON_INITIATOR, k=5, n_edges=0, seed=1,
+                              want_csr=True)], tile_edges=64)
+    arena = pg.gen_batch(plan)
+    row_ptr, col = pg.gen_batch_csr(plan, arena, check=True)
+    torch.cuda.synchronize()
+    assert plan.total_edges == 0 and plan.csr_cols_total == 0
+    assert torch.equal(row_ptr[:33], torch.zeros(33, dtype=torch.int64, device="cuda"))
