@@ -101,6 +101,7 @@ PbaGeom make_geom(uint64_t n_b, uint64_t N_e, uint32_t m, uint32_t B, uint32_t n
     if (n_b > 0 && (n_b & (n_b - 1)) == 0) {
         g.nb_shift = 0;
         while (((uint64_t)1 << g.nb_shift) < n_b) ++g.nb_shift;
+        g.lean_add = (n_b - 1) + (g.e0 << g.nb_shift);
     }
     g.div_m = make_fastdiv(m);
     g.div_m32 = make_fastdiv32(m);

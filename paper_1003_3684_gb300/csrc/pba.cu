@@ -446,10 +446,10 @@ __device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, bool& 
     // load of the target's reciprocal has the draw's time to land
     if (fresh) sig = sigma32(cur, c);
     fresh = false;
-    const uint32_t nb = (uint32_t)g.n_b;
-    const uint32_t before = (uint32_t)(((uint64_t)sig * c.R + (nb - 1)) >> g.nb_shift);
+    // X = e0 + ceil(sig*R / n_b) = (sig*R + (n_b - 1) + e0*n_b) >> log2(n_b):
+    // e0*n_b is a multiple of n_b, and the sum stays below n_b*(R + e0 + 1) <= 2^64
+    const uint32_t X = (uint32_t)(((uint64_t)sig * c.R + g.lean_add) >> g.nb_shift);
     const uint32_t e0 = (uint32_t)g.e0;
-    const uint32_t X = e0 + before;
     const uint64_t s = (uint64_t)w.y * X + (((uint64_t)w.x * X) >> 32);
     const uint32_t e = (uint32_t)(s >> 32);
     const uint32_t side = ((uint32_t)s) >> 31;
@@ -460,10 +460,11 @@ __device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, bool& 
     const uint32_t ab = PG_CHECK(ti, kSeedTab) ? __ldg(stab + ti) : 0u;
     const uint32_t vs = side ? (ab >> 16) : (ab & 0xFFFFu);
     v = seed ? vs : g.n0 + sig2;
-    const bool fin = seed || side == 0;
-    cur = fin ? cur : e2;
-    sig = fin ? sig : sig2;
-    return fin;
+    // a continuing chain moves to e2; an ended one is replaced by the caller's
+    // next claim (which sets cur and marks sig fresh) or goes idle
+    cur = e2;
+    sig = sig2;
+    return seed || side == 0;
 }
 
 // Serial BA (blocks = 1): sigma(i) = i div m, E = sigma * m.

@@ -98,6 +98,7 @@ struct PbaGeom {
     uint64_t seg_len;              // entries per segment (a multiple of 16384)
     uint32_t P;                    // phase-1 prefix kept in shared memory
     uint32_t nb_shift;             // log2(n_b) when n_b is a power of two, else 0xffffffff
+    uint64_t lean_add;             // (n_b - 1) + e0 * n_b when n_b is a power of two
     FastDiv div_m, div_nb;
     FastDiv32 div_m32;             // j div m for j < 2^32
     const uint16_t* ftab;          // faction table (device), or null: aligned width-W factions
