@@ -9,13 +9,13 @@
 // marks each row's end in row_ptr.
 //
 // Any other list: least-significant-digit radix sort of the (src, dst) keys,
-// first the digits of dst, then those of src, up to 10 bits per pass:
+// from the low bits of dst to the high bits of src, up to 8 bits per pass:
 //   radix_hist_all one read of the list counts the digits of every pass
 //                  (the totals do not depend on the order a pass leaves);
 //   radix_dstart   per pass, where each digit's run starts in the output;
 //   radix_scatter  per pass: stable rank of each element within its tile
-//                  among equal digits (warp match + per-warp counters +
-//                  cross-warp scan), a reorder in shared memory, the tile's
+//                  among equal digits (shared-memory peer words + per-warp
+//                  counters + cross-warp scan), a reorder in shared memory, the tile's
 //                  start in each digit's run by decoupled look-back over the
 //                  earlier tiles' published counts, and coalesced writes.
 // Ranks come from counts in entry order, never from atomics racing for a
@@ -39,7 +39,7 @@ namespace {
 
 constexpr int kSortWarps = 16;
 constexpr int kSortThreads = kSortWarps * 32;
-constexpr int kMaxDigitBits = 10;
+constexpr int kMaxDigitBits = 8;
 constexpr uint32_t kMaxBuckets = 1u << kMaxDigitBits;
 constexpr uint32_t kScanTile = 4096;
 constexpr uint32_t kGroupedMaxRow = 32;
@@ -55,10 +55,16 @@ struct PairOf<uint64_t> {
     using T = ulonglong2;
 };
 
+// The digit of a pass: field 0 = dst and field 1 = src take `mask` bits at
+// `shift` of that id; field 2 is a digit of the key (src << nd) | dst that
+// starts in dst (shift < nd) and ends in src.
 template <typename P>
-__device__ __forceinline__ uint32_t digit_of(const P& e, int field, int shift, uint32_t mask)
+__device__ __forceinline__ uint32_t digit_of(const P& e, int field, int shift, uint32_t mask,
+                                             int nd)
 {
-    const uint64_t v = field ? (uint64_t)e.x : (uint64_t)e.y;   // field 1 = src, 0 = dst
+    if (field == 2)
+        return (uint32_t)(((uint64_t)e.y >> shift) | ((uint64_t)e.x << (nd - shift))) & mask;
+    const uint64_t v = field ? (uint64_t)e.x : (uint64_t)e.y;
     return (uint32_t)(v >> shift) & mask;
 }
 
@@ -70,10 +76,13 @@ struct SortShape {
 };
 
 // The digits of every LSD pass, from the host: pass k sorts by `bits[k]`
-// bits of the source (field 1) or destination (field 0) at `shift[k]`.
-constexpr int kMaxPasses = 14;   // 64-bit ids: up to 7 digits per field
+// bits of the destination (field 0) or source (field 1) at `shift[k]`, or
+// (field 2) by the bits [shift[k], shift[k] + bits[k]) of the key
+// (src << nd) | dst, which straddle the two ids.
+constexpr int kMaxPasses = 16;   // 64-bit ids: 128 key bits in digits of 8
 struct PassList {
     uint32_t n;
+    int nd;   // bits of the dst field
     int field[kMaxPasses], shift[kMaxPasses], bits[kMaxPasses];
 };
 // Digit totals of every pass in one read of the list: tot[k][d] = number of
@@ -96,12 +105,15 @@ __global__ void __launch_bounds__(256) radix_hist_all_kernel(
 #pragma unroll
         for (int u = 0; u < kU; ++u)
             if (i0 + u * stride < M) e[u] = in[i0 + u * stride];
+        // pass by pass, so that each pass's digit rule is read once for the
+        // kU elements
+        for (uint32_t k = 0; k < pl.n; ++k) {
+            const int field = pl.field[k], shift = pl.shift[k];
+            const uint32_t mask = (1u << pl.bits[k]) - 1;
+            uint32_t* hk = h + k * kMaxBuckets;
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (i0 + u * stride >= M) continue;
-            for (uint32_t k = 0; k < pl.n; ++k)
-                atomicAdd(&h[k * kMaxBuckets +
-                             digit_of(e[u], pl.field[k], pl.shift[k], (1u << pl.bits[k]) - 1)], 1u);
+            for (int u = 0; u < kU; ++u)
+                if (i0 + u * stride < M) atomicAdd(&hk[digit_of(e[u], field, shift, mask, pl.nd)], 1u);
         }
     }
     __syncthreads();
@@ -109,13 +121,15 @@ __global__ void __launch_bounds__(256) radix_hist_all_kernel(
         if (h[t]) atomicAdd(&tot[t], (unsigned long long)h[t]);
 }
 
-// Tile status words, one per (tile, digit): bits 63..60 the pass (1 + its
-// index, so the words of an earlier pass read as not ready), bits 59..58 the
+// Tile status words, one per (tile, digit): bits 63..59 the pass (1 + its
+// index, so the words of an earlier pass read as not ready), bits 58..57 the
 // kind, a pair count below. kAgg: the tile's own count of the digit; kInc: the
 // count of the digit in this tile and every earlier one. The array is zeroed
 // once per call.
-constexpr unsigned long long kAgg = 1ull << 58, kInc = 2ull << 58;
-constexpr unsigned long long kCountMask = (1ull << 58) - 1;
+constexpr int kPassShift = 59;
+constexpr unsigned long long kAgg = 1ull << 57, kInc = 2ull << 57;
+constexpr unsigned long long kCountMask = (1ull << 57) - 1;
+static_assert(kMaxPasses < 32, "the pass tag fits bits 63..59");
 constexpr uint32_t kSpinLimit = 1u << 18;   // polls of one status word
 constexpr int kLookWindow = 8;              // earlier tiles read per round trip
 
@@ -146,7 +160,7 @@ CsrWaitHook csr_wait_hook() { return CsrWaitHook{g_hook_spin.load(), g_hook_with
 template <typename Id>
 __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const typename PairOf<Id>::T* __restrict__ in, typename PairOf<Id>::T* __restrict__ out,
-    uint64_t M, int field, int shift, int bits, unsigned long long* __restrict__ status,
+    uint64_t M, int field, int shift, int bits, int nd, unsigned long long* __restrict__ status,
     uint32_t pass, const uint64_t* __restrict__ dstart, uint32_t* __restrict__ ticket,
     uint32_t* __restrict__ err, const uint32_t* __restrict__ sort_needed, uint32_t spin_limit,
     uint32_t withhold)
@@ -155,9 +169,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     constexpr int kItems = SortShape<Id>::items;
     constexpr uint32_t kTile = SortShape<Id>::tile;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t (*wcnt)[kMaxBuckets] = reinterpret_cast<uint16_t (*)[kMaxBuckets]>(smem);   // 32 KB
-    uint64_t* tbase = reinterpret_cast<uint64_t*>(smem + kSortWarps * kMaxBuckets * 2);   // 8 KB
-    uint32_t* loff = reinterpret_cast<uint32_t*>(tbase + kMaxBuckets);                  // 4 KB
+    uint16_t (*wcnt)[kMaxBuckets] = reinterpret_cast<uint16_t (*)[kMaxBuckets]>(smem);   // 8 KB
+    uint64_t* tbase = reinterpret_cast<uint64_t*>(smem + kSortWarps * kMaxBuckets * 2);   // 2 KB
+    uint32_t* loff = reinterpret_cast<uint32_t*>(tbase + kMaxBuckets);                  // 1 KB
     P* buf = reinterpret_cast<P*>(loff + kMaxBuckets);                                  // tile
     __shared__ uint32_t s_part[kSortWarps + 1];
     __shared__ uint32_t s_tile;
@@ -189,8 +203,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     // item r of every lane, in lane order: the lanes holding equal digits
     // find each other through a word per digit (each ORs in its lane bit,
     // then all read the word back and clear it; the word table is the
-    // reorder buffer, unused until the ranks are done, one 1024-word slab
-    // per warp); the lowest lane of each group reads and advances the
+    // reorder buffer, unused until the ranks are done, one kMaxBuckets-word
+    // slab per warp); the lowest lane of each group reads and advances the
     // warp's counter, the group gets the old value by shuffle; the counter
     // is touched by one thread per group and the syncwarp orders it before
     // the next item's read
@@ -201,7 +215,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     for (int r = 0; r < kItems; ++r) {
         const uint32_t t = wbase + r * 32 + lane;
         const bool valid = t < n;
-        const uint32_t d = valid ? digit_of(e[r], field, shift, mask) : 0xFFFFFFFFu;
+        const uint32_t d = valid ? digit_of(e[r], field, shift, mask, nd) : 0xFFFFFFFFu;
         if (valid) atomicOr(&pmask[d], 1u << lane);
         __syncwarp();
         const uint32_t peers = valid ? pmask[d] : 0u;
@@ -222,7 +236,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     __syncthreads();
     // per digit: prefix over warps (in wcnt) and the tile total (in loff),
     // published at once so that later tiles can sum it
-    const unsigned long long tag = (unsigned long long)(pass + 1) << 60;
+    const unsigned long long tag = (unsigned long long)(pass + 1) << kPassShift;
     volatile unsigned long long* st = status + (uint64_t)tile * nb;
     for (uint32_t d = threadIdx.x; d < nb; d += blockDim.x) {
         uint32_t acc = 0;
@@ -273,7 +287,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     for (int r = 0; r < kItems; ++r) {
         const uint32_t t = wbase + r * 32 + lane;
         if (t < n) {
-            const uint32_t d = digit_of(e[r], field, shift, mask);
+            const uint32_t d = digit_of(e[r], field, shift, mask, nd);
             const uint32_t rank = (rk[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
             const uint32_t at = loff[d] + wcnt[wid][d] + rank;
             if (PG_CHECK(at, n)) buf[at] = e[r];
@@ -300,7 +314,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
                 for (int u = 0; u < kLookWindow; ++u) {
                     if (found || stalled) continue;
                     const unsigned long long flag =
-                        (w[u] >> 60) == pass + 1 ? w[u] & (3ull << 58) : 0;
+                        (w[u] >> kPassShift) == pass + 1 ? w[u] & (3ull << 57) : 0;
                     if (flag == 0) {
                         stalled = true;
                         continue;
@@ -333,7 +347,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     // write runs: sorted position p goes to tbase[d] + p (one table read per pair)
     for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
         const P v = buf[p];
-        const uint32_t d = digit_of(v, field, shift, mask);
+        const uint32_t d = digit_of(v, field, shift, mask, nd);
         if (PG_CHECK(tbase[d] + p, M)) out[tbase[d] + p] = v;
     }
 }
@@ -740,29 +754,37 @@ struct CsrLayout {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// The LSD passes that sort pairs by (src, dst): the digits of dst (the bits
-// of n_dst - 1), then those of src (the bits of n_src - 1), each field cut
-// into equal digits of at most kMaxDigitBits.
+// The LSD passes that sort pairs by (src, dst): the key (src << nd) | dst,
+// nd = the bits of n_dst - 1 and ns those of n_src - 1, cut from its low end
+// into ceil((nd + ns) / kMaxDigitBits) digits whose widths differ by at most
+// one (the wider ones first). A digit inside one id reads that id alone; the
+// one that contains the boundary reads both.
 PassList make_passes(uint64_t n_src, uint64_t n_dst)
 {
     PassList pl;
     std::memset(&pl, 0, sizeof(pl));
-    for (int field = 0; field < 2; ++field) {
-        const uint64_t n = field ? n_src : n_dst;
-        const int bits = bit_length(n > 0 ? n - 1 : 0);
-        const int per_field = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
-        const int width = per_field ? (bits + per_field - 1) / per_field : 0;
-        int shift = 0;
-        for (int ps = 0; ps < per_field; ++ps) {
-            const int b = bits - shift < width ? bits - shift : width;
-            if (b <= 0) break;
-            pl.field[pl.n] = field;
-            pl.shift[pl.n] = shift;
-            pl.bits[pl.n] = b;
-            ++pl.n;
-            shift += b;
+    const int nd = bit_length(n_dst > 0 ? n_dst - 1 : 0);
+    const int ns = bit_length(n_src > 0 ? n_src - 1 : 0);
+    const int total = nd + ns;
+    const int n = (total + kMaxDigitBits - 1) / kMaxDigitBits;
+    pl.nd = nd;
+    int shift = 0;
+    for (int k = 0; k < n; ++k) {
+        const int b = total / n + (k < total % n ? 1 : 0);
+        if (shift + b <= nd) {
+            pl.field[k] = 0;
+            pl.shift[k] = shift;
+        } else if (shift >= nd) {
+            pl.field[k] = 1;
+            pl.shift[k] = shift - nd;
+        } else {
+            pl.field[k] = 2;
+            pl.shift[k] = shift;
         }
+        pl.bits[k] = b;
+        shift += b;
     }
+    pl.n = (uint32_t)n;
     return pl;
 }
 
@@ -829,7 +851,7 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
     uint64_t* dstart = (uint64_t*)(ws + L.off_dig) + (size_t)kMaxPasses * kMaxBuckets;
     uint32_t* tickets = (uint32_t*)(ws + L.off_flag + 64);
     uint32_t* err = (uint32_t*)(ws + L.off_flag + 128);
-    // the passes: dst digits, then src digits, at most kMaxDigitBits each
+    // the passes: digits of the key (src << nd) | dst, at most kMaxDigitBits each
     const PassList pl = make_passes(N, N_dst);
     const P* cur = in;
     int which = 0;
@@ -856,7 +878,7 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
         for (uint32_t k = 0; k < pl.n; ++k) {
             TraceScope trace("csr_radix_scatter", s);
             radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
-                cur, buf[which], M, pl.field[k], pl.shift[k], pl.bits[k], status, k,
+                cur, buf[which], M, pl.field[k], pl.shift[k], pl.bits[k], pl.nd, status, k,
                 dstart + (size_t)k * kMaxBuckets, tickets + k, err, sort_needed, hk.spin_limit,
                 hk.withhold);
             if ((err_c = cudaGetLastError()) != cudaSuccess) return err_c;
