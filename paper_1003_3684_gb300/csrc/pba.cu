@@ -260,12 +260,13 @@ __global__ void __launch_bounds__(kPassThreads) pba_pass_kernel(const __grid_con
         else if (PG_CHECK(v, g.B)) atomicAdd(&hist[v], 1u);
     }
     // the run back to A: 16-byte stores when the run is whole (run is a
-    // multiple of 8 entries and rows are 16-byte aligned)
+    // multiple of 8 entries and rows are 16-byte aligned), marked streaming
+    // so that they do not evict the finished prefixes the copies read
     const bool in_row = n_items == 0 || PG_CHECK(run + n_items - 1, g.N_e);
     if (in_row && n_items == kPassRun) {
         const uint4* src = reinterpret_cast<const uint4*>(my);
         uint4* dst = reinterpret_cast<uint4*>(Ap + run);
-        for (uint32_t t = lane; t < kPassRun / 8; t += 32) dst[t] = src[t];
+        for (uint32_t t = lane; t < kPassRun / 8; t += 32) __stcs(dst + t, src[t]);
     } else if (in_row) {
         for (uint32_t t = lane; t < n_items; t += 32) Ap[run + t] = my[t];
     }
