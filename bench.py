@@ -564,7 +564,9 @@ def run_serve(args, rank: int, world: int, local_rank: int):
     sampler = ClockSampler(local_rank) if rank == 0 else None
     if sampler:
         sampler.start()
+    launch0 = pg.pg_launch_count()
     served = replay(False, trace)
+    launches = pg.pg_launch_count() - launch0
     clocks = sampler.stop() if sampler else None
     pg.pg_trace_enable(False)
     kernels = pg.pg_trace_dump()
@@ -579,7 +581,7 @@ def run_serve(args, rank: int, world: int, local_rank: int):
                             streams=3),
                 latency_ms=dict(p50=served["p50_ms"], p99=served["p99_ms"]),
                 served=served, per_graph=per_graph,
-                gpu_launches=sum(v[0] for v in kernels.values()),
+                gpu_launches=launches,
                 kernels={kk: [v[0], round(v[1], 3)] for kk, v in kernels.items()},
                 clocks=clocks)
     return line if rank == 0 else None
@@ -773,6 +775,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     if sampler:
         sampler.start()
         time.sleep(0.3)
+    launch0 = pg.pg_launch_count()  # the library's kernel launches from here on
     if flush is None:
         # one event between consecutive steps: the region's time and each step's
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -810,7 +813,9 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             raise RuntimeError("edges_to_csr: a bounded wait of the sort gave up (PG_ETIMEOUT)")
     ms_max = max_over_ranks(ms, dev, world)
     value = job_throughput(E, args.steps, world, ms_max)
-    launches = sum(v[0] for v in kernels.values())
+    # every kernel the library launched in the timed steps (the trace above
+    # groups some launches under one name, e.g. all phase-1 levels of a step)
+    launches = pg.pg_launch_count() - launch0
 
     # roofline of the dominant kernel
     peaks = load_peaks()

@@ -550,6 +550,12 @@ pg_status gen_batch_csr(const void* h_plan, const void* d_plan, uint32_t n_jobs,
 void pg_trace_enable(int on);
 size_t pg_trace_dump(char* buf, size_t len);
 
+/* Number of kernels the library has launched in this process, on every
+ * device and stream, since it was loaded (accounting, not part of the
+ * method): a caller reads it before and after a region of work. Counting is
+ * always on and costs one relaxed atomic add per launch. */
+uint64_t pg_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

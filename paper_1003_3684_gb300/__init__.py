@@ -36,7 +36,7 @@ __all__ = [
     "DEG_OUT", "DEG_IN", "DEG_TOTAL", "degrees", "degree_histogram", "bfs", "powerlaw_exponent",
     "path_length_stats",
     "pg_kron_edge_count", "gen_kronecker",
-    "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump",
+    "pg_csr_workspace_size", "edges_to_csr", "pg_trace_enable", "pg_trace_dump", "pg_launch_count",
     "pg_csr_wait_error_offset", "csr_wait_error", "pg_csr_check", "pg_csr_test_wait_hook",
     "pg_checked_build", "pg_check_read", "pg_check_test_out_shift", "CheckReport",
     "empty_device", "set_fail_alloc_at", "BatchPlan", "gen_batch", "pg_batch_workspace_size",
@@ -110,6 +110,8 @@ def lib():
             L.pg_trace_enable.restype = None
             L.pg_trace_dump.argtypes = [C.c_char_p, sz]
             L.pg_trace_dump.restype = sz
+            L.pg_launch_count.argtypes = []
+            L.pg_launch_count.restype = u64
             _lib = L
     return _lib
 
@@ -768,6 +770,11 @@ def kronecker_xor_random(initiator, k: int, n_random: int, n_edges: int = 0, see
 def pg_trace_enable(on: bool = True) -> None:
     """Bracket every library kernel launch with CUDA events (see pgen.h)."""
     lib().pg_trace_enable(1 if on else 0)
+
+
+def pg_launch_count() -> int:
+    """Kernels the library has launched in this process (see pgen.h)."""
+    return int(lib().pg_launch_count())
 
 
 def pg_trace_dump() -> dict:

@@ -367,11 +367,11 @@ pg_status pg_degrees(const void* d_edges, uint64_t n_edges, uint64_t n_vertices,
     TraceScope trace("degrees", s);
     const int grid = grid_cap(n_edges);
     if (w == PG_ID64)
-        degree_kernel<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)d_edges, n_edges, n_vertices,
-                                                    which, (unsigned long long*)d_deg);
+        { degree_kernel<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)d_edges, n_edges, n_vertices,
+                                                    which, (unsigned long long*)d_deg); note_launch(); }
     else
-        degree_kernel<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)d_edges, n_edges, n_vertices,
-                                                    which, (unsigned long long*)d_deg);
+        { degree_kernel<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)d_edges, n_edges, n_vertices,
+                                                    which, (unsigned long long*)d_deg); note_launch(); }
     return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
 }
 
@@ -383,8 +383,8 @@ pg_status pg_degree_histogram(const uint64_t* d_deg, uint64_t n_vertices, uint32
     if (cudaMemsetAsync(d_hist, 0, ((size_t)max_degree + 2) * 8, s) != cudaSuccess) return PG_ECUDA;
     if (n_vertices == 0) return PG_OK;
     TraceScope trace("degree_histogram", s);
-    histogram_kernel<<<grid_cap(n_vertices), 256, 0, s>>>(d_deg, n_vertices, max_degree,
-                                                         (unsigned long long*)d_hist);
+    { histogram_kernel<<<grid_cap(n_vertices), 256, 0, s>>>(d_deg, n_vertices, max_degree,
+                                                         (unsigned long long*)d_hist); note_launch(); }
     return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
 }
 
@@ -422,7 +422,7 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
     if (cudaMemsetAsync(d_dist, 0xFF, n_vertices * 4, s) != cudaSuccess) return PG_ECUDA;
     if (cudaMemsetAsync(ws + 2 * fbytes, 0, 256, s) != cudaSuccess) return PG_ECUDA;
     if (cudaMemsetAsync(vis, 0, vbytes, s) != cudaSuccess) return PG_ECUDA;
-    bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, vis, fr[0], (uint32_t)source);
+    { bfs_seed_kernel<<<1, 1, 0, s>>>(d_dist, vis, fr[0], (uint32_t)source); note_launch(); }
     uint32_t fsize = 1, level = 0, cur = 0;
     uint64_t visited = 1;
     bool bottom_up = false;
@@ -444,29 +444,29 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
             TraceScope bu_trace("bfs_bottom_up", s);
             const int grid = grid_cap(n_vertices);
             if (w == PG_ID64)
-                bfs_bottom_up_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                { bfs_bottom_up_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
                     d_row_ptr, (const uint64_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
-                    n_vertices);
+                    n_vertices); note_launch(); }
             else
-                bfs_bottom_up_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                { bfs_bottom_up_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
                     d_row_ptr, (const uint32_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
-                    n_vertices);
+                    n_vertices); note_launch(); }
         } else {
             const int grid = grid_cap(fsize);
             if (w == PG_ID64) {
-                bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                { bfs_level_kernel<uint64_t><<<grid, kBfsWarps * 32, 0, s>>>(
                     d_row_ptr, (const uint64_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist,
-                    vis, level, n_vertices, long_ctr, long_v, long_base);
-                bfs_long_kernel<uint64_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
+                    vis, level, n_vertices, long_ctr, long_v, long_base); note_launch(); }
+                { bfs_long_kernel<uint64_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
                     d_row_ptr, (const uint64_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
-                    n_vertices, long_ctr, long_v, long_base);
+                    n_vertices, long_ctr, long_v, long_base); note_launch(); }
             } else {
-                bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
+                { bfs_level_kernel<uint32_t><<<grid, kBfsWarps * 32, 0, s>>>(
                     d_row_ptr, (const uint32_t*)d_col, fr[cur], fsize, fr[cur ^ 1], nsize, d_dist,
-                    vis, level, n_vertices, long_ctr, long_v, long_base);
-                bfs_long_kernel<uint32_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
+                    vis, level, n_vertices, long_ctr, long_v, long_base); note_launch(); }
+                { bfs_long_kernel<uint32_t><<<long_grid, kBfsWarps * 32, 0, s>>>(
                     d_row_ptr, (const uint32_t*)d_col, fr[cur ^ 1], nsize, d_dist, vis, level,
-                    n_vertices, long_ctr, long_v, long_base);
+                    n_vertices, long_ctr, long_v, long_base); note_launch(); }
             }
         }
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
@@ -478,7 +478,7 @@ pg_status pg_bfs(const uint64_t* d_row_ptr, const void* d_col, uint64_t n_vertic
         cur ^= 1;
         ++level;
     }
-    bfs_reach_kernel<<<grid_cap(n_vertices), 256, 0, s>>>(d_row_ptr, d_dist, n_vertices, scanned);
+    { bfs_reach_kernel<<<grid_cap(n_vertices), 256, 0, s>>>(d_row_ptr, d_dist, n_vertices, scanned); note_launch(); }
     uint64_t sc = 0;
     if (cudaMemcpyAsync(&sc, scanned, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

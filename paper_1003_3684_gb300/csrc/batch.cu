@@ -706,13 +706,13 @@ pg_status gen_batch(const void* h_plan, const void* d_plan, uint32_t n_jobs, pg_
         if (cudaMemsetAsync(d_ws, 0, 8, s) != cudaSuccess) return PG_ECUDA;
         TraceScope trace("batch_persistent", s);
         if (w == PG_ID64)
-            batch_kernel<uint64_t><<<grid, kBatchThreads, smem, s>>>(
+            { batch_kernel<uint64_t><<<grid, kBatchThreads, smem, s>>>(
                 (const unsigned char*)d_plan, (uint64_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
-                n_jobs);
+                n_jobs); note_launch(); }
         else
-            batch_kernel<uint32_t><<<grid, kBatchThreads, smem, s>>>(
+            { batch_kernel<uint32_t><<<grid, kBatchThreads, smem, s>>>(
                 (const unsigned char*)d_plan, (uint32_t*)d_arena, (unsigned long long*)d_ws, cap_edges,
-                n_jobs);
+                n_jobs); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
     }
     // two-phase PBA jobs: phase 1, the count exchange and the emission of
@@ -818,11 +818,11 @@ pg_status gen_batch_csr(const void* h_plan, const void* d_plan, uint32_t n_jobs,
         const uint64_t full = (uint64_t)device_sm_count() * 8;
         const int grid = (int)(warps / 8 + 1 < full ? warps / 8 + 1 : full);
         if (w == PG_ID64)
-            batch_union_kernel<uint64_t><<<grid, 256, 0, s>>>(
-                (const unsigned char*)d_plan, (const uint64_t*)d_arena, (uint64_t*)ws);
+            { batch_union_kernel<uint64_t><<<grid, 256, 0, s>>>(
+                (const unsigned char*)d_plan, (const uint64_t*)d_arena, (uint64_t*)ws); note_launch(); }
         else
-            batch_union_kernel<uint32_t><<<grid, 256, 0, s>>>(
-                (const unsigned char*)d_plan, (const uint32_t*)d_arena, (uint32_t*)ws);
+            { batch_union_kernel<uint32_t><<<grid, 256, 0, s>>>(
+                (const unsigned char*)d_plan, (const uint32_t*)d_arena, (uint32_t*)ws); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
     }
     const uint64_t col_base[2] = {0, H.csr_edges[0]};
@@ -835,16 +835,16 @@ pg_status gen_batch_csr(const void* h_plan, const void* d_plan, uint32_t n_jobs,
                        L.total - L.off_csr, s, nd) != cudaSuccess)
             return PG_ECUDA;
         if (E > 0 && V >= 2)   // the group's sort had a wait word: fold it into the call's
-            or_word_kernel<<<1, 1, 0, s>>>(
+            { or_word_kernel<<<1, 1, 0, s>>>(
                 wait, (const uint32_t*)(ws + L.off_csr + csr_wait_error_offset(E, V, 0, (int)H.id64,
-                                                                               nd)));
+                                                                               nd))); note_launch(); }
         TraceScope trace("batch_csr_rebase", s);
         const uint64_t R = V + H.csr_jobs[g];
         const uint64_t full = (uint64_t)device_sm_count() * 8;
         const int grid = (int)(R / 256 + 1 < full ? R / 256 + 1 : full);
-        batch_rebase_kernel<<<grid, 256, 0, s>>>(
+        { batch_rebase_kernel<<<grid, 256, 0, s>>>(
             (const uint64_t*)((const unsigned char*)d_plan + H.off_rstart[g]), H.csr_jobs[g], V,
-            rp_u, d_row_ptr);
+            rp_u, d_row_ptr); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
     }
     return PG_OK;

@@ -866,21 +866,21 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
             return cudaErrorUnknown;
         {
             TraceScope trace("csr_radix_hist", s);
-            zero_status_kernel<<<sort_grid(L.n_status / 2 + 1), 256, 0, s>>>(
-                (uint4*)status, (L.n_status * 8 + 15) / 16, sort_needed);
-            radix_hist_all_kernel<Id><<<sort_grid(M), 256, (size_t)pl.n * kMaxBuckets * 4, s>>>(
-                cur, M, pl, tot, sort_needed);
+            { zero_status_kernel<<<sort_grid(L.n_status / 2 + 1), 256, 0, s>>>(
+                (uint4*)status, (L.n_status * 8 + 15) / 16, sort_needed); note_launch(); }
+            { radix_hist_all_kernel<Id><<<sort_grid(M), 256, (size_t)pl.n * kMaxBuckets * 4, s>>>(
+                cur, M, pl, tot, sort_needed); note_launch(); }
         }
         {
             TraceScope trace("csr_scan", s);
-            radix_dstart_kernel<<<pl.n, kMaxBuckets, 0, s>>>(tot, pl, dstart, sort_needed);
+            { radix_dstart_kernel<<<pl.n, kMaxBuckets, 0, s>>>(tot, pl, dstart, sort_needed); note_launch(); }
         }
         for (uint32_t k = 0; k < pl.n; ++k) {
             TraceScope trace("csr_radix_scatter", s);
-            radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
+            { radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
                 cur, buf[which], M, pl.field[k], pl.shift[k], pl.bits[k], pl.nd, status, k,
                 dstart + (size_t)k * kMaxBuckets, tickets + k, err, sort_needed, hk.spin_limit,
-                hk.withhold);
+                hk.withhold); note_launch(); }
             if ((err_c = cudaGetLastError()) != cudaSuccess) return err_c;
             cur = buf[which];
             which ^= 1;
@@ -896,9 +896,9 @@ cudaError_t prefix_max(uint64_t* data, uint64_t n, uint64_t* parts, cudaStream_t
 {
     const uint64_t n_parts = (n + kScanTile - 1) / kScanTile;
     if (n_parts == 0) return cudaSuccess;
-    max_reduce_kernel<<<(unsigned)n_parts, 256, 0, s>>>(data, n, parts);
-    max_parts_kernel<<<1, 1024, 0, s>>>(parts, n_parts);
-    max_apply_kernel<<<(unsigned)n_parts, 256, 0, s>>>(data, n, parts);
+    { max_reduce_kernel<<<(unsigned)n_parts, 256, 0, s>>>(data, n, parts); note_launch(); }
+    { max_parts_kernel<<<1, 1024, 0, s>>>(parts, n_parts); note_launch(); }
+    { max_apply_kernel<<<(unsigned)n_parts, 256, 0, s>>>(data, n, parts); note_launch(); }
     return cudaGetLastError();
 }
 
@@ -925,9 +925,9 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t N_dst
     if (cudaMemsetAsync(d_row_ptr, 0, (N + 1) * 8, s) != cudaSuccess) return cudaErrorUnknown;
     {
         TraceScope trace("csr_check", s);
-        csr_check_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, sort_needed);
-        csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, N, (Id*)d_col, d_row_ptr,
-                                                   sort_needed);
+        { csr_check_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, sort_needed); note_launch(); }
+        { csr_grouped_kernel<Id><<<grid, 256, 0, s>>>((const P*)d_edges, M, N, (Id*)d_col, d_row_ptr,
+                                                   sort_needed); note_launch(); }
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const P* cur;
@@ -936,7 +936,7 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t N_dst
                                 &spare)) != cudaSuccess)
         return err;
     TraceScope trace("csr_finish", s);
-    csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed);
+    { csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed); note_launch(); }
     return prefix_max(d_row_ptr, N + 1, (uint64_t*)(ws + L.off_rpart), s);
 }
 
@@ -982,7 +982,7 @@ cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t 
     const P* in = (const P*)d_edges;
     if ((flags & kOptSym) && M > 0) {
         P* x = (P*)(ws + O.off_x);
-        csr_sym_kernel<Id><<<sort_grid(M), 256, 0, s>>>(in, M, x);
+        { csr_sym_kernel<Id><<<sort_grid(M), 256, 0, s>>>(in, M, x); note_launch(); }
         in = x;
     }
     const P* cur;
@@ -995,15 +995,15 @@ cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t 
         uint64_t* S = nullptr;
         if (flags & kOptOdd) {
             S = reinterpret_cast<uint64_t*>(spare);    // M2 words fit: a pair is >= 8 bytes
-            csr_runstart_kernel<Id><<<sort_grid(M2), 256, 0, s>>>(cur, M2, S);
+            { csr_runstart_kernel<Id><<<sort_grid(M2), 256, 0, s>>>(cur, M2, S); note_launch(); }
             if ((err = prefix_max(S, M2, (uint64_t*)(ws + O.off_spart), s)) != cudaSuccess)
                 return err;
         }
         uint64_t* cpart = (uint64_t*)(ws + O.off_cpart);
-        csr_keep_count_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, flags, S, cpart);
-        scan_parts_kernel<<<1, 1024, 0, s>>>(cpart, O.n_cparts, sort_needed);
-        csr_keep_apply_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, N, flags, S, cpart,
-                                                                        (Id*)d_col, d_row_ptr);
+        { csr_keep_count_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, flags, S, cpart); note_launch(); }
+        { scan_parts_kernel<<<1, 1024, 0, s>>>(cpart, O.n_cparts, sort_needed); note_launch(); }
+        { csr_keep_apply_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, N, flags, S, cpart,
+                                                                        (Id*)d_col, d_row_ptr); note_launch(); }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     return prefix_max(d_row_ptr, N + 1, (uint64_t*)(ws + O.L.off_rpart), s);

@@ -378,28 +378,28 @@ cudaError_t launch_kron_stochastic(const KronParams& p, int id64, void* d_out, u
             const uint32_t b = (uint32_t)e_begin, n = (uint32_t)n_edges;
             if (id64) {
                 auto k = full ? kron2_kernel32<uint64_t, true> : kron2_kernel32<uint64_t, false>;
-                k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, b, n);
+                { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, b, n); note_launch(); }
             } else {
                 auto k = full ? kron2_kernel32<uint32_t, true> : kron2_kernel32<uint32_t, false>;
-                k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, b, n);
+                { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, b, n); note_launch(); }
             }
         } else if (id64 && p.k > 32) {
             auto k = full ? kron2_kernel<uint64_t, uint64_t, true> : kron2_kernel<uint64_t, uint64_t, false>;
-            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+            { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
         } else if (id64) {
             auto k = full ? kron2_kernel<uint64_t, uint32_t, true> : kron2_kernel<uint64_t, uint32_t, false>;
-            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+            { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
         } else {
             auto k = full ? kron2_kernel<uint32_t, uint32_t, true> : kron2_kernel<uint32_t, uint32_t, false>;
-            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
+            { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
         }
     } else {
         if (id64) {
             auto k = kron_generic_kernel<uint64_t>;
-            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+            { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
         } else {
             auto k = kron_generic_kernel<uint32_t>;
-            k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
+            { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
         }
     }
     return cudaGetLastError();
@@ -418,10 +418,10 @@ cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint6
     TraceScope trace("kron_det", s);
     if (id64) {
         auto k = narrow ? kron_det_kernel<uint64_t, true> : kron_det_kernel<uint64_t, false>;
-        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges);
+        { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
     } else {
         auto k = narrow ? kron_det_kernel<uint32_t, true> : kron_det_kernel<uint32_t, false>;
-        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges);
+        { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
     }
     return cudaGetLastError();
 }
@@ -434,10 +434,10 @@ cudaError_t launch_random_cells(const Key& key, uint64_t n_vertices, int id64, v
     TraceScope trace("random_cells", s);
     if (id64) {
         auto k = random_cells_kernel<uint64_t>;
-        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(key, n_vertices, (uint64_t*)d_out, e_begin, n_edges);
+        { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(key, n_vertices, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
     } else {
         auto k = random_cells_kernel<uint32_t>;
-        k<<<grid_for(k, pairs, 256), 256, 0, s>>>(key, n_vertices, (uint32_t*)d_out, e_begin, n_edges);
+        { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(key, n_vertices, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
     }
     return cudaGetLastError();
 }

@@ -430,14 +430,13 @@ __device__ __forceinline__ bool t_link32(uint32_t& cur, uint32_t q, const QRecip
     return fin;
 }
 
-// The same link with sigma(cur) carried in from the previous link (the
-// side-0 value of a link is sigma of the edge the chain moves to, so a link
-// of a continuing chain computes one sigma instead of two), n_b a power of
-// two, and the seed
-// clique's edges read from a table in the workspace (stab[e] = a | b << 16;
-// every lane reads entry 0 unless it hit a seed slot, so the load is a
-// broadcast from L1)
-// instead of a branch: straight-line code apart from nothing.
+// The same link for n_b a power of two, with sigma(cur) carried in from the
+// previous link (the side-0 value of a link is sigma of the edge the chain
+// moves to, so a continuing chain computes one sigma per link instead of
+// two) and the seed clique's edges read from a table in the workspace
+// (stab[e] = a | b << 16; every lane reads entry 0 unless it hit a seed
+// slot, so the load is a broadcast from L1) instead of a branch: the link is
+// straight-line code.
 __device__ __forceinline__ bool t_link_lean(uint32_t& cur, uint32_t& sig, bool& fresh, uint32_t q,
                                             const QRecip& c, const PbaGeom& g,
                                             const uint32_t* __restrict__ stab, uint32_t& v)
@@ -946,11 +945,11 @@ cudaError_t launch_ba(const PbaGeom& g, int id64, void* d_out, cudaStream_t s)
     const bool fast = !wide_path_forced() && g.N_e + g.e0 < ((uint64_t)1 << 32);
     TraceScope trace("ba_chain", s);
     if (id64) {
-        if (fast) ba_kernel<uint64_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out);
-        else ba_kernel<uint64_t, false><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out);
+        if (fast) { ba_kernel<uint64_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out); note_launch(); }
+        else { ba_kernel<uint64_t, false><<<grid, kBaThreads, 0, s>>>(g, (uint64_t*)d_out); note_launch(); }
     } else {
-        if (fast) ba_kernel<uint32_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out);
-        else ba_kernel<uint32_t, false><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out);
+        if (fast) { ba_kernel<uint32_t, true><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out); note_launch(); }
+        else { ba_kernel<uint32_t, false><<<grid, kBaThreads, 0, s>>>(g, (uint32_t*)d_out); note_launch(); }
     }
     return cudaGetLastError();
 }
@@ -1031,9 +1030,9 @@ cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
             TraceScope trace("pba_prefix", s);
             const size_t smem = ((size_t)g.P * 2 + 15) / 16 * 16 + (size_t)g.B * 4;
             if (g.ftab)
-                pba_prefix_kernel<true><<<g.B, kPrefixThreads, smem, s>>>(g, W.A, W.cnt);
+                { pba_prefix_kernel<true><<<g.B, kPrefixThreads, smem, s>>>(g, W.A, W.cnt); note_launch(); }
             else
-                pba_prefix_kernel<false><<<g.B, kPrefixThreads, smem, s>>>(g, W.A, W.cnt);
+                { pba_prefix_kernel<false><<<g.B, kPrefixThreads, smem, s>>>(g, W.A, W.cnt); note_launch(); }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         TraceScope trace("pba_phase1", s);
@@ -1045,21 +1044,21 @@ cudaError_t launch_pba_phase1(const PbaGeom& g, void* d_ws, cudaStream_t s)
             const size_t smem = (((size_t)g.B * 4 + 15) & ~(size_t)15) +
                                 (size_t)(kPassThreads / 32) * kPassRun * 2;
             if (g.ftab)
-                pba_pass_kernel<true><<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
-                    g, (uint32_t)lvl, (uint32_t)hi, W.A, W.cnt);
+                { pba_pass_kernel<true><<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
+                    g, (uint32_t)lvl, (uint32_t)hi, W.A, W.cnt); note_launch(); }
             else
-                pba_pass_kernel<false><<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
-                    g, (uint32_t)lvl, (uint32_t)hi, W.A, W.cnt);
+                { pba_pass_kernel<false><<<dim3(chunks, g.B), kPassThreads, smem, s>>>(
+                    g, (uint32_t)lvl, (uint32_t)hi, W.A, W.cnt); note_launch(); }
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             lvl = hi;
         }
     }
     {
         TraceScope trace("pba_scan", s);
-        pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(W.cnt, W.off, W.R, W.divR, W.recip,
+        { pba_scan_kernel<<<(g.B + 31) / 32, 1024, 0, s>>>(W.cnt, W.off, W.R, W.divR, W.recip,
                                                           (uint32_t)g.n_b, g.B, g.B * g.S, g.e0,
                                                           wide_path_forced() ? 1u : 0u, W.wide,
-                                                          g.n0, W.stab);
+                                                          g.n0, W.stab); note_launch(); }
     }
     return cudaGetLastError();
 }
@@ -1090,30 +1089,30 @@ cudaError_t launch_pba_emit(const PbaGeom& g, int id64, void* d_out, const void*
             TraceScope trace("pba_emit", s);
             if (id64) {
                 if (lean)
-                    pba_emit_kernel<uint64_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
+                    { pba_emit_kernel<uint64_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
                         g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin,
-                        out_cap);
+                        out_cap); note_launch(); }
                 else
-                    pba_emit_kernel<uint64_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
+                    { pba_emit_kernel<uint64_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
                         g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin,
-                        out_cap);
+                        out_cap); note_launch(); }
                 if (!surely_fast)
-                    pba_emit_kernel<uint64_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
+                    { pba_emit_kernel<uint64_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
                         g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint64_t*)d_out, b0, b_begin,
-                        out_cap);
+                        out_cap); note_launch(); }
             } else {
                 if (lean)
-                    pba_emit_kernel<uint32_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
+                    { pba_emit_kernel<uint32_t, 2><<<grid, kEmitThreads, kSmemFast, s>>>(
                         g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin,
-                        out_cap);
+                        out_cap); note_launch(); }
                 else
-                    pba_emit_kernel<uint32_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
+                    { pba_emit_kernel<uint32_t, 1><<<grid, kEmitThreads, kSmemFast, s>>>(
                         g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin,
-                        out_cap);
+                        out_cap); note_launch(); }
                 if (!surely_fast)
-                    pba_emit_kernel<uint32_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
+                    { pba_emit_kernel<uint32_t, 0><<<grid, kEmitThreads, kSmemWide, s>>>(
                         g, W.A, W.off, W.R, W.divR, W.recip, W.wide, W.stab, (uint32_t*)d_out, b0, b_begin,
-                        out_cap);
+                        out_cap); note_launch(); }
             }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -3,6 +3,7 @@
 // `stream` and returns the cudaGetLastError() of its launches.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <initializer_list>
@@ -13,6 +14,11 @@
 #include "pg_common.cuh"
 
 namespace pgen {
+
+// Kernels launched by the library in this process (pg_launch_count): every
+// launch site calls note_launch() right after its launch.
+extern std::atomic<uint64_t> g_launch_count;
+inline void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 
 // Once-per-device set-up (kernel attributes such as the opt-in shared-memory
 // size apply to the device that is current when they are set). run() calls

@@ -94,8 +94,8 @@ pg_status pg_int_probe(int op, uint32_t iters, uint32_t* d_out, size_t out_words
 {
     const size_t threads = pg_philox_probe_threads();
     if (op < 0 || op > 3 || !d_out || out_words < threads || iters == 0) return PG_EINVAL;
-    pgen::int_probe_kernel<<<(unsigned)(threads / pgen::kProbeThreads), pgen::kProbeThreads, 0,
-                             (cudaStream_t)stream>>>(d_out, iters, op, 0x9E3779B9u, 0x7F4A7C15u);
+    { pgen::int_probe_kernel<<<(unsigned)(threads / pgen::kProbeThreads), pgen::kProbeThreads, 0,
+                             (cudaStream_t)stream>>>(d_out, iters, op, 0x9E3779B9u, 0x7F4A7C15u); pgen::note_launch(); }
     return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
 }
 
@@ -111,8 +111,8 @@ pg_status pg_philox_probe(uint32_t calls_per_thread, uint32_t* d_out, size_t out
     const size_t threads = pg_philox_probe_threads();
     if (!d_out || out_words < threads || calls_per_thread == 0) return PG_EINVAL;
     const pgen::Key key = pgen::make_key(0x9E3779B97F4A7C15ull);
-    pgen::philox_probe_kernel<<<(unsigned)(threads / pgen::kProbeThreads), pgen::kProbeThreads, 0,
-                                (cudaStream_t)stream>>>(d_out, calls_per_thread, key);
+    { pgen::philox_probe_kernel<<<(unsigned)(threads / pgen::kProbeThreads), pgen::kProbeThreads, 0,
+                                (cudaStream_t)stream>>>(d_out, calls_per_thread, key); pgen::note_launch(); }
     return cudaGetLastError() == cudaSuccess ? PG_OK : PG_ECUDA;
 }
 

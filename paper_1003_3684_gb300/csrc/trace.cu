@@ -11,9 +11,13 @@
 #include <vector>
 
 #include "../../include/pgen.h"
+#include "pg_internal.h"
 #include "pg_trace.h"
 
 namespace pgen {
+
+std::atomic<uint64_t> g_launch_count{0};
+
 namespace {
 
 struct Rec {
@@ -65,6 +69,8 @@ using namespace pgen;
 extern "C" {
 
 void pg_trace_enable(int on) { g_on.store(on ? 1 : 0); }
+
+uint64_t pg_launch_count(void) { return g_launch_count.load(std::memory_order_relaxed); }
 
 size_t pg_trace_dump(char* buf, size_t len)
 {

@@ -650,3 +650,24 @@ def test_throughput_probes_run():
     pipes = pg.int_pipe_rates(iters=256)
     assert r > 1e10
     assert set(pipes) == {"mul_wide", "mad32", "lop3", "add3"} and min(pipes.values()) > 1e11
+
+
+def test_launch_count_counts_every_kernel():
+    """pg_launch_count rises by one per kernel the library launches: one for a
+    Kronecker descent; for two-phase PBA the phase-1 prefix, one pass per
+    level (levels growing 1.5x from the 96K-entry prefix, in 16384-entry
+    granules), the scan and the emit, plus the 64-bit emit once any earlier
+    call forced the wide path in this process."""
+    c0 = pg.pg_launch_count()
+    pg.gen_kronecker(W.KRON_INITIATOR, 10, 4096, 7)
+    assert pg.pg_launch_count() - c0 == 1
+    B, n_b, m = 8, 30_000, 5
+    N_e, gran = n_b * m, 16384
+    lvl, levels = min(N_e, 6 * gran), 0
+    while lvl < N_e:
+        lvl = min(lvl + -(-(lvl // 2) // gran) * gran, N_e)
+        levels += 1
+    c0 = pg.pg_launch_count()
+    pg.gen_pba(B * n_b, m, B, 6, 1, 0.1, 3)
+    torch.cuda.synchronize()
+    assert pg.pg_launch_count() - c0 in (3 + levels, 4 + levels), levels
