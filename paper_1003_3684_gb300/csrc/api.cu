@@ -484,6 +484,22 @@ pg_status kron_common(const double* h_initiator, uint32_t n0, uint32_t k, uint64
     p.e0 = e0;
     p.div_e0 = make_fastdiv(e0);
     p.div_e0_32 = make_fastdiv32(e0);
+    // the widest digit group whose table fits and whose row and column parts
+    // fit 16 bits each
+    uint64_t E = e0, n0g = n0;
+    uint32_t g = 1;
+    while (g < k && E * e0 <= kDetGroupTable && n0g * n0 <= 65536) {
+        ++g;
+        E *= e0;
+        n0g *= n0;
+    }
+    p.g = g;
+    p.E = (uint32_t)E;
+    p.n_groups = k / g;
+    p.n_rest = k % g;
+    p.n0g = n0g;
+    p.div_E = make_fastdiv(E);
+    p.div_E32 = make_fastdiv32((uint32_t)E);
     if (e_end == ~(uint64_t)0) e_end = (uint64_t)total;
     if (e_begin > e_end || e_end > (uint64_t)total) return PG_EINVAL;
     const uint64_t count = e_end - e_begin;

@@ -11,11 +11,15 @@
 // Deterministic mode: the stack expansion of Sec. 3 visits meta-edges
 // depth first with children in seed order, so the e-th emitted edge is the
 // one whose base-e0 digits (most significant first) name the seed edge taken
-// at each expansion. Each thread decodes its own edge index; the order is
-// the stack's without running a stack.
+// at each expansion. Each thread decodes its own edge index, several digits
+// per lookup in a shared-memory table of digit groups; the order is the
+// stack's without running a stack.
 //
-// Both kernels are integer-ALU bound (Philox and digit arithmetic) and
-// write their output once, as coalesced 16-byte vector stores of two edges.
+// The stochastic kernels are integer-ALU bound (Philox and the descent); the
+// deterministic one is bound by its output. Both write their output once, as
+// coalesced 16-byte vector stores of two edges.
+#include <type_traits>
+
 #include "pg_internal.h"
 #include "pg_trace.h"
 
@@ -253,67 +257,100 @@ __global__ void __launch_bounds__(256) kron_generic_kernel(const __grid_constant
 }
 
 // ---- deterministic expansion: base-e0 digits of the edge index ------------
-__device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint16_t* ab,
-                                              uint64_t e, uint64_t& row, uint64_t& col)
+// Edge e's digits d_0 (most significant) ... d_{k-1} select seed edges
+// (a_d, b_d); row = sum a_{d_l} n0^(k-1-l), col likewise. Taken from the
+// least significant end, g digits at a time: tab[c] holds the row and column
+// parts (16 bits each) of the group of g digits whose base-e0 value is c, so
+// a group costs one division by e0^g and one lookup; the n_rest most
+// significant digits, if any, go one at a time through the seed table.
+// Digits and groups are clamped to their tables, so a lookup stays inside
+// them whatever the arithmetic gives.
+template <typename T, typename Div>
+__device__ __forceinline__ T div_by(T x, const Div& f);
+template <>
+__device__ __forceinline__ uint32_t div_by(uint32_t x, const FastDiv32& f)
+{
+    return fdiv32(x, f);
+}
+template <>
+__device__ __forceinline__ uint64_t div_by(uint64_t x, const FastDiv& f)
+{
+    return fdiv(x, f);
+}
+
+template <typename T>
+__device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint32_t* tab,
+                                              const uint16_t* ab, T e, T& row, T& col)
 {
     row = 0;
     col = 0;
-    uint64_t mul = 1;
-    for (uint32_t l = 0; l < p.k; ++l) {   // least significant digit first
-        const uint64_t q = fdiv(e, p.div_e0);
-        const uint32_t d = (uint32_t)(e - q * p.e0);
+    T mul = 1;
+    for (uint32_t i = 0; i < p.n_groups; ++i) {
+        T q;
+        if constexpr (sizeof(T) == 4) q = div_by(e, p.div_E32);
+        else q = div_by(e, p.div_E);
+        const T c = e - q * p.E;
         e = q;
-        const uint32_t v = PG_CHECK(d, p.e0) ? ab[d] : 0u;
-        row += (v & 0xFFu) * mul;
-        col += (v >> 8) * mul;
+        const uint32_t v = tab[(PG_CHECK(c, p.E) && c < p.E) ? (uint32_t)c : p.E - 1];
+        row += (T)(v & 0xFFFFu) * mul;
+        col += (T)(v >> 16) * mul;
+        mul *= (T)p.n0g;
+    }
+    for (uint32_t l = 0; l < p.n_rest; ++l) {
+        T q;
+        if constexpr (sizeof(T) == 4) q = div_by(e, p.div_e0_32);
+        else q = div_by(e, p.div_e0);
+        const T r = e - q * p.e0;
+        e = q;
+        const uint32_t v = ab[(PG_CHECK(r, p.e0) && r < p.e0) ? (uint32_t)r : p.e0 - 1];
+        row += (T)(v & 0xFFu) * mul;
+        col += (T)(v >> 8) * mul;
         mul *= p.n0;
     }
 }
 
-// The same digits in 32-bit arithmetic, for edge indices and ids below 2^32
-// (e0^k edges of n0^k vertices, both at most 2^32). The digit is clamped to
-// the table, so the lookup stays inside it whatever the arithmetic gives.
-__device__ __forceinline__ void kron_det_edge32(const KronDetParams& p, const uint16_t* ab,
-                                                uint32_t e, uint32_t& row, uint32_t& col)
+// Dynamic shared memory: the group table (E words), then the seed table.
+size_t kron_det_smem(const KronDetParams& p)
 {
-    row = 0;
-    col = 0;
-    uint32_t mul = 1;
-    for (uint32_t l = 0; l < p.k; ++l) {   // least significant digit first
-        const uint32_t q = fdiv32(e, p.div_e0_32);
-        const uint32_t r = e - q * p.e0;
-        const uint32_t d = r < p.e0 ? r : p.e0 - 1;
-        e = q;
-        const uint32_t v = ab[d];
-        row += (v & 0xFFu) * mul;
-        col += (v >> 8) * mul;
-        mul *= p.n0;
-    }
+    return (size_t)p.E * 4 + ((size_t)p.e0 * 2 + 15) / 16 * 16;
 }
 
+// kNarrow: every edge index of the launch and every id below 2^32, so the
+// digits, ids and weights are 32-bit.
 template <typename Id, bool kNarrow>
 __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ KronDetParams p,
                                                        Id* __restrict__ out, uint64_t e_begin,
                                                        uint64_t n_edges)
 {
-    __shared__ uint16_t ab[kMaxDetSeedEdges];
+    using T = typename std::conditional<kNarrow, uint32_t, uint64_t>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem);
+    uint16_t* ab = reinterpret_cast<uint16_t*>(smem + (size_t)p.E * 4);
     for (uint32_t t = threadIdx.x; t < p.e0; t += blockDim.x) ab[t] = p.ab[t];
+    __syncthreads();
+    // the table of digit groups, least significant digit first
+    for (uint32_t c = threadIdx.x; c < p.E; c += blockDim.x) {
+        uint32_t x = c, rr = 0, cc = 0, mul = 1;
+        for (uint32_t j = 0; j < p.g; ++j) {
+            const uint32_t q = fdiv32(x, p.div_e0_32);
+            const uint32_t d = x - q * p.e0;
+            x = q;
+            const uint32_t v = ab[(PG_CHECK(d, p.e0) && d < p.e0) ? d : p.e0 - 1];
+            rr += (v & 0xFFu) * mul;
+            cc += (v >> 8) * mul;
+            mul *= p.n0;
+        }
+        tab[c] = rr | (cc << 16);
+    }
     __syncthreads();
     const uint64_t n_pairs = (n_edges + 1) >> 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
         const uint64_t e = 2 * t;
         const bool two = e + 1 < n_edges;
-        uint64_t r0, c0, r1 = 0, c1 = 0;
-        if constexpr (kNarrow) {
-            uint32_t a0, b0, a1 = 0, b1 = 0;
-            kron_det_edge32(p, ab, (uint32_t)(e_begin + e), a0, b0);
-            if (two) kron_det_edge32(p, ab, (uint32_t)(e_begin + e + 1), a1, b1);
-            r0 = a0; c0 = b0; r1 = a1; c1 = b1;
-        } else {
-            kron_det_edge(p, ab, e_begin + e, r0, c0);
-            if (two) kron_det_edge(p, ab, e_begin + e + 1, r1, c1);
-        }
+        T r0, c0, r1 = 0, c1 = 0;
+        kron_det_edge<T>(p, tab, ab, (T)(e_begin + e), r0, c0);
+        if (two) kron_det_edge<T>(p, tab, ab, (T)(e_begin + e + 1), r1, c1);
         if (two) {
             if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
@@ -348,11 +385,12 @@ __global__ void __launch_bounds__(256) random_cells_kernel(const Key key, uint64
 }
 
 template <typename K>
-int grid_for(K kernel, uint64_t work_items, int threads)
+int grid_for(K kernel, uint64_t work_items, int threads, size_t smem = 0)
 {
     const int sms = device_sm_count();   // of the current device
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const uint64_t full = (uint64_t)sms * per_sm;
@@ -415,13 +453,29 @@ cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint6
     for (uint32_t l = 0; l < p.k && n_vertices <= ((uint64_t)1 << 32); ++l) n_vertices *= p.n0;
     const bool narrow = e_begin + n_edges <= ((uint64_t)1 << 32) &&
                         n_vertices <= ((uint64_t)1 << 32);
+    const size_t smem = kron_det_smem(p);
+    // the opt-in shared-memory size of every variant, set once per device
+    static PerDeviceOnce attrs;
+    const cudaError_t ae = attrs.run_current([] {
+        const int most = (int)(kDetGroupTable * 4 + kMaxDetSeedEdges * 2);
+        return first_error({
+            cudaFuncSetAttribute(kron_det_kernel<uint64_t, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, most),
+            cudaFuncSetAttribute(kron_det_kernel<uint64_t, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, most),
+            cudaFuncSetAttribute(kron_det_kernel<uint32_t, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, most),
+            cudaFuncSetAttribute(kron_det_kernel<uint32_t, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, most)});
+    });
+    if (ae != cudaSuccess) return ae;
     TraceScope trace("kron_det", s);
     if (id64) {
         auto k = narrow ? kron_det_kernel<uint64_t, true> : kron_det_kernel<uint64_t, false>;
-        { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
+        { k<<<grid_for(k, pairs, 256, smem), 256, smem, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
     } else {
         auto k = narrow ? kron_det_kernel<uint32_t, true> : kron_det_kernel<uint32_t, false>;
-        { k<<<grid_for(k, pairs, 256), 256, 0, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
+        { k<<<grid_for(k, pairs, 256, smem), 256, smem, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
     }
     return cudaGetLastError();
 }

@@ -77,12 +77,20 @@ struct KronParams {
 };
 
 // Deterministic Kronecker: seed edges (row-major; a in the low byte, b in
-// the high byte, so n0 <= 256) and the divisor for base-e0 digits.
+// the high byte, so n0 <= 256) and the divisor for base-e0 digits. The k
+// digits of an edge index are taken g at a time from the least significant
+// end: n_groups groups of g digits, each resolved by one lookup in a table of
+// all E = e0^g digit groups, then n_rest = k - g * n_groups single digits.
 constexpr int kMaxDetSeedEdges = 8192;
+constexpr uint32_t kDetGroupTable = 16384;   // entries of the digit-group table (64 KB)
 struct KronDetParams {
     uint32_t n0, k, e0, pad;
     FastDiv div_e0;
     FastDiv32 div_e0_32;   // for edge indices below 2^32
+    uint32_t g, E, n_groups, n_rest;
+    uint64_t n0g;          // n0^g: the weight of one digit group in row and column
+    FastDiv div_E;
+    FastDiv32 div_E32;
     uint16_t ab[kMaxDetSeedEdges];
 };
 
