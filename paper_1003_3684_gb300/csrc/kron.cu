@@ -309,6 +309,43 @@ __device__ __forceinline__ void kron_det_edge(const KronDetParams& p, const uint
     }
 }
 
+// The contribution of every digit above the lowest group, given q = e div
+// e0^g: the remaining groups, then the single digits, at weights from n0^g.
+template <typename T>
+__device__ __forceinline__ void kron_det_upper(const KronDetParams& p, const uint32_t* tab,
+                                               const uint16_t* ab, T e, T& row, T& col)
+{
+    row = 0;
+    col = 0;
+    T mul = (T)p.n0g;
+    for (uint32_t i = 1; i < p.n_groups; ++i) {
+        T q;
+        if constexpr (sizeof(T) == 4) q = div_by(e, p.div_E32);
+        else q = div_by(e, p.div_E);
+        const T c = e - q * p.E;
+        e = q;
+        const uint32_t v = tab[(PG_CHECK(c, p.E) && c < p.E) ? (uint32_t)c : p.E - 1];
+        row += (T)(v & 0xFFFFu) * mul;
+        col += (T)(v >> 16) * mul;
+        mul *= (T)p.n0g;
+    }
+    for (uint32_t l = 0; l < p.n_rest; ++l) {
+        T q;
+        if constexpr (sizeof(T) == 4) q = div_by(e, p.div_e0_32);
+        else q = div_by(e, p.div_e0);
+        const T r = e - q * p.e0;
+        e = q;
+        const uint32_t v = ab[(PG_CHECK(r, p.e0) && r < p.e0) ? (uint32_t)r : p.e0 - 1];
+        row += (T)(v & 0xFFu) * mul;
+        col += (T)(v >> 8) * mul;
+        mul *= p.n0;
+    }
+}
+
+// One CTA of kDetThreads threads per table copy: the table is built once per
+// CTA, and two CTAs (2 x 64 KB at most) fill an SM's warp slots.
+constexpr int kDetThreads = 1024;
+
 // Dynamic shared memory: the group table (E words), then the seed table.
 size_t kron_det_smem(const KronDetParams& p)
 {
@@ -318,7 +355,7 @@ size_t kron_det_smem(const KronDetParams& p)
 // kNarrow: every edge index of the launch and every id below 2^32, so the
 // digits, ids and weights are 32-bit.
 template <typename Id, bool kNarrow>
-__global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ KronDetParams p,
+__global__ void __launch_bounds__(kDetThreads) kron_det_kernel(const __grid_constant__ KronDetParams p,
                                                        Id* __restrict__ out, uint64_t e_begin,
                                                        uint64_t n_edges)
 {
@@ -349,8 +386,28 @@ __global__ void __launch_bounds__(256) kron_det_kernel(const __grid_constant__ K
         const uint64_t e = 2 * t;
         const bool two = e + 1 < n_edges;
         T r0, c0, r1 = 0, c1 = 0;
-        kron_det_edge<T>(p, tab, ab, (T)(e_begin + e), r0, c0);
-        if (two) kron_det_edge<T>(p, tab, ab, (T)(e_begin + e + 1), r1, c1);
+        // the two edges differ only in their lowest digit group unless it
+        // carries: the part above it is decoded once for both
+        const T ea = (T)(e_begin + e);
+        T q;
+        if constexpr (sizeof(T) == 4) q = div_by(ea, p.div_E32);
+        else q = div_by(ea, p.div_E);
+        const T lo = ea - q * p.E;
+        T ur, uc;
+        kron_det_upper<T>(p, tab, ab, q, ur, uc);
+        const uint32_t l0 = (PG_CHECK(lo, p.E) && lo < p.E) ? (uint32_t)lo : p.E - 1;
+        const uint32_t v0 = tab[l0];
+        r0 = (T)(v0 & 0xFFFFu) + ur;
+        c0 = (T)(v0 >> 16) + uc;
+        if (two) {
+            if (l0 + 1 < p.E) {
+                const uint32_t v1 = tab[l0 + 1];
+                r1 = (T)(v1 & 0xFFFFu) + ur;
+                c1 = (T)(v1 >> 16) + uc;
+            } else {
+                kron_det_edge<T>(p, tab, ab, ea + 1, r1, c1);
+            }
+        }
         if (two) {
             if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
@@ -472,10 +529,10 @@ cudaError_t launch_kron_det(const KronDetParams& p, int id64, void* d_out, uint6
     TraceScope trace("kron_det", s);
     if (id64) {
         auto k = narrow ? kron_det_kernel<uint64_t, true> : kron_det_kernel<uint64_t, false>;
-        { k<<<grid_for(k, pairs, 256, smem), 256, smem, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
+        { k<<<grid_for(k, pairs, kDetThreads, smem), kDetThreads, smem, s>>>(p, (uint64_t*)d_out, e_begin, n_edges); note_launch(); }
     } else {
         auto k = narrow ? kron_det_kernel<uint32_t, true> : kron_det_kernel<uint32_t, false>;
-        { k<<<grid_for(k, pairs, 256, smem), 256, smem, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
+        { k<<<grid_for(k, pairs, kDetThreads, smem), kDetThreads, smem, s>>>(p, (uint32_t*)d_out, e_begin, n_edges); note_launch(); }
     }
     return cudaGetLastError();
 }
