@@ -380,38 +380,55 @@ __global__ void __launch_bounds__(kDetThreads) kron_det_kernel(const __grid_cons
         tab[c] = rr | (cc << 16);
     }
     __syncthreads();
+    // each warp owns a contiguous range of pairs, lane l taking pairs l,
+    // l + 32, ... of it, so a lane's edge index grows by 64 per step: its
+    // lowest digit group advances by 64 and the part above it is decoded
+    // again only when that group wraps
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t n_pairs = (n_edges + 1) >> 1;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs; t += stride) {
-        const uint64_t e = 2 * t;
-        const bool two = e + 1 < n_edges;
-        T r0, c0, r1 = 0, c1 = 0;
-        // the two edges differ only in their lowest digit group unless it
-        // carries: the part above it is decoded once for both
-        const T ea = (T)(e_begin + e);
-        T q;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t per_warp = ((n_pairs + warps - 1) / warps + 31) / 32 * 32;
+    const uint64_t p_end0 = (gw + 1) * per_warp;
+    const uint64_t p_end = p_end0 < n_pairs ? p_end0 : n_pairs;
+    uint64_t pi = gw * per_warp + lane;
+    if (pi >= p_end) return;
+    T q, lo, ur, uc;
+    {
+        const T ea = (T)(e_begin + 2 * pi);
         if constexpr (sizeof(T) == 4) q = div_by(ea, p.div_E32);
         else q = div_by(ea, p.div_E);
-        const T lo = ea - q * p.E;
-        T ur, uc;
+        lo = ea - q * p.E;
+        if (!(PG_CHECK(lo, p.E) && lo < p.E)) lo = p.E - 1;
         kron_det_upper<T>(p, tab, ab, q, ur, uc);
-        const uint32_t l0 = (PG_CHECK(lo, p.E) && lo < p.E) ? (uint32_t)lo : p.E - 1;
+    }
+    for (; pi < p_end; pi += 32) {
+        const uint64_t e = 2 * pi;
+        const bool two = e + 1 < n_edges;
+        const uint32_t l0 = (uint32_t)lo;
         const uint32_t v0 = tab[l0];
-        r0 = (T)(v0 & 0xFFFFu) + ur;
-        c0 = (T)(v0 >> 16) + uc;
+        const T r0 = (T)(v0 & 0xFFFFu) + ur, c0 = (T)(v0 >> 16) + uc;
+        T r1 = 0, c1 = 0;
         if (two) {
             if (l0 + 1 < p.E) {
                 const uint32_t v1 = tab[l0 + 1];
                 r1 = (T)(v1 & 0xFFFFu) + ur;
                 c1 = (T)(v1 >> 16) + uc;
             } else {
-                kron_det_edge<T>(p, tab, ab, ea + 1, r1, c1);
+                kron_det_edge<T>(p, tab, ab, (T)(e_begin + e + 1), r1, c1);
             }
-        }
-        if (two) {
             if (PG_CHECK_OUT(e + 1, n_edges)) Pair2<Id>::store(out, e, r0, c0, r1, c1);
         } else {
             if (PG_CHECK_OUT(e, n_edges)) Pair2<Id>::store1(out, e, r0, c0);
+        }
+        lo += 64;
+        if (lo >= p.E) {
+            // the group wrapped (several times when e0^g < 64)
+            do {
+                lo -= p.E;
+                ++q;
+            } while (lo >= p.E);
+            kron_det_upper<T>(p, tab, ab, q, ur, uc);
         }
     }
 }
