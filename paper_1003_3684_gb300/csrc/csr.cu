@@ -657,27 +657,42 @@ __device__ __forceinline__ bool same_pair(const P& a, const P& b)
     return a.x == b.x && a.y == b.y;
 }
 
-// S[i] = i where a run of equal pairs starts, else 0 (a prefix max then
-// gives every position the start of its run).
-template <typename Id>
-__global__ void __launch_bounds__(256) csr_runstart_kernel(const typename PairOf<Id>::T* __restrict__ s,
-                                                           uint64_t M, uint64_t* __restrict__ S)
+template <typename P>
+__device__ __forceinline__ bool pair_less(const P& a, const P& b)
 {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride)
-        S[i] = (i == 0 || !same_pair(s[i], s[i - 1])) ? i : 0;
+    return a.x < b.x || (a.x == b.x && a.y < b.y);
+}
+
+// Where the run of pairs equal to e = s[i] starts. Runs are short in
+// practice, so the first steps go back one pair at a time; a longer run is
+// found by binary search of the sorted list below. (With ids outside the
+// vertex range the list need not be in lexicographic order there, and the
+// search only stays within [0, i].)
+template <typename P>
+__device__ __forceinline__ uint64_t run_start(const P* s, uint64_t i, const P& e)
+{
+    uint64_t j = i;
+    for (int t = 0; t < 8 && j > 0 && same_pair(s[j - 1], e); ++t) --j;
+    if (j == 0 || !same_pair(s[j - 1], e)) return j;
+    uint64_t lo = 0, hi = j;   // s[hi] == e: the first index of e lies in [lo, hi]
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (pair_less(s[mid], e)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Whether sorted position i survives the options.
 template <typename P>
-__device__ __forceinline__ bool keep_at(const P* s, uint64_t M, uint64_t i, uint32_t flags,
-                                        const uint64_t* S)
+__device__ __forceinline__ bool keep_at(const P* s, uint64_t M, uint64_t i, uint32_t flags)
 {
     const P e = s[i];
     if ((flags & kOptNoLoops) && e.x == e.y) return false;
     if (flags & kOptOdd) {
+        // the last pair of each run is kept when the run's length is odd
         const bool end = (i + 1 == M) || !same_pair(s[i + 1], e);
-        return end && (((i + 1 - S[i]) & 1) != 0);
+        return end && (((i + 1 - run_start(s, i, e)) & 1) != 0);
     }
     if (flags & kOptDedup) return i == 0 || !same_pair(s[i - 1], e);
     return true;
@@ -686,47 +701,62 @@ __device__ __forceinline__ bool keep_at(const P* s, uint64_t M, uint64_t i, uint
 template <typename Id>
 __global__ void __launch_bounds__(256) csr_keep_count_kernel(const typename PairOf<Id>::T* __restrict__ s,
                                                              uint64_t M, uint32_t flags,
-                                                             const uint64_t* __restrict__ S,
                                                              uint64_t* __restrict__ part)
 {
     __shared__ uint64_t s_warp[32];
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
     uint64_t cnt = 0;
     for (uint32_t t = threadIdx.x; t < kScanTile; t += blockDim.x)
-        if (base + t < M) cnt += keep_at(s, M, base + t, flags, S) ? 1 : 0;
+        if (base + t < M) cnt += keep_at(s, M, base + t, flags) ? 1 : 0;
     uint64_t total;
     block_exclusive_scan(cnt, s_warp, total);
     if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
-// Each thread takes kScanTile/256 consecutive positions of its tile, so the
-// kept destinations are written in sorted order; the last position of every
-// row writes row_ptr[src + 1] = kept entries up to and including it.
+// Each warp takes kScanTile/8 consecutive positions of its tile, 32 at a
+// time (consecutive lanes on consecutive pairs, so the reads coalesce): one
+// ballot per round gives every kept position its place among the warp's,
+// the warps' counts are scanned across the block, and the kept destinations
+// are written in sorted order. The last position of every row writes
+// row_ptr[src + 1] = kept entries up to and including it.
 template <typename Id>
-__global__ void __launch_bounds__(256) csr_keep_apply_kernel(const typename PairOf<Id>::T* __restrict__ s,
+__global__ void __launch_bounds__(256, 4) csr_keep_apply_kernel(const typename PairOf<Id>::T* __restrict__ s,
                                                              uint64_t M, uint64_t N, uint32_t flags,
-                                                             const uint64_t* __restrict__ S,
                                                              const uint64_t* __restrict__ part,
                                                              Id* __restrict__ col,
                                                              uint64_t* __restrict__ row_ptr)
 {
+    using P = typename PairOf<Id>::T;
     __shared__ uint64_t s_warp[32];
-    constexpr int per = kScanTile / 256;
-    const uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * per;
-    uint32_t keep = 0;
+    constexpr int kRounds = kScanTile / 256;   // rounds of 32 positions per warp
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint64_t wbase = (uint64_t)blockIdx.x * kScanTile + (uint64_t)wid * (32 * kRounds);
+    uint32_t m[kRounds];
+    uint32_t cnt = 0;
 #pragma unroll
-    for (int t = 0; t < per; ++t)
-        if (base + t < M && keep_at(s, M, base + t, flags, S)) keep |= 1u << t;
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t i = wbase + r * 32 + lane;
+        m[r] = __ballot_sync(0xFFFFFFFFu, i < M && keep_at(s, M, i, flags));
+        cnt += __popc(m[r]);
+    }
+    // the warps before this one in the tile, from lane 0's exclusive prefix
     uint64_t total;
-    uint64_t e = part[blockIdx.x] + block_exclusive_scan((uint64_t)__popc(keep), s_warp, total);
+    const uint64_t ex = block_exclusive_scan(lane == 0 ? (uint64_t)cnt : 0, s_warp, total);
+    uint64_t e = part[blockIdx.x] + __shfl_sync(0xFFFFFFFFu, ex, 0);
 #pragma unroll
-    for (int t = 0; t < per; ++t) {
-        const uint64_t i = base + t;
-        if (i >= M) break;
-        const uint64_t v = s[i].x;
-        if ((keep & (1u << t)) && PG_CHECK_OUT(e, M)) col[e] = (Id)s[i].y;
-        if (keep & (1u << t)) ++e;
-        if (v < N && (i + 1 == M || (uint64_t)s[i + 1].x != v)) row_ptr[v + 1] = e;
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t i = wbase + r * 32 + lane;
+        const bool keep = (m[r] >> lane) & 1u;
+        const uint64_t at = e + __popc(m[r] & lt);   // this position's place if kept
+        if (i < M) {
+            const P pv = s[i];
+            if (keep && PG_CHECK_OUT(at, M)) col[at] = (Id)pv.y;
+            const uint64_t v = pv.x;
+            if (v < N && (i + 1 == M || (uint64_t)s[i + 1].x != v))
+                row_ptr[v + 1] = at + (keep ? 1 : 0);
+        }
+        e += __popc(m[r]);
     }
 }
 
@@ -944,7 +974,7 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t N_dst
 // doubled) list, then the doubled list, and the parts of two scans.
 struct OptsLayout {
     CsrLayout L;
-    size_t off_x, off_cpart, off_spart, total;
+    size_t off_x, off_cpart, total;
     uint64_t M2, n_cparts;
 };
 
@@ -958,8 +988,6 @@ OptsLayout opts_layout(uint64_t M, uint64_t N, uint32_t flags, size_t pair_bytes
     if (flags & kOptSym) o += a256(O.M2 * pair_bytes);
     O.n_cparts = (O.M2 + kScanTile - 1) / kScanTile;
     O.off_cpart = o;
-    o += a256((O.n_cparts + 1) * 8);
-    O.off_spart = o;
     o += a256((O.n_cparts + 1) * 8);
     O.total = o;
     return O;
@@ -992,17 +1020,10 @@ cudaError_t csr_opts_impl(const void* d_edges, uint64_t M, uint64_t N, uint32_t 
         return err;
     TraceScope trace("csr_compact", s);
     if (M2 > 0) {
-        uint64_t* S = nullptr;
-        if (flags & kOptOdd) {
-            S = reinterpret_cast<uint64_t*>(spare);    // M2 words fit: a pair is >= 8 bytes
-            { csr_runstart_kernel<Id><<<sort_grid(M2), 256, 0, s>>>(cur, M2, S); note_launch(); }
-            if ((err = prefix_max(S, M2, (uint64_t*)(ws + O.off_spart), s)) != cudaSuccess)
-                return err;
-        }
         uint64_t* cpart = (uint64_t*)(ws + O.off_cpart);
-        { csr_keep_count_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, flags, S, cpart); note_launch(); }
+        { csr_keep_count_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, flags, cpart); note_launch(); }
         { scan_parts_kernel<<<1, 1024, 0, s>>>(cpart, O.n_cparts, sort_needed); note_launch(); }
-        { csr_keep_apply_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, N, flags, S, cpart,
+        { csr_keep_apply_kernel<Id><<<(unsigned)O.n_cparts, 256, 0, s>>>(cur, M2, N, flags, cpart,
                                                                         (Id*)d_col, d_row_ptr); note_launch(); }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
