@@ -20,9 +20,10 @@
 //                  earlier tiles' published counts, and coalesced writes.
 // Ranks come from counts in entry order, never from atomics racing for a
 // slot, so the result does not depend on the schedule, and a power-law row
-// (a hub with 10^5 edges) costs no more than any other key. A final pass
-// writes col and marks row ends. Both paths then take a parallel prefix
-// maximum over row_ptr, which fills the rows without edges. The sort kernels
+// (a hub with 10^5 edges) costs no more than any other key. The last pass
+// writes the destinations to col itself and raises row_ptr[src + 1] at the
+// last pair of each source in each tile. Both paths then take a parallel
+// prefix maximum over row_ptr, which fills the rows without edges. The sort kernels
 // read the sortedness flag and return at once when the grouped path applied,
 // so no host round trip decides the path.
 //
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     uint64_t M, int field, int shift, int bits, int nd, unsigned long long* __restrict__ status,
     uint32_t pass, const uint64_t* __restrict__ dstart, uint32_t* __restrict__ ticket,
     uint32_t* __restrict__ err, const uint32_t* __restrict__ sort_needed, uint32_t spin_limit,
-    uint32_t withhold)
+    uint32_t withhold, Id* __restrict__ col_out, uint64_t* __restrict__ row_ptr, uint64_t N)
 {
     using P = typename PairOf<Id>::T;
     constexpr int kItems = SortShape<Id>::items;
@@ -345,10 +346,27 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     }
     __syncthreads();
     // write runs: sorted position p goes to tbase[d] + p (one table read per pair)
+    if (col_out == nullptr) {
+        for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
+            const P v = buf[p];
+            const uint32_t d = digit_of(v, field, shift, mask, nd);
+            if (PG_CHECK(tbase[d] + p, M)) out[tbase[d] + p] = v;
+        }
+        return;
+    }
+    // the last pass of a CSR: the tile is in (src, dst) order, so each
+    // destination goes straight to col, and the last pair of each source
+    // in the tile raises row_ptr[src + 1] to its end (the source's last pair
+    // overall gives the maximum; the prefix maximum fills empty rows)
     for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
         const P v = buf[p];
         const uint32_t d = digit_of(v, field, shift, mask, nd);
-        if (PG_CHECK(tbase[d] + p, M)) out[tbase[d] + p] = v;
+        const uint64_t o = tbase[d] + p;
+        if (PG_CHECK_OUT(o, M)) col_out[o] = (Id)v.y;
+        const uint64_t src = v.x;
+        if (src < N && (p + 1 == n || (uint64_t)buf[p + 1].x != src))
+            atomicMax(reinterpret_cast<unsigned long long*>(row_ptr) + src + 1,
+                      (unsigned long long)(o + 1));
     }
 }
 
@@ -863,16 +881,20 @@ cudaError_t set_csr_attributes()
     });
 }
 
-// LSD radix passes over M pairs starting at `in` (dst digits, then src
-// digits). *sorted receives the sorted list (in itself when there is no
-// digit to sort), *spare a ping-pong buffer the result does not occupy.
+// LSD radix passes over M pairs starting at `in` (the digits of the key
+// (src << nd) | dst from its low end). *sorted receives the sorted list (in
+// itself when there is no digit to sort), *spare a ping-pong buffer the
+// result does not occupy. With col_final set, the last pass writes the CSR
+// directly instead of the sorted pairs: destinations to col_final, row ends
+// raised into row_ptr (zeroed by the caller); *sorted is then not a list.
 int sort_grid(uint64_t work);
 
 template <typename Id>
 cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t N, uint64_t N_dst,
                          const CsrLayout& L, unsigned char* ws, const uint32_t* sort_needed,
                          cudaStream_t s, const typename PairOf<Id>::T** sorted,
-                         typename PairOf<Id>::T** spare)
+                         typename PairOf<Id>::T** spare, Id* col_final = nullptr,
+                         uint64_t* row_ptr = nullptr)
 {
     using P = typename PairOf<Id>::T;
     P* buf[2] = {(P*)(ws + L.off_a), (P*)(ws + L.off_b)};
@@ -910,7 +932,7 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
             { radix_scatter_kernel<Id><<<L.n_tiles, kSortThreads, scatter_smem_bytes<Id>(), s>>>(
                 cur, buf[which], M, pl.field[k], pl.shift[k], pl.bits[k], pl.nd, status, k,
                 dstart + (size_t)k * kMaxBuckets, tickets + k, err, sort_needed, hk.spin_limit,
-                hk.withhold); note_launch(); }
+                hk.withhold, k + 1 == pl.n ? col_final : nullptr, row_ptr, N); note_launch(); }
             if ((err_c = cudaGetLastError()) != cudaSuccess) return err_c;
             cur = buf[which];
             which ^= 1;
@@ -962,11 +984,18 @@ cudaError_t csr_impl(const void* d_edges, uint64_t M, uint64_t N, uint64_t N_dst
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const P* cur;
     P* spare;
+    // with at least one digit to sort, the last pass writes col and the row
+    // ends itself; a key without digits (one vertex) leaves the list as it is
+    const bool in_sort = M > 0 && make_passes(N, N_dst).n > 0;
     if ((err = radix_passes<Id>((const P*)d_edges, M, N, N_dst, L, ws, sort_needed, s, &cur,
-                                &spare)) != cudaSuccess)
+                                &spare, in_sort ? (Id*)d_col : nullptr, d_row_ptr)) !=
+        cudaSuccess)
         return err;
-    TraceScope trace("csr_finish", s);
-    { csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed); note_launch(); }
+    if (!in_sort) {
+        TraceScope trace("csr_finish", s);
+        { csr_finish_kernel<Id><<<grid, 256, 0, s>>>(cur, M, N, d_row_ptr, (Id*)d_col, sort_needed); note_launch(); }
+    }
+    TraceScope trace("csr_rows", s);   // rows without edges take the previous row's end
     return prefix_max(d_row_ptr, N + 1, (uint64_t*)(ws + L.off_rpart), s);
 }
 
