@@ -44,6 +44,7 @@ constexpr int kMaxDigitBits = 8;
 constexpr uint32_t kMaxBuckets = 1u << kMaxDigitBits;
 constexpr uint32_t kScanTile = 4096;
 constexpr uint32_t kGroupedMaxRow = 32;
+constexpr uint32_t kHistCopies = 8;   // copies of each digit counter in the histogram kernel
 
 template <typename Id>
 struct PairOf;
@@ -88,7 +89,8 @@ struct PassList {
 };
 // Digit totals of every pass in one read of the list: tot[k][d] = number of
 // pairs whose pass-k digit is d. Each CTA counts into shared memory
-// (n passes x kMaxBuckets) and adds its counts once.
+// (n passes x kMaxBuckets counters, kHistCopies copies of each) and adds its
+// counts once.
 template <typename Id>
 __global__ void __launch_bounds__(256) radix_hist_all_kernel(
     const typename PairOf<Id>::T* __restrict__ in, uint64_t M, const __grid_constant__ PassList pl,
@@ -96,9 +98,13 @@ __global__ void __launch_bounds__(256) radix_hist_all_kernel(
 {
     extern __shared__ uint32_t h[];
     if (*sort_needed == 0) return;
+    // kHistCopies copies of every counter, interleaved, lane l adding to copy
+    // l mod kHistCopies: lanes whose digits agree (the skewed digits of a
+    // power-law graph) mostly hit different words
     const uint32_t cells = pl.n * kMaxBuckets;
-    for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x) h[t] = 0;
+    for (uint32_t t = threadIdx.x; t < cells * kHistCopies; t += blockDim.x) h[t] = 0;
     __syncthreads();
+    const uint32_t copy = threadIdx.x & (kHistCopies - 1);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     constexpr int kU = 4;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += kU * stride) {
@@ -111,15 +117,20 @@ __global__ void __launch_bounds__(256) radix_hist_all_kernel(
         for (uint32_t k = 0; k < pl.n; ++k) {
             const int field = pl.field[k], shift = pl.shift[k];
             const uint32_t mask = (1u << pl.bits[k]) - 1;
-            uint32_t* hk = h + k * kMaxBuckets;
+            uint32_t* hk = h + (k * kMaxBuckets) * kHistCopies + copy;
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (i0 + u * stride < M) atomicAdd(&hk[digit_of(e[u], field, shift, mask, pl.nd)], 1u);
+                if (i0 + u * stride < M)
+                    atomicAdd(&hk[digit_of(e[u], field, shift, mask, pl.nd) * kHistCopies], 1u);
         }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x)
-        if (h[t]) atomicAdd(&tot[t], (unsigned long long)h[t]);
+    for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x) {
+        uint32_t c = 0;
+#pragma unroll
+        for (uint32_t r = 0; r < kHistCopies; ++r) c += h[t * kHistCopies + r];
+        if (c) atomicAdd(&tot[t], (unsigned long long)c);
+    }
 }
 
 // Tile status words, one per (tile, digit): bits 63..59 the pass (1 + its
@@ -877,7 +888,7 @@ cudaError_t set_csr_attributes()
                                  (int)scatter_smem_bytes<Id>()),
             cudaFuncSetAttribute(radix_hist_all_kernel<Id>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kMaxPasses * 4 * kMaxBuckets))});
+                                 (int)(kMaxPasses * 4 * kMaxBuckets * kHistCopies))});
     });
 }
 
@@ -920,7 +931,7 @@ cudaError_t radix_passes(const typename PairOf<Id>::T* in, uint64_t M, uint64_t 
             TraceScope trace("csr_radix_hist", s);
             { zero_status_kernel<<<sort_grid(L.n_status / 2 + 1), 256, 0, s>>>(
                 (uint4*)status, (L.n_status * 8 + 15) / 16, sort_needed); note_launch(); }
-            { radix_hist_all_kernel<Id><<<sort_grid(M), 256, (size_t)pl.n * kMaxBuckets * 4, s>>>(
+            { radix_hist_all_kernel<Id><<<sort_grid(M), 256, (size_t)pl.n * kMaxBuckets * 4 * kHistCopies, s>>>(
                 cur, M, pl, tot, sort_needed); note_launch(); }
         }
         {
