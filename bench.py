@@ -608,6 +608,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
     stream = torch.cuda.current_stream()
     kind = cfg["kind"]
     csr_call = None   # (workspace, edges, vertices, flags) of a timed CSR call
+    e2e_outs = None   # every buffer a step writes, when more than `out`
 
     if kind == "pba":
         n, m, B, n0 = cfg["n"], cfg["m"], cfg["blocks"], cfg["n0"]
@@ -715,6 +716,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             pg.gen_random_cells(N, Mr, seed, out=out[M:])
             pg.edges_to_csr_opts(out, N, pg.CSR_ODD, row_ptr=row_ptr, col=col, workspace=ws)
         csr_call = (ws, E, N, pg.CSR_ODD)
+        e2e_outs = [out, row_ptr, col]
         units = {"kron_descent_n0_2": M}
         work = {"kron_descent_n0_2": kron_work(k)}
         units.update({kk: E for kk in CSR_WORK})
@@ -739,6 +741,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
                 pg.edges_to_csr(out, N, row_ptr=row_ptr, col=col, workspace=ws)
         if cfg.get("csr"):
             csr_call = (ws, M, N, 0)
+            e2e_outs = [out, row_ptr, col]
         units = {"kron_descent_n0_2": M}
         work = {"kron_descent_n0_2": kron_work(k)}
         if cfg.get("csr"):
@@ -893,7 +896,7 @@ def run_pgen(args, rank: int, world: int, local_rank: int):
             # copies go through a 4 GB pinned buffer per rank instead
             line["e2e"] = measure_e2e_pba(args, cfg, seed, out, ws, E, dev, world)
         else:
-            line["e2e"] = measure_e2e(args, step, out, cfg, E, dev, world, rank)
+            line["e2e"] = measure_e2e(args, step, e2e_outs or [out], cfg, E, dev, world, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, tsec, ns = oracle_sample(args.workload, cfg, args.cpu_budget)
         line["cpu_baseline"] = dict(value=v, unit=unit, cores=1, kind="oracle",
@@ -992,13 +995,13 @@ def measure_e2e_parts(args, cfg, seed, out, ws, E, dev, world):
                             f"{rows * 8 / 2**30:.1f} GiB, each range copied while the next is made")
 
 
-def measure_e2e(args, step, out, cfg, E, dev, world, rank):
+def measure_e2e(args, step, outs, cfg, E, dev, world, rank):
     import torch
     import torch.distributed as dist
-    out_bytes = out.numel() * out.element_size()
+    flats = [o.reshape(-1).view(torch.uint8) for o in outs]
+    out_bytes = sum(f.numel() for f in flats)
     chunk = min(out_bytes, 4 << 30)
     host = torch.empty(chunk, dtype=torch.uint8, pin_memory=True)
-    flat = out.view(torch.uint8).view(-1)
     h2d = 0
     if cfg["kind"] in ("kron", "kron_det"):
         init = torch.tensor(cfg["initiator"], dtype=torch.float64).pin_memory()
@@ -1008,9 +1011,14 @@ def measure_e2e(args, step, out, cfg, E, dev, world, rank):
         if h2d:
             init.to(dev, non_blocking=True)
         step()
-        for off in range(0, out_bytes, chunk):
-            n = min(chunk, out_bytes - off)
-            host[:n].copy_(flat[off:off + n], non_blocking=True)
+        pos = 0
+        for flat in flats:
+            for off in range(0, flat.numel(), chunk):
+                n = min(chunk, flat.numel() - off)
+                if pos + n > chunk:
+                    pos = 0
+                host[pos:pos + n].copy_(flat[off:off + n], non_blocking=True)
+                pos += n
         torch.cuda.current_stream().synchronize()
 
     e2e_step()
@@ -1027,8 +1035,10 @@ def measure_e2e(args, step, out, cfg, E, dev, world, rank):
     dt = float(t.item())
     return dict(value=E * steps * world / dt, unit="edges/s", h2d_bytes_per_step=h2d,
                 d2h_bytes_per_step=out_bytes, steps=steps,
-                host_buffer=f"pinned {chunk / 2**30:.1f} GiB, output copied through it in "
-                            f"{(out_bytes + chunk - 1) // chunk} chunk(s) per step")
+                host_buffer=f"pinned {chunk / 2**30:.1f} GiB; "
+                            + ("edges, row_ptr and col" if len(flats) == 3 else "the output")
+                            + f" copied into it in {(out_bytes + chunk - 1) // chunk} "
+                              "chunk(s) per step")
 
 
 # The default run's line also carries the metric's other parts, measured in
